@@ -1,0 +1,142 @@
+/*
+ * adc.h -- C ABI of the GB300 spin-adapted, density-fitted EA/IP-ADC(n) library
+ * (n = 2, 3): setup of the static blocks, the Davidson sigma-vector build
+ * sigma = M X, and the Davidson eigensolver with spectroscopic factors.
+ *
+ * Method: Banerjee & Sokolov, single-reference ADC for charged excitations.
+ *   - M and T matrices: Sec. II A, Eqs. M_ea, M_ip, T_ea, T_ip (orders k+l+m = n).
+ *   - Algorithm steps (amplitudes -> 1p-1p/1h-1h block -> Davidson sigma loop ->
+ *     spectroscopic factors): Sec. III A, step list and Table 1.
+ *   - Spin adaptation (closed shells): Sec. III B, Eqs. M_ij ... sigma_jka_bab,
+ *     with the renormalisation of the Appendix (Eqs. appendix_1..4).
+ *   - Density fitting (pq|rs) = sum_Q B^Q_pq B^Q_rs: Sec. III C, Eq. 19.
+ *
+ * Conventions
+ *   - Orbitals: nmo = nocc + nvir spatial orbitals, occupied first.
+ *   - eps[nmo]: orbital energies (Eh), diagonal Fock operator (H(0) of the
+ *     Moller-Plesset partitioning).
+ *   - Bq[naux][nmo][nmo]: density-fitting factors, row-major, symmetric in the
+ *     last two indices (only the symmetric part is meaningful).
+ *   - kind: ADC_EA (+1) or ADC_IP (-1).  order: 2 or 3.
+ *   - Spin-adapted vector layout (length adc_dim):
+ *       EA  [ Y_a (nvir) | Y_iab (nocc*nvir*nvir, b fastest) ]
+ *       IP  [ Y_i (nocc) | Y_ija (nocc*nocc*nvir, a fastest) ]
+ *     The metric of this basis is S = diag(1, 2 - P) where P swaps the two
+ *     like indices (Appendix norm); M is S-symmetric.
+ *   - Energies are eigenvalues w of the matrix the library applies:
+ *       EA  M_+ (w = E_{N+1} - E_N; the paper's electron affinity is -w),
+ *       IP  -M_- (w = E_{N-1} - E_N, the ionisation energy).
+ *   - Spectroscopic factors use the Appendix normalisation (P = 2 sum_p X_p^2,
+ *     so a Koopmans state has P = 2), with T through second order.
+ *
+ * Ownership: all inputs are caller-owned and copied; the handle owns every
+ * device allocation it makes and releases it in adc_destroy.  Pointers marked
+ * "host" are host memory; with on_device = 1 the vector arguments of
+ * adc_sigma are device pointers (current device, row-major [nvec][dim]).
+ * Work is issued on the handle's stream (adc_set_stream; default stream 0)
+ * and every call returns after its work has completed on that stream.
+ *
+ * Errors: every int-returning call returns ADC_OK (0) or a negative code; the
+ * message of the last failure is available from adc_last_error.  No C++
+ * exception crosses the ABI.  A failed handle stays valid for adc_destroy.
+ */
+#ifndef GB300_ADC_H
+#define GB300_ADC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ADC_OK 0
+#define ADC_ERR_ARG (-1)            /* invalid argument or size               */
+#define ADC_ERR_OOM (-2)            /* device allocation failed               */
+#define ADC_ERR_CUDA (-3)           /* CUDA runtime / cuBLAS failure          */
+#define ADC_ERR_NOT_CONVERGED (-4)  /* Davidson hit max_iter; outputs filled  */
+                                    /* with the best estimates                */
+#define ADC_ERR_TIMEOUT (-5)        /* a bounded device wait gave up          */
+
+#define ADC_EA 1
+#define ADC_IP (-1)
+
+#define ADC_PREC_FP64 0   /* every contraction in FP64                              */
+#define ADC_PREC_BF16X3 1 /* DF ladder (sigma and setup) on tcgen05 tensor cores:   */
+                          /* split hi/lo BF16 operands, 3 products, FP32 accumulate */
+                          /* per auxiliary chunk, FP64 across chunks; the rest FP64 */
+
+typedef struct adc_handle adc_handle; /* opaque */
+
+typedef struct {
+    int precision;           /* ADC_PREC_FP64 (default) or ADC_PREC_BF16X3            */
+    int max_space_per_root;  /* Davidson subspace limit per root (default 8)          */
+    int max_iter;            /* Davidson iteration limit (default 100)                */
+    int nguess_extra;        /* extra guess vectors beyond nroots (default 2)         */
+    double res_tol;          /* S-norm residual tolerance; <= 0 means sqrt(tol)       */
+    int aux_chunk;           /* auxiliary functions per ladder chunk; 0 = automatic   */
+} adc_options;
+
+/* Fill *opt with the defaults listed above.  Returns ADC_OK or ADC_ERR_ARG (NULL). */
+int adc_default_options(adc_options* opt);
+
+/*
+ * Set up one system (Sec. III A steps 1-3): copies eps and Bq to the device,
+ * forms the o-containing integral blocks, the MP amplitudes t(1) (and t(2),
+ * t1(2) for order 3), and the 1p-1p (EA) / 1h-1h (IP) block through order n.
+ *   eps  host [nmo]; Bq host [naux][nmo][nmo] (or device pointers if on_device=1)
+ *   nocc >= 1, nvir >= 1, naux >= 1, order in {2,3}, kind in {ADC_EA, ADC_IP}
+ *   opt  NULL for defaults
+ *   out  receives the new handle (NULL on failure)
+ * Errors: ADC_ERR_ARG, ADC_ERR_OOM, ADC_ERR_CUDA.
+ */
+int adc_setup(const double* eps, const double* Bq, int nocc, int nvir, int naux, int order, int kind,
+              const adc_options* opt, int on_device, adc_handle** out);
+
+/* Length of the spin-adapted vector (see layout above). */
+int adc_dim(const adc_handle* h, long long* dim);
+
+/* Issue subsequent work on this CUDA stream (cudaStream_t passed as void*). */
+int adc_set_stream(adc_handle* h, void* stream);
+
+/*
+ * sigma = M X for nvec vectors (Sec. III A step 4; Eqs. sigma_i_adapted_3,
+ * sigma_jka_bab and their EA analogue).  X and S are row-major [nvec][dim];
+ * host pointers if on_device = 0 (copied in and out inside the call), device
+ * pointers if on_device = 1.  X and S must not overlap.
+ * Errors: ADC_ERR_ARG (nvec < 1, NULL), ADC_ERR_OOM, ADC_ERR_CUDA.
+ */
+int adc_sigma(adc_handle* h, const double* X, double* S, int nvec, int on_device);
+
+/*
+ * Lowest nroots roots by multi-root Davidson in the S inner product (Eq. eig,
+ * Sec. III A step 4), then spectroscopic factors (Eq. spec_factors, Appendix).
+ *   tol       convergence threshold on the eigenvalue change (Eh)
+ *   guess     NULL or host [nguess = nroots][dim] initial vectors
+ *   energies  host [nroots], ascending
+ *   specfac   host [nroots] or NULL
+ *   vectors   host [nroots][dim] (S-normalised eigenvectors) or NULL
+ *   stats     host double[8] or NULL: {iterations, sigma vectors, seconds,
+ *             max S-norm residual, sigma seconds, 0, 0, 0}
+ * Errors: ADC_ERR_ARG, ADC_ERR_OOM, ADC_ERR_CUDA, ADC_ERR_NOT_CONVERGED.
+ */
+int adc_davidson(adc_handle* h, int nroots, double tol, const double* guess, double* energies, double* specfac,
+                 double* vectors, double* stats);
+
+/*
+ * Copy an intermediate to host memory (for verification).  name is one of
+ * "M11" [n1][n1], "t2" [o][o][v][v] (first-order doubles), "t2_2" (second-
+ * order doubles), "t1_2" [o][v], "diag" [dim].  n = number of doubles the
+ * buffer holds.  Errors: ADC_ERR_ARG (unknown name, buffer too small, or the
+ * intermediate does not exist at this order).
+ */
+int adc_get_tensor(adc_handle* h, const char* name, double* out, long long n);
+
+/* Message of the last error on this handle (or of the last failed adc_setup
+ * when h is NULL).  Never NULL. */
+const char* adc_last_error(const adc_handle* h);
+
+/* Release the handle and all its device memory.  NULL is ignored. */
+void adc_destroy(adc_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_ADC_H */

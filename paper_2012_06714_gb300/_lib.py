@@ -1,0 +1,182 @@
+"""ctypes binding of libadc.so: argument marshalling only (see include/adc.h)."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "_build", "libadc.so")
+_lib = None
+
+ADC_OK, ADC_ERR_ARG, ADC_ERR_OOM, ADC_ERR_CUDA, ADC_ERR_NOT_CONVERGED, ADC_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
+ADC_EA, ADC_IP = 1, -1
+PRECISIONS = {"fp64": 0, "bf16x3": 1}
+
+EXPORTED = [
+    "adc_default_options",
+    "adc_setup",
+    "adc_dim",
+    "adc_set_stream",
+    "adc_sigma",
+    "adc_davidson",
+    "adc_get_tensor",
+    "adc_last_error",
+    "adc_destroy",
+]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("max_space_per_root", ctypes.c_int),
+        ("max_iter", ctypes.c_int),
+        ("nguess_extra", ctypes.c_int),
+        ("res_tol", ctypes.c_double),
+        ("aux_chunk", ctypes.c_int),
+    ]
+
+
+class ADCError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _LIBPATH
+
+
+def build_library(verbose: bool = False) -> str:
+    from .build import build
+
+    return build(verbose=verbose)
+
+
+def load_library():
+    """Load libadc.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIBPATH):
+        raise ImportError(f"libadc.so not built at {_LIBPATH}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(_LIBPATH)
+    P, I, D, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    lib.adc_default_options.argtypes = [ctypes.POINTER(Options)]
+    lib.adc_setup.argtypes = [P, P, I, I, I, I, I, ctypes.POINTER(Options), I, ctypes.POINTER(P)]
+    lib.adc_dim.argtypes = [P, ctypes.POINTER(LL)]
+    lib.adc_set_stream.argtypes = [P, P]
+    lib.adc_sigma.argtypes = [P, P, P, I, I]
+    lib.adc_davidson.argtypes = [P, I, D, P, P, P, P, P]
+    lib.adc_get_tensor.argtypes = [P, ctypes.c_char_p, P, LL]
+    lib.adc_last_error.argtypes = [P]
+    lib.adc_last_error.restype = ctypes.c_char_p
+    lib.adc_destroy.argtypes = [P]
+    lib.adc_destroy.restype = None
+    for name in EXPORTED:
+        if not hasattr(lib, name):
+            raise ImportError(f"libadc.so lacks {name}")
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """(pointer, on_device) for a numpy array or a CUDA torch tensor."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data, 0
+    return a.data_ptr(), 1
+
+
+class ADC:
+    """One system: setup on construction, then sigma / davidson.
+
+    eps [nmo] and B [naux, nmo, nmo] are float64 numpy arrays (host) or CUDA
+    torch tensors (device); kind 'ea' or 'ip'; precision 'fp64' or 'bf16x3'.
+    """
+
+    def __init__(self, eps, B, nocc, order=3, kind="ea", precision="fp64", max_space_per_root=8, max_iter=100,
+                 nguess_extra=2, res_tol=0.0, aux_chunk=0):
+        lib = load_library()
+        self._lib = lib
+        opt = Options()
+        lib.adc_default_options(ctypes.byref(opt))
+        opt.precision = PRECISIONS[precision]
+        opt.max_space_per_root = max_space_per_root
+        opt.max_iter = max_iter
+        opt.nguess_extra = nguess_extra
+        opt.res_tol = res_tol
+        opt.aux_chunk = aux_chunk
+        if isinstance(eps, np.ndarray):
+            eps = np.ascontiguousarray(eps, dtype=np.float64)
+            B = np.ascontiguousarray(B, dtype=np.float64)
+        else:
+            eps = eps.contiguous().double()
+            B = B.contiguous().double()
+        naux, nmo = B.shape[0], B.shape[1]
+        self.nocc, self.nvir, self.naux, self.order, self.kind = nocc, nmo - nocc, naux, order, kind
+        pe, dev = _ptr(eps)
+        pb, _ = _ptr(B)
+        h = ctypes.c_void_p()
+        rc = lib.adc_setup(pe, pb, nocc, nmo - nocc, naux, order, ADC_EA if kind == "ea" else ADC_IP,
+                           ctypes.byref(opt), dev, ctypes.byref(h))
+        if rc != ADC_OK:
+            raise ADCError(rc, lib.adc_last_error(None).decode())
+        self._h = h
+        d = ctypes.c_longlong()
+        lib.adc_dim(h, ctypes.byref(d))
+        self.dim = d.value
+
+    def _check(self, rc):
+        if rc != ADC_OK:
+            raise ADCError(rc, self._lib.adc_last_error(self._h).decode())
+
+    def set_stream(self, stream_ptr: int):
+        self._check(self._lib.adc_set_stream(self._h, ctypes.c_void_p(stream_ptr)))
+
+    def sigma(self, X, out=None):
+        """sigma = M X for X [nvec, dim] (numpy -> numpy, CUDA tensor -> CUDA tensor)."""
+        if isinstance(X, np.ndarray):
+            X = np.ascontiguousarray(np.atleast_2d(X), dtype=np.float64)
+            S = np.empty_like(X) if out is None else out
+        else:
+            X = X.contiguous()
+            if X.dim() == 1:
+                X = X.unsqueeze(0)
+            S = X.new_empty(X.shape) if out is None else out
+        assert X.shape[-1] == self.dim
+        px, dev = _ptr(X)
+        ps, _ = _ptr(S)
+        self._check(self._lib.adc_sigma(self._h, px, ps, X.shape[0], dev))
+        return S
+
+    def davidson(self, nroots, tol=1e-8, guess=None, want_vectors=False):
+        """(energies, spectroscopic factors, vectors or None, stats dict)."""
+        e = np.zeros(nroots)
+        p = np.zeros(nroots)
+        vec = np.zeros((nroots, self.dim)) if want_vectors else None
+        st = np.zeros(8)
+        g = None if guess is None else np.ascontiguousarray(guess, dtype=np.float64)
+        rc = self._lib.adc_davidson(self._h, nroots, tol, None if g is None else g.ctypes.data, e.ctypes.data,
+                                    p.ctypes.data, None if vec is None else vec.ctypes.data, st.ctypes.data)
+        stats = dict(iterations=int(st[0]), sigma_vectors=int(st[1]), seconds=st[2], max_residual=st[3],
+                     sigma_seconds=st[4], status=rc)
+        if rc not in (ADC_OK, ADC_ERR_NOT_CONVERGED):
+            self._check(rc)
+        return e, p, vec, stats
+
+    def get(self, name, shape):
+        out = np.zeros(int(np.prod(shape)))
+        self._check(self._lib.adc_get_tensor(self._h, name.encode(), out.ctypes.data, out.size))
+        return out.reshape(shape)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.adc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,1111 @@
+// Spin-adapted, density-fitted EA/IP-ADC(n) (n = 2, 3) on one GPU: setup,
+// sigma = M X and the Davidson solver behind the C ABI of include/adc.h.
+//
+// Working equations (closed-shell, spin-adapted; (pq|rs) = sum_Q B^Q_pq B^Q_rs,
+// Eq. 19; t_ij^ab the alpha-beta MP amplitudes):
+//   t_ij^ab(1) = (ia|jb) / D_ij^ab
+//   D t_ij^ab(2) = sum_cd (ac|bd) t_ij^cd + sum_kl (ki|lj) t_kl^ab + W_ij^ab + W_ji^ba
+//   D_i^a t_i^a(2) = sum (kc|ad)(2 t_ik^dc - t_ik^cd) - sum (ki|lc)(2 t_kl^ac - t_kl^ca)
+// and the 1p-1p / 1h-1h block, coupling and 2p1h / 2h1p blocks written out
+// term by term below (each term's four-index form is in its comment).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/adc.h"
+#include "common.cuh"
+#include "ladder_tc.cuh"
+
+using namespace adc;
+
+struct adc_handle {
+    int o = 0, v = 0, naux = 0, order = 3, kind = ADC_EA;
+    adc_options opt{};
+    Ctx ctx;
+    // device tensors (FP64)
+    double *eps = nullptr, *Boo = nullptr, *Bov = nullptr, *Bvv = nullptr;
+    double *ovov = nullptr, *oovv = nullptr, *oooo = nullptr, *ooov = nullptr;
+    double *t = nullptr, *tau = nullptr, *t_2 = nullptr, *t1_2 = nullptr, *M11 = nullptr, *diag = nullptr;
+    LadderTC* tc = nullptr;  // tensor-core ladder state (BF16x3 operands of B^Q_vv)
+    std::vector<void*> owned;
+    std::string err;
+    long long dim() const {
+        return kind == ADC_EA ? (long long)v + (long long)o * v * v : (long long)o + (long long)o * o * v;
+    }
+    int n1() const { return kind == ADC_EA ? v : o; }
+    double* dmalloc(size_t n) {
+        void* p = nullptr;
+        ADC_CUDA(cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(double)));
+        owned.push_back(p);
+        return (double*)p;
+    }
+    ~adc_handle() {
+        ladder_tc_destroy(tc);
+        for (void* p : owned) cudaFree(p);
+        if (ctx.blas) cublasDestroy(ctx.blas);
+    }
+};
+
+static std::string g_setup_error = "no error";
+
+// --------------------------------------------------------------------------
+// ADC-specific elementwise kernels
+// --------------------------------------------------------------------------
+namespace {
+
+inline int grid_for(long long n) {
+    long long g = (n + 255) / 256;
+    return (int)std::min<long long>(std::max<long long>(g, 1), 152LL * 32);
+}
+#define GRID_STRIDE(i, n) for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
+
+// t[i,j,a,b] = ovov[i,a,j,b] / (e_i + e_j - e_a - e_b)
+__global__ void k_make_t(int o, int v, const double* __restrict__ eps, const double* __restrict__ ovov, double* __restrict__ t) {
+    long long n = (long long)o * o * v * v;
+    GRID_STRIDE(x, n) {
+        int b = x % v, a = (x / v) % v, j = (x / ((long long)v * v)) % o, i = x / ((long long)v * v * o);
+        double D = eps[i] + eps[j] - eps[o + a] - eps[o + b];
+        t[x] = ovov[(((long long)i * v + a) * o + j) * v + b] / D;
+    }
+}
+// X[i,j,a,b] /= D_ij^ab
+__global__ void k_div_D2(int o, int v, const double* __restrict__ eps, double* __restrict__ X) {
+    long long n = (long long)o * o * v * v;
+    GRID_STRIDE(x, n) {
+        int b = x % v, a = (x / v) % v, j = (x / ((long long)v * v)) % o, i = x / ((long long)v * v * o);
+        X[x] /= eps[i] + eps[j] - eps[o + a] - eps[o + b];
+    }
+}
+__global__ void k_div_D1(int o, int v, const double* __restrict__ eps, double* __restrict__ X) {
+    long long n = (long long)o * v;
+    GRID_STRIDE(x, n) {
+        int a = x % v, i = x / v;
+        X[x] /= eps[i] - eps[o + a];
+    }
+}
+// Y~ = 2 Y - P Y on the 2p1h (EA: swap last two) or 2h1p (IP: swap first two) part, nvec blocks
+__global__ void k_two_minus_swap(int ea, int o, int v, long long nvec, const double* __restrict__ Y, double* __restrict__ Yt) {
+    long long blk = ea ? (long long)o * v * v : (long long)o * o * v;
+    long long n = nvec * blk;
+    GRID_STRIDE(x, n) {
+        long long r = x % blk, base = x - r;
+        long long s;
+        if (ea) {
+            int b = r % v, a = (r / v) % v;
+            long long i = r / ((long long)v * v);
+            s = (i * v + b) * v + a;
+        } else {
+            int a = r % v, k = (r / v) % o;
+            long long j = r / ((long long)o * v);
+            s = ((long long)k * o + j) * v + a;
+        }
+        Yt[x] = 2.0 * Y[x] - Y[base + s];
+    }
+}
+// full vectors [nvec][dim]: out = S Y (mode 0) or S^-1 Y (mode 1); S = diag(1, 2 - P)
+__global__ void k_metric(int ea, int o, int v, long long nvec, const double* __restrict__ Y, double* __restrict__ out, int inverse) {
+    long long n1 = ea ? v : o;
+    long long blk = ea ? (long long)o * v * v : (long long)o * o * v;
+    long long dim = n1 + blk;
+    long long n = nvec * dim;
+    GRID_STRIDE(x, n) {
+        long long r = x % dim, base = x - r;
+        if (r < n1) {
+            out[x] = Y[x];
+            continue;
+        }
+        long long q = r - n1, s;
+        if (ea) {
+            int b = q % v, a = (q / v) % v;
+            long long i = q / ((long long)v * v);
+            s = (i * v + b) * v + a;
+        } else {
+            int a = q % v, k = (q / v) % o;
+            long long j = q / ((long long)o * v);
+            s = ((long long)k * o + j) * v + a;
+        }
+        double y = Y[x], ys = Y[base + n1 + s];
+        out[x] = inverse ? (2.0 * y + ys) / 3.0 : 2.0 * y - ys;
+    }
+}
+// zeroth-order 2p1h/2h1p diagonal: EA e_a + e_b - e_i ; IP (M_-) e_i + e_j - e_a
+__device__ inline double d22(int ea, int o, int v, const double* eps, long long q) {
+    if (ea) {
+        int b = q % v, a = (q / v) % v;
+        long long i = q / ((long long)v * v);
+        return eps[o + a] + eps[o + b] - eps[i];
+    } else {
+        int a = q % v, k = (q / v) % o;
+        long long j = q / ((long long)o * v);
+        return eps[j] + eps[k] - eps[o + a];
+    }
+}
+// S2 += d22 * Y2 over nvec blocks
+__global__ void k_diag22(int ea, int o, int v, long long nvec, const double* __restrict__ eps, const double* __restrict__ Y2,
+                         double* __restrict__ S2) {
+    long long blk = ea ? (long long)o * v * v : (long long)o * o * v;
+    long long n = nvec * blk;
+    GRID_STRIDE(x, n) { S2[x] += d22(ea, o, v, eps, x % blk) * Y2[x]; }
+}
+// preconditioner diagonal of the applied matrix: [diag(M11), +/- d22]
+__global__ void k_diag(int ea, int o, int v, const double* __restrict__ eps, const double* __restrict__ M11, double* __restrict__ D) {
+    long long n1 = ea ? v : o;
+    long long blk = ea ? (long long)o * v * v : (long long)o * o * v;
+    long long n = n1 + blk;
+    GRID_STRIDE(x, n) {
+        if (x < n1)
+            D[x] = M11[x * n1 + x];
+        else
+            D[x] = ea ? d22(1, o, v, eps, x - n1) : -d22(0, o, v, eps, x - n1);
+    }
+}
+// copy strided blocks: out[n][r] = in[n*ldin + off + r]
+__global__ void k_gather(long long nvec, long long len, const double* __restrict__ in, long long ldin, long long off,
+                         double* __restrict__ out, long long ldout, long long offo, double beta) {
+    long long n = nvec * len;
+    GRID_STRIDE(x, n) {
+        long long r = x % len, k = x / len;
+        double val = in[k * ldin + off + r];
+        double* dst = out + k * ldout + offo + r;
+        *dst = (beta == 0.0) ? val : val + beta * *dst;
+    }
+}
+// Davidson correction: out[r][x] = R[r][x] / (w_r - D[x]) with |w - D| >= 1e-8
+__global__ void k_precond(long long nr, long long dim, const double* __restrict__ R, const double* __restrict__ w,
+                          const double* __restrict__ D, double* __restrict__ out) {
+    long long n = nr * dim;
+    GRID_STRIDE(x, n) {
+        long long r = x / dim, k = x % dim;
+        double den = w[r] - D[k];
+        if (fabs(den) < 1e-8) den = den < 0 ? -1e-8 : 1e-8;
+        out[x] = R[x] / den;
+    }
+}
+// unit vectors: V[k][idx[k]] = 1
+__global__ void k_units(int n, const long long* __restrict__ idx, long long dim, double* __restrict__ V) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) V[(long long)k * dim + idx[k]] = 1.0;
+}
+
+void launch_check(Ctx& c) {
+    ++c.kernels;
+    ADC_CUDA(cudaGetLastError());
+}
+
+// mark/release helper
+struct Scope {
+    Arena& a;
+    Arena::Mark m;
+    explicit Scope(Arena& ar) : a(ar), m(ar.mark()) {}
+    ~Scope() { a.release(m); }
+};
+
+T tn(const double* p, std::initializer_list<long long> d) { return T{p, std::vector<long long>(d)}; }
+
+}  // namespace
+
+// --------------------------------------------------------------------------
+// DF ladder: out[n] += sum_Q B^Q_vv X_n B^Q_vv for nmat v x v matrices
+//   (sum_cd (ac|bd) X_n[c,d]; the vvvv integral is never formed)
+// --------------------------------------------------------------------------
+static void ladder(adc_handle* h, const double* X, long long nmat, double* out) {
+    Ctx& c = h->ctx;
+    const long long v = h->v;
+    if (h->opt.precision == ADC_PREC_BF16X3 && h->tc) {
+        ladder_tc_apply(*h->tc, c, X, nmat, out);
+        return;
+    }
+    Scope sc(c.arena);
+    // chunk the matrices so the intermediate stays modest
+    long long per = std::max<long long>(1, std::min<long long>(nmat, (256LL << 20) / (8 * v * v)));
+    double* W = c.arena.dalloc((size_t)(per * v * v));
+    for (long long n0 = 0; n0 < nmat; n0 += per) {
+        long long nn = std::min(per, nmat - n0);
+        for (int Q = 0; Q < h->naux; ++Q) {
+            const double* BQ = h->Bvv + (long long)Q * v * v;
+            // W[(n,c), b] = X[(n,c), d] B^Q[d, b]
+            gemm(c, false, false, nn * v, v, v, 1.0, X + n0 * v * v, v, 0, BQ, v, 0, 0.0, W, v, 0, 1);
+            // out_n[a, b] += B^Q[a, c] W_n[c, b]
+            gemm(c, false, false, v, v, v, 1.0, BQ, v, 0, W, v, v * v, 1.0, out + n0 * v * v, v, v * v, nn);
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// setup (Sec. III A steps 1-3)
+// --------------------------------------------------------------------------
+static void sym_add(adc_handle* h, const double* X, double* M, int n, double alpha) {
+    // M += alpha (X + X^T)
+    Ctx& c = h->ctx;
+    axpby(c, (long long)n * n, alpha, X, 1.0, M);
+    Shape s{2, {n, n}};
+    int perm[2] = {1, 0};
+    permute(c, X, s, perm, M, alpha, 1.0);
+}
+
+static void setup_m11_ea(adc_handle* h) {
+    Ctx& c = h->ctx;
+    const long long o = h->o, v = h->v, Q = h->naux;
+    Scope sc(c.arena);
+    double* M = h->M11;
+    double* X = c.arena.dalloc(v * v);
+    const double* t = h->t;
+    // second order: -sum t_kl^ac [(kb|lc) - 1/2 (kc|lb)] + (a<->b)
+    einsum(c, "klac,kblc->ab", -1.0, tn(t, {o, o, v, v}), tn(h->ovov, {o, v, o, v}), 0.0, X, {v, v});
+    einsum(c, "klac,kclb->ab", 0.5, tn(t, {o, o, v, v}), tn(h->ovov, {o, v, o, v}), 1.0, X, {v, v});
+    sym_add(h, X, M, (int)v, 1.0);
+    if (h->order < 3) return;
+    const double *t2 = h->t_2, *t1 = h->t1_2;
+    // t1(2): sum_kc t_k^c [2 (kc|ab) - (kb|ac)] + (a<->b)
+    double* g = c.arena.dalloc(Q);
+    einsum(c, "Qkc,kc->Q", 1.0, tn(h->Bov, {Q, o, v}), tn(t1, {o, v}), 0.0, g, {Q});
+    einsum(c, "Q,Qab->ab", 2.0, tn(g, {Q}), tn(h->Bvv, {Q, v, v}), 0.0, X, {v, v});
+    double* Hq = c.arena.dalloc(Q * o * v);
+    einsum(c, "kc,Qac->Qka", 1.0, tn(t1, {o, v}), tn(h->Bvv, {Q, v, v}), 0.0, Hq, {Q, o, v});
+    einsum(c, "Qkb,Qka->ab", -1.0, tn(h->Bov, {Q, o, v}), tn(Hq, {Q, o, v}), 1.0, X, {v, v});
+    // t2(2): same shape as second order
+    einsum(c, "klac,kblc->ab", -1.0, tn(t2, {o, o, v, v}), tn(h->ovov, {o, v, o, v}), 1.0, X, {v, v});
+    einsum(c, "klac,kclb->ab", 0.5, tn(t2, {o, o, v, v}), tn(h->ovov, {o, v, o, v}), 1.0, X, {v, v});
+    // vvvv, one open line: -sum t_kl^ac [L_kl^bc - 1/2 L_kl^cb], L_kl = sum_cd (bc..) ladder of t
+    double* L = c.arena.dalloc(o * o * v * v);
+    fill(c, o * o * v * v, 0.0, L);
+    ladder(h, t, o * o, L);
+    einsum(c, "klac,klbc->ab", -1.0, tn(t, {o, o, v, v}), tn(L, {o, o, v, v}), 1.0, X, {v, v});
+    einsum(c, "klac,klcb->ab", 0.5, tn(t, {o, o, v, v}), tn(L, {o, o, v, v}), 1.0, X, {v, v});
+    // ring with the open lines on the amplitudes (G_A with t_km^ac, G_B with t_km^ca):
+    //   u1 = -t/2 + t^T, u2 = t - 2 t^T, u3 = t - t^T/2 (t^T swaps the virtual pair)
+    double* u = c.arena.dalloc(o * o * v * v);
+    double* G = c.arena.dalloc(o * o * v * v);
+    Shape s4{4, {o, o, v, v}};
+    int swp[4] = {0, 1, 3, 2};
+    auto make_u = [&](double a, double b) {  // u = a t + b t^T
+        axpby(c, o * o * v * v, a, t, 0.0, u);
+        permute(c, t, s4, swp, u, b, 1.0);
+    };
+    // G_A = sum_ld (kl|db) u1_lm^cd + sum_ld (kb|ld) u2_lm^cd
+    make_u(-0.5, 1.0);
+    einsum(c, "kldb,lmcd->kmcb", 1.0, tn(h->oovv, {o, o, v, v}), tn(u, {o, o, v, v}), 0.0, G, {o, o, v, v});
+    double* GB = c.arena.dalloc(o * o * v * v);
+    einsum(c, "kbld,lmcd->kmcb", 1.0, tn(h->ovov, {o, v, o, v}), tn(u, {o, o, v, v}), 0.0, GB, {o, o, v, v});  // u1 part of G_B
+    make_u(1.0, -2.0);
+    einsum(c, "kbld,lmcd->kmcb", 1.0, tn(h->ovov, {o, v, o, v}), tn(u, {o, o, v, v}), 1.0, G, {o, o, v, v});
+    make_u(1.0, -0.5);
+    einsum(c, "kldb,lmcd->kmcb", 1.0, tn(h->oovv, {o, o, v, v}), tn(u, {o, o, v, v}), 1.0, GB, {o, o, v, v});
+    einsum(c, "kmac,kmcb->ab", 1.0, tn(t, {o, o, v, v}), tn(G, {o, o, v, v}), 1.0, X, {v, v});
+    einsum(c, "kmca,kmcb->ab", 1.0, tn(t, {o, o, v, v}), tn(GB, {o, o, v, v}), 1.0, X, {v, v});
+    sym_add(h, X, M, (int)v, 1.0);
+    // vvvv with both lines on the integral: sum_cd [2 (ab|cd) - (ad|cb)] (2X - X')_cd
+    double* Z = c.arena.dalloc(v * v);
+    einsum(c, "klce,klde->cd", 2.0, tn(t, {o, o, v, v}), tn(t, {o, o, v, v}), 0.0, Z, {v, v});
+    einsum(c, "klce,kled->cd", -1.0, tn(t, {o, o, v, v}), tn(t, {o, o, v, v}), 1.0, Z, {v, v});
+    einsum(c, "Qcd,cd->Q", 1.0, tn(h->Bvv, {Q, v, v}), tn(Z, {v, v}), 0.0, g, {Q});
+    einsum(c, "Q,Qab->ab", 2.0, tn(g, {Q}), tn(h->Bvv, {Q, v, v}), 1.0, M, {v, v});
+    double* H2 = c.arena.dalloc(Q * v * v);
+    einsum(c, "Qad,cd->Qac", 1.0, tn(h->Bvv, {Q, v, v}), tn(Z, {v, v}), 0.0, H2, {Q, v, v});
+    einsum(c, "Qac,Qcb->ab", -1.0, tn(H2, {Q, v, v}), tn(h->Bvv, {Q, v, v}), 1.0, M, {v, v});
+    // ring with both lines on the integral: -sum_kl [2 (kl|ab) - (kb|la)] (2U - U')_kl
+    double* U = c.arena.dalloc(o * o);
+    einsum(c, "kmcd,lmcd->kl", 2.0, tn(t, {o, o, v, v}), tn(t, {o, o, v, v}), 0.0, U, {o, o});
+    einsum(c, "kmcd,lmdc->kl", -1.0, tn(t, {o, o, v, v}), tn(t, {o, o, v, v}), 1.0, U, {o, o});
+    einsum(c, "klab,kl->ab", -2.0, tn(h->oovv, {o, o, v, v}), tn(U, {o, o}), 1.0, M, {v, v});
+    einsum(c, "kbla,kl->ab", 1.0, tn(h->ovov, {o, v, o, v}), tn(U, {o, o}), 1.0, M, {v, v});
+}
+
+static void setup_m11_ip(adc_handle* h) {
+    // paper's M_- 1h-1h block, negated at the end (the library applies -M_-)
+    Ctx& c = h->ctx;
+    const long long o = h->o, v = h->v;
+    Scope sc(c.arena);
+    double* M = h->M11;
+    double* X = c.arena.dalloc(o * o);
+    const double* t = h->t;
+    einsum(c, "ilcd,jcld->ij", 1.0, tn(t, {o, o, v, v}), tn(h->ovov, {o, v, o, v}), 0.0, X, {o, o});
+    einsum(c, "ilcd,jdlc->ij", -0.5, tn(t, {o, o, v, v}), tn(h->ovov, {o, v, o, v}), 1.0, X, {o, o});
+    sym_add(h, X, M, (int)o, 1.0);
+    if (h->order >= 3) {
+        const double *t2 = h->t_2, *t1 = h->t1_2;
+        // t1(2): sum_kc t_k^c [2 (ck|ij) - (cj|ik)]
+        einsum(c, "kc,ijkc->ij", 2.0, tn(t1, {o, v}), tn(h->ooov, {o, o, o, v}), 0.0, X, {o, o});
+        einsum(c, "kc,ikjc->ij", -1.0, tn(t1, {o, v}), tn(h->ooov, {o, o, o, v}), 1.0, X, {o, o});
+        // t2(2): sum t2_ik^cd [(cj|dk) - 1/2 (ck|dj)]
+        einsum(c, "ikcd,jckd->ij", 1.0, tn(t2, {o, o, v, v}), tn(h->ovov, {o, v, o, v}), 1.0, X, {o, o});
+        einsum(c, "ikcd,kcjd->ij", -0.5, tn(t2, {o, o, v, v}), tn(h->ovov, {o, v, o, v}), 1.0, X, {o, o});
+        // oooo with one open line: sum t_ik^cd (jl|km)(t_lm^cd - 1/2 t_lm^dc)
+        double* u = c.arena.dalloc(o * o * v * v);
+        double* G = c.arena.dalloc(o * o * v * v);
+        Shape s4{4, {o, o, v, v}};
+        int swp[4] = {0, 1, 3, 2};
+        auto make_u = [&](double a, double b) {
+            axpby(c, o * o * v * v, a, t, 0.0, u);
+            permute(c, t, s4, swp, u, b, 1.0);
+        };
+        make_u(1.0, -0.5);
+        einsum(c, "jlkm,lmcd->jkcd", 1.0, tn(h->oooo, {o, o, o, o}), tn(u, {o, o, v, v}), 0.0, G, {o, o, v, v});
+        einsum(c, "ikcd,jkcd->ij", 1.0, tn(t, {o, o, v, v}), tn(G, {o, o, v, v}), 1.0, X, {o, o});
+        // ring with open lines on the amplitudes: w1 = t/2 - t^T, w2 = -t + 2 t^T, w3 = -t + t^T/2
+        double* GB = c.arena.dalloc(o * o * v * v);
+        make_u(0.5, -1.0);
+        einsum(c, "ljcd,klde->kecj", 1.0, tn(h->oovv, {o, o, v, v}), tn(u, {o, o, v, v}), 0.0, G, {o, v, v, o});
+        einsum(c, "jcld,klde->kecj", 1.0, tn(h->ovov, {o, v, o, v}), tn(u, {o, o, v, v}), 0.0, GB, {o, v, v, o});
+        make_u(-1.0, 2.0);
+        einsum(c, "jcld,klde->kecj", 1.0, tn(h->ovov, {o, v, o, v}), tn(u, {o, o, v, v}), 1.0, G, {o, v, v, o});
+        make_u(-1.0, 0.5);
+        einsum(c, "ljcd,klde->kecj", 1.0, tn(h->oovv, {o, o, v, v}), tn(u, {o, o, v, v}), 1.0, GB, {o, v, v, o});
+        einsum(c, "ikce,kecj->ij", 1.0, tn(t, {o, o, v, v}), tn(G, {o, v, v, o}), 1.0, X, {o, o});
+        einsum(c, "ikec,kecj->ij", 1.0, tn(t, {o, o, v, v}), tn(GB, {o, v, v, o}), 1.0, X, {o, o});
+        sym_add(h, X, M, (int)o, 1.0);
+        // oooo with both lines on the integral: -[2 (ij|kl) - (il|kj)] (2U - U')_kl
+        double* U = c.arena.dalloc(o * o);
+        einsum(c, "kmcd,lmcd->kl", 2.0, tn(t, {o, o, v, v}), tn(t, {o, o, v, v}), 0.0, U, {o, o});
+        einsum(c, "kmcd,lmdc->kl", -1.0, tn(t, {o, o, v, v}), tn(t, {o, o, v, v}), 1.0, U, {o, o});
+        einsum(c, "ijkl,kl->ij", -2.0, tn(h->oooo, {o, o, o, o}), tn(U, {o, o}), 1.0, M, {o, o});
+        einsum(c, "ilkj,kl->ij", 1.0, tn(h->oooo, {o, o, o, o}), tn(U, {o, o}), 1.0, M, {o, o});
+        // ring with both lines on the integral: [2 (cd|ij) - (cj|id)] (2X - X')_cd
+        double* Z = c.arena.dalloc(v * v);
+        einsum(c, "klce,klde->cd", 2.0, tn(t, {o, o, v, v}), tn(t, {o, o, v, v}), 0.0, Z, {v, v});
+        einsum(c, "klce,kled->cd", -1.0, tn(t, {o, o, v, v}), tn(t, {o, o, v, v}), 1.0, Z, {v, v});
+        einsum(c, "ijcd,cd->ij", 2.0, tn(h->oovv, {o, o, v, v}), tn(Z, {v, v}), 1.0, M, {o, o});
+        einsum(c, "jcid,cd->ij", -1.0, tn(h->ovov, {o, v, o, v}), tn(Z, {v, v}), 1.0, M, {o, o});
+    }
+    axpby(c, o * o, 0.0, M, -1.0, M);  // apply -M_-
+}
+
+static void setup(adc_handle* h, const double* eps_in, const double* B_in, int on_device) {
+    Ctx& c = h->ctx;
+    ADC_BLAS(cublasCreate(&c.blas));
+    ADC_BLAS(cublasSetStream(c.blas, c.stream));
+    ADC_BLAS(cublasSetMathMode(c.blas, CUBLAS_DEFAULT_MATH));
+    const long long o = h->o, v = h->v, Q = h->naux, nmo = o + v;
+    h->eps = h->dmalloc(nmo);
+    ADC_CUDA(cudaMemcpyAsync(h->eps, eps_in, nmo * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             c.stream));
+    h->Boo = h->dmalloc(Q * o * o);
+    h->Bov = h->dmalloc(Q * o * v);
+    h->Bvv = h->dmalloc(Q * v * v);
+    {
+        // slice B^Q into its oo, ov and vv blocks (2-D strided copies per block)
+        cudaMemcpyKind kd = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        for (long long q = 0; q < Q; ++q) {
+            const double* src = B_in + q * nmo * nmo;
+            ADC_CUDA(cudaMemcpy2DAsync(h->Boo + q * o * o, o * sizeof(double), src, nmo * sizeof(double), o * sizeof(double), o, kd, c.stream));
+            ADC_CUDA(cudaMemcpy2DAsync(h->Bov + q * o * v, v * sizeof(double), src + o, nmo * sizeof(double), v * sizeof(double), o, kd, c.stream));
+            ADC_CUDA(cudaMemcpy2DAsync(h->Bvv + q * v * v, v * sizeof(double), src + o * nmo + o, nmo * sizeof(double), v * sizeof(double), v, kd,
+                                       c.stream));
+        }
+    }
+    if (h->opt.precision == ADC_PREC_BF16X3) h->tc = ladder_tc_create(c, h->Bvv, (int)Q, (int)v, h->opt.aux_chunk);
+    // integrals (Eq. 19)
+    h->ovov = h->dmalloc(o * v * o * v);
+    h->oovv = h->dmalloc(o * o * v * v);
+    h->oooo = h->dmalloc(o * o * o * o);
+    h->ooov = h->dmalloc(o * o * o * v);
+    einsum(c, "Qia,Qjb->iajb", 1.0, tn(h->Bov, {Q, o, v}), tn(h->Bov, {Q, o, v}), 0.0, h->ovov, {o, v, o, v});
+    einsum(c, "Qij,Qab->ijab", 1.0, tn(h->Boo, {Q, o, o}), tn(h->Bvv, {Q, v, v}), 0.0, h->oovv, {o, o, v, v});
+    einsum(c, "Qij,Qkl->ijkl", 1.0, tn(h->Boo, {Q, o, o}), tn(h->Boo, {Q, o, o}), 0.0, h->oooo, {o, o, o, o});
+    einsum(c, "Qij,Qka->ijka", 1.0, tn(h->Boo, {Q, o, o}), tn(h->Bov, {Q, o, v}), 0.0, h->ooov, {o, o, o, v});
+    // amplitudes (Eqs. t_singles, t_doubles)
+    h->t = h->dmalloc(o * o * v * v);
+    k_make_t<<<grid_for(o * o * v * v), 256, 0, c.stream>>>((int)o, (int)v, h->eps, h->ovov, h->t);
+    launch_check(c);
+    h->tau = h->dmalloc(o * o * v * v);
+    {
+        axpby(c, o * o * v * v, 2.0, h->t, 0.0, h->tau);
+        Shape s4{4, {o, o, v, v}};
+        int swp[4] = {0, 1, 3, 2};
+        permute(c, h->t, s4, swp, h->tau, -1.0, 1.0);
+    }
+    if (h->order >= 3) {
+        Scope sc(c.arena);
+        const double* t = h->t;
+        h->t_2 = h->dmalloc(o * o * v * v);
+        double* N = h->t_2;
+        fill(c, o * o * v * v, 0.0, N);
+        ladder(h, t, o * o, N);  // sum_cd (ac|bd) t_ij^cd
+        einsum(c, "kilj,klab->ijab", 1.0, tn(h->oooo, {o, o, o, o}), tn(t, {o, o, v, v}), 1.0, N, {o, o, v, v});
+        double* W = c.arena.dalloc(o * o * v * v);
+        einsum(c, "kcjb,ikac->ijab", 2.0, tn(h->ovov, {o, v, o, v}), tn(t, {o, o, v, v}), 0.0, W, {o, o, v, v});
+        einsum(c, "kcjb,ikca->ijab", -1.0, tn(h->ovov, {o, v, o, v}), tn(t, {o, o, v, v}), 1.0, W, {o, o, v, v});
+        einsum(c, "kjbc,ikac->ijab", -1.0, tn(h->oovv, {o, o, v, v}), tn(t, {o, o, v, v}), 1.0, W, {o, o, v, v});
+        einsum(c, "kjac,ikcb->ijab", -1.0, tn(h->oovv, {o, o, v, v}), tn(t, {o, o, v, v}), 1.0, W, {o, o, v, v});
+        axpby(c, o * o * v * v, 1.0, W, 1.0, N);
+        Shape s4{4, {o, o, v, v}};
+        int tr[4] = {1, 0, 3, 2};
+        permute(c, W, s4, tr, N, 1.0, 1.0);
+        k_div_D2<<<grid_for(o * o * v * v), 256, 0, c.stream>>>((int)o, (int)v, h->eps, N);
+        launch_check(c);
+        // singles: D t_i^a = sum (kc|ad)(2 t_ik^dc - t_ik^cd) - sum (ki|lc)(2 t_kl^ac - t_kl^ca)
+        h->t1_2 = h->dmalloc(o * v);
+        double* Gq = c.arena.dalloc(Q * o * v);
+        einsum(c, "Qkc,ikdc->Qid", 1.0, tn(h->Bov, {Q, o, v}), tn(h->tau, {o, o, v, v}), 0.0, Gq, {Q, o, v});
+        einsum(c, "Qid,Qad->ia", 1.0, tn(Gq, {Q, o, v}), tn(h->Bvv, {Q, v, v}), 0.0, h->t1_2, {o, v});
+        einsum(c, "kilc,klac->ia", -1.0, tn(h->ooov, {o, o, o, v}), tn(h->tau, {o, o, v, v}), 1.0, h->t1_2, {o, v});
+        k_div_D1<<<grid_for(o * v), 256, 0, c.stream>>>((int)o, (int)v, h->eps, h->t1_2);
+        launch_check(c);
+    }
+    const long long n1 = h->n1();
+    h->M11 = h->dmalloc(n1 * n1);
+    {
+        // zeroth order: diag(eps)
+        std::vector<double> e(nmo);
+        ADC_CUDA(cudaMemcpyAsync(e.data(), h->eps, nmo * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        ADC_CUDA(cudaStreamSynchronize(c.stream));
+        std::vector<double> m0(n1 * n1, 0.0);
+        for (long long p = 0; p < n1; ++p) m0[p * n1 + p] = e[h->kind == ADC_EA ? o + p : p];
+        ADC_CUDA(cudaMemcpyAsync(h->M11, m0.data(), n1 * n1 * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+        ADC_CUDA(cudaStreamSynchronize(c.stream));
+    }
+    if (h->kind == ADC_EA)
+        setup_m11_ea(h);
+    else
+        setup_m11_ip(h);
+    h->diag = h->dmalloc(h->dim());
+    k_diag<<<grid_for(h->dim()), 256, 0, c.stream>>>(h->kind == ADC_EA, (int)o, (int)v, h->eps, h->M11, h->diag);
+    launch_check(c);
+    ADC_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+// --------------------------------------------------------------------------
+// sigma (Sec. III A step 4; Eqs. sigma_i_adapted_3, sigma_jka_bab, EA analogue)
+// --------------------------------------------------------------------------
+static void sigma_ea(adc_handle* h, const double* Xin, double* Sout, long long nv_) {
+    Ctx& c = h->ctx;
+    const long long o = h->o, v = h->v, Q = h->naux, n = nv_, dim = h->dim(), blk = o * v * v;
+    Scope sc(c.arena);
+    // split into 1p and 2p1h parts (contiguous per part)
+    double* y1 = c.arena.dalloc(n * v);
+    double* Y2 = c.arena.dalloc(n * blk);
+    double* s1 = c.arena.dalloc(n * v);
+    double* S2 = c.arena.dalloc(n * blk);
+    k_gather<<<grid_for(n * v), 256, 0, c.stream>>>(n, v, Xin, dim, 0, y1, v, 0, 0.0);
+    launch_check(c);
+    k_gather<<<grid_for(n * blk), 256, 0, c.stream>>>(n, blk, Xin, dim, v, Y2, blk, 0, 0.0);
+    launch_check(c);
+    double* Yt = c.arena.dalloc(n * blk);
+    k_two_minus_swap<<<grid_for(n * blk), 256, 0, c.stream>>>(1, (int)o, (int)v, n, Y2, Yt);
+    launch_check(c);
+    // 1p row: M_ab Y_b
+    einsum(c, "nb,ab->na", 1.0, tn(y1, {n, v}), tn(h->M11, {v, v}), 0.0, s1, {n, v});
+    // coupling row, first order: sum (ad|jc) Y~_jcd
+    double* Wq = c.arena.dalloc(n * Q * v);
+    einsum(c, "Qjc,njcd->nQd", 1.0, tn(h->Bov, {Q, o, v}), tn(Yt, {n, o, v, v}), 0.0, Wq, {n, Q, v});
+    einsum(c, "nQd,Qda->na", 1.0, tn(Wq, {n, Q, v}), tn(h->Bvv, {Q, v, v}), 1.0, s1, {n, v});
+    // 2p1h column, first order: (cb|ia) Y_c
+    double* hq = c.arena.dalloc(n * Q * v);
+    einsum(c, "nc,Qcb->nQb", 1.0, tn(y1, {n, v}), tn(h->Bvv, {Q, v, v}), 0.0, hq, {n, Q, v});
+    einsum(c, "Qia,nQb->niab", 1.0, tn(h->Bov, {Q, o, v}), tn(hq, {n, Q, v}), 0.0, S2, {n, o, v, v});
+    // 2p1h block, zeroth order
+    k_diag22<<<grid_for(n * blk), 256, 0, c.stream>>>(1, (int)o, (int)v, n, h->eps, Y2, S2);
+    launch_check(c);
+    if (h->order >= 3) {
+        const double *t = h->t, *tau = h->tau;
+        // coupling row, second order:
+        //  sum (al|jm) t_lm^dc Y~_jcd
+        double* Z = c.arena.dalloc(n * o * o * o);
+        einsum(c, "lmdc,njcd->nlmj", 1.0, tn(t, {o, o, v, v}), tn(Yt, {n, o, v, v}), 0.0, Z, {n, o, o, o});
+        double* P = c.arena.dalloc(n * Q * o);
+        einsum(c, "Qjm,nlmj->nQl", 1.0, tn(h->Boo, {Q, o, o}), tn(Z, {n, o, o, o}), 0.0, P, {n, Q, o});
+        einsum(c, "nQl,Qla->na", 1.0, tn(P, {n, Q, o}), tn(h->Bov, {Q, o, v}), 1.0, s1, {n, v});
+        //  sum (ad|em)(2 t_jm^ce - t_jm^ec) Y~_jcd
+        double* V = c.arena.dalloc(n * o * v * v);
+        einsum(c, "jmce,njcd->nmed", 1.0, tn(tau, {o, o, v, v}), tn(Yt, {n, o, v, v}), 0.0, V, {n, o, v, v});
+        einsum(c, "nmed,Qme->nQd", 1.0, tn(V, {n, o, v, v}), tn(h->Bov, {Q, o, v}), 0.0, Wq, {n, Q, v});
+        einsum(c, "nQd,Qda->na", 1.0, tn(Wq, {n, Q, v}), tn(h->Bvv, {Q, v, v}), 1.0, s1, {n, v});
+        //  - sum (am|ed) [t_jm^ce Y~_jcd + t_jm^ed Y~_jdc]   (the two exchange-type terms)
+        einsum(c, "jmce,njcd->nmed", 1.0, tn(t, {o, o, v, v}), tn(Yt, {n, o, v, v}), 0.0, V, {n, o, v, v});
+        einsum(c, "jmec,njdc->nmed", 1.0, tn(t, {o, o, v, v}), tn(Yt, {n, o, v, v}), 1.0, V, {n, o, v, v});
+        double* R = c.arena.dalloc(n * Q * o);
+        einsum(c, "nmed,Qed->nQm", 1.0, tn(V, {n, o, v, v}), tn(h->Bvv, {Q, v, v}), 0.0, R, {n, Q, o});
+        einsum(c, "nQm,Qma->na", -1.0, tn(R, {n, Q, o}), tn(h->Bov, {Q, o, v}), 1.0, s1, {n, v});
+        // 2p1h column, second order:
+        //  sum_lm (cl|im) t_lm^ba Y_c
+        double* p = c.arena.dalloc(n * Q * o);
+        einsum(c, "nc,Qlc->nQl", 1.0, tn(y1, {n, v}), tn(h->Bov, {Q, o, v}), 0.0, p, {n, Q, o});
+        double* Pl = c.arena.dalloc(n * o * o * o);
+        einsum(c, "nQl,Qim->nlim", 1.0, tn(p, {n, Q, o}), tn(h->Boo, {Q, o, o}), 0.0, Pl, {n, o, o, o});
+        einsum(c, "nlim,lmba->niab", 1.0, tn(Pl, {n, o, o, o}), tn(t, {o, o, v, v}), 1.0, S2, {n, o, v, v});
+        //  sum_me (cb|em)(2 t_im^ae - t_im^ea) Y_c
+        double* q = c.arena.dalloc(n * o * v * v);
+        einsum(c, "nQb,Qme->nbme", 1.0, tn(hq, {n, Q, v}), tn(h->Bov, {Q, o, v}), 0.0, q, {n, v, o, v});
+        einsum(c, "nbme,imae->niab", 1.0, tn(q, {n, v, o, v}), tn(tau, {o, o, v, v}), 1.0, S2, {n, o, v, v});
+        //  - sum_me (cm|eb) t_im^ae Y_c - sum_me (cm|ea) t_im^eb Y_c
+        einsum(c, "nQm,Qeb->nmeb", 1.0, tn(p, {n, Q, o}), tn(h->Bvv, {Q, v, v}), 0.0, q, {n, o, v, v});
+        einsum(c, "nmeb,imae->niab", -1.0, tn(q, {n, o, v, v}), tn(t, {o, o, v, v}), 1.0, S2, {n, o, v, v});
+        einsum(c, "nmea,imeb->niab", -1.0, tn(q, {n, o, v, v}), tn(t, {o, o, v, v}), 1.0, S2, {n, o, v, v});
+        // 2p1h block, first order: ladder sum_cd (ac|bd) Y_icd (vvvv never stored)
+        ladder(h, Y2, n * o, S2);
+        //  - (ac|ji) Y_jcb + 2 (ai|jc) Y_jcb - (ai|jc) Y_jbc - (bd|ji) Y_jad
+        einsum(c, "jiac,njcb->niab", -1.0, tn(h->oovv, {o, o, v, v}), tn(Y2, {n, o, v, v}), 1.0, S2, {n, o, v, v});
+        einsum(c, "iajc,njcb->niab", 2.0, tn(h->ovov, {o, v, o, v}), tn(Y2, {n, o, v, v}), 1.0, S2, {n, o, v, v});
+        einsum(c, "iajc,njbc->niab", -1.0, tn(h->ovov, {o, v, o, v}), tn(Y2, {n, o, v, v}), 1.0, S2, {n, o, v, v});
+        einsum(c, "jibd,njad->niab", -1.0, tn(h->oovv, {o, o, v, v}), tn(Y2, {n, o, v, v}), 1.0, S2, {n, o, v, v});
+    }
+    k_gather<<<grid_for(n * v), 256, 0, c.stream>>>(n, v, s1, v, 0, Sout, dim, 0, 0.0);
+    launch_check(c);
+    k_gather<<<grid_for(n * blk), 256, 0, c.stream>>>(n, blk, S2, blk, 0, Sout, dim, v, 0.0);
+    launch_check(c);
+}
+
+static void sigma_ip(adc_handle* h, const double* Xin, double* Sout, long long nv_) {
+    // contributions of the paper's M_- are accumulated, then negated; M11 already holds -M_-11
+    Ctx& c = h->ctx;
+    const long long o = h->o, v = h->v, Q = h->naux, n = nv_, dim = h->dim(), blk = o * o * v;
+    Scope sc(c.arena);
+    double* y1 = c.arena.dalloc(n * o);
+    double* Y2 = c.arena.dalloc(n * blk);
+    double* s1 = c.arena.dalloc(n * o);
+    double* S2 = c.arena.dalloc(n * blk);
+    k_gather<<<grid_for(n * o), 256, 0, c.stream>>>(n, o, Xin, dim, 0, y1, o, 0, 0.0);
+    launch_check(c);
+    k_gather<<<grid_for(n * blk), 256, 0, c.stream>>>(n, blk, Xin, dim, o, Y2, blk, 0, 0.0);
+    launch_check(c);
+    double* Yt = c.arena.dalloc(n * blk);
+    k_two_minus_swap<<<grid_for(n * blk), 256, 0, c.stream>>>(0, (int)o, (int)v, n, Y2, Yt);
+    launch_check(c);
+    // coupling row, first order: -(ki|ja) Y~_jka
+    double* G = c.arena.dalloc(n * Q * o);
+    einsum(c, "Qja,njka->nQk", 1.0, tn(h->Bov, {Q, o, v}), tn(Yt, {n, o, o, v}), 0.0, G, {n, Q, o});
+    einsum(c, "nQk,Qki->ni", -1.0, tn(G, {n, Q, o}), tn(h->Boo, {Q, o, o}), 0.0, s1, {n, o});
+    // 2h1p column, first order: -(ki|ja) Y_i
+    double* g = c.arena.dalloc(n * Q * o);
+    einsum(c, "ni,Qki->nQk", 1.0, tn(y1, {n, o}), tn(h->Boo, {Q, o, o}), 0.0, g, {n, Q, o});
+    einsum(c, "nQk,Qja->njka", -1.0, tn(g, {n, Q, o}), tn(h->Bov, {Q, o, v}), 0.0, S2, {n, o, o, v});
+    k_diag22<<<grid_for(n * blk), 256, 0, c.stream>>>(0, (int)o, (int)v, n, h->eps, Y2, S2);
+    launch_check(c);
+    if (h->order >= 3) {
+        const double *t = h->t, *tau = h->tau;
+        // coupling row, second order
+        //  - sum (ad|ie) t_jk^de Y~_jka
+        double* Z = c.arena.dalloc(n * v * v * v);
+        einsum(c, "jkde,njka->ndea", 1.0, tn(t, {o, o, v, v}), tn(Yt, {n, o, o, v}), 0.0, Z, {n, v, v, v});
+        double* Hq = c.arena.dalloc(n * Q * v);
+        einsum(c, "ndea,Qad->nQe", 1.0, tn(Z, {n, v, v, v}), tn(h->Bvv, {Q, v, v}), 0.0, Hq, {n, Q, v});
+        einsum(c, "nQe,Qie->ni", -1.0, tn(Hq, {n, Q, v}), tn(h->Bov, {Q, o, v}), 1.0, s1, {n, o});
+        //  - sum (ik|lc)(2 t_jl^ac - t_jl^ca) Y~_jka + sum (ic|lk) t_jl^ac Y~_jka + sum (ic|lj) t_kl^ca Y~_jka
+        double* G2 = c.arena.dalloc(n * o * o * v);
+        einsum(c, "jlac,njka->nklc", 1.0, tn(tau, {o, o, v, v}), tn(Yt, {n, o, o, v}), 0.0, G2, {n, o, o, v});
+        einsum(c, "iklc,nklc->ni", -1.0, tn(h->ooov, {o, o, o, v}), tn(G2, {n, o, o, v}), 1.0, s1, {n, o});
+        einsum(c, "jlac,njka->nlkc", 1.0, tn(t, {o, o, v, v}), tn(Yt, {n, o, o, v}), 0.0, G2, {n, o, o, v});
+        einsum(c, "lkic,nlkc->ni", 1.0, tn(h->ooov, {o, o, o, v}), tn(G2, {n, o, o, v}), 1.0, s1, {n, o});
+        einsum(c, "klca,njka->nljc", 1.0, tn(t, {o, o, v, v}), tn(Yt, {n, o, o, v}), 0.0, G2, {n, o, o, v});
+        einsum(c, "ljic,nljc->ni", 1.0, tn(h->ooov, {o, o, o, v}), tn(G2, {n, o, o, v}), 1.0, s1, {n, o});
+        // 2h1p column, second order (same tensor, applied to Y_i)
+        double* bq = c.arena.dalloc(n * Q * v);
+        einsum(c, "ni,Qie->nQe", 1.0, tn(y1, {n, o}), tn(h->Bov, {Q, o, v}), 0.0, bq, {n, Q, v});
+        double* w = c.arena.dalloc(n * v * v * v);
+        einsum(c, "nQe,Qad->nead", 1.0, tn(bq, {n, Q, v}), tn(h->Bvv, {Q, v, v}), 0.0, w, {n, v, v, v});
+        einsum(c, "nead,jkde->njka", -1.0, tn(w, {n, v, v, v}), tn(t, {o, o, v, v}), 1.0, S2, {n, o, o, v});
+        double* m = c.arena.dalloc(n * o * o * v);
+        einsum(c, "ni,iklc->nklc", 1.0, tn(y1, {n, o}), tn(h->ooov, {o, o, o, v}), 0.0, m, {n, o, o, v});
+        einsum(c, "nklc,jlac->njka", -1.0, tn(m, {n, o, o, v}), tn(tau, {o, o, v, v}), 1.0, S2, {n, o, o, v});
+        einsum(c, "ni,lkic->nlkc", 1.0, tn(y1, {n, o}), tn(h->ooov, {o, o, o, v}), 0.0, m, {n, o, o, v});
+        einsum(c, "nlkc,jlac->njka", 1.0, tn(m, {n, o, o, v}), tn(t, {o, o, v, v}), 1.0, S2, {n, o, o, v});
+        einsum(c, "ni,ljic->nljc", 1.0, tn(y1, {n, o}), tn(h->ooov, {o, o, o, v}), 0.0, m, {n, o, o, v});
+        einsum(c, "nljc,klca->njka", 1.0, tn(m, {n, o, o, v}), tn(t, {o, o, v, v}), 1.0, S2, {n, o, o, v});
+        // 2h1p block, first order: -(ki|lj) Y_kla + (ki|ab) Y_kjb - 2 (ia|kb) Y_kjb + (ia|kb) Y_jkb + (kj|ab) Y_ikb
+        einsum(c, "kilj,nkla->nija", -1.0, tn(h->oooo, {o, o, o, o}), tn(Y2, {n, o, o, v}), 1.0, S2, {n, o, o, v});
+        einsum(c, "kiab,nkjb->nija", 1.0, tn(h->oovv, {o, o, v, v}), tn(Y2, {n, o, o, v}), 1.0, S2, {n, o, o, v});
+        einsum(c, "iakb,nkjb->nija", -2.0, tn(h->ovov, {o, v, o, v}), tn(Y2, {n, o, o, v}), 1.0, S2, {n, o, o, v});
+        einsum(c, "iakb,njkb->nija", 1.0, tn(h->ovov, {o, v, o, v}), tn(Y2, {n, o, o, v}), 1.0, S2, {n, o, o, v});
+        einsum(c, "kjab,nikb->nija", 1.0, tn(h->oovv, {o, o, v, v}), tn(Y2, {n, o, o, v}), 1.0, S2, {n, o, o, v});
+    }
+    // negate (M_IP = -M_-) and add the 1h-1h block (already negated)
+    einsum(c, "nj,ij->ni", 1.0, tn(y1, {n, o}), tn(h->M11, {o, o}), -1.0, s1, {n, o});
+    k_gather<<<grid_for(n * o), 256, 0, c.stream>>>(n, o, s1, o, 0, Sout, dim, 0, 0.0);
+    launch_check(c);
+    axpby(c, n * blk, 0.0, S2, -1.0, S2);
+    k_gather<<<grid_for(n * blk), 256, 0, c.stream>>>(n, blk, S2, blk, 0, Sout, dim, o, 0.0);
+    launch_check(c);
+}
+
+static void sigma_device(adc_handle* h, const double* X, double* S, long long nvec) {
+    if (h->kind == ADC_EA)
+        sigma_ea(h, X, S, nvec);
+    else
+        sigma_ip(h, X, S, nvec);
+}
+
+// --------------------------------------------------------------------------
+// Davidson (Eq. eig) in the S inner product
+// --------------------------------------------------------------------------
+namespace {
+
+// cyclic Jacobi eigen-decomposition of a symmetric n x n matrix (row-major);
+// eigenvalues ascending, eigenvectors as columns of V
+void jacobi_eigh(int n, std::vector<double> A, std::vector<double>& w, std::vector<double>& V) {
+    V.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                double a = A[(size_t)i * n + j] * A[(size_t)i * n + j];
+                tot += a;
+                if (i != j) off += a;
+            }
+        if (off <= 1e-30 * std::max(tot, 1e-300)) break;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double apq = A[(size_t)p * n + q];
+                if (std::fabs(apq) < 1e-300) continue;
+                double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+                double theta = 0.5 * (aqq - app) / apq;
+                double tt = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                double cs = 1.0 / std::sqrt(tt * tt + 1.0), sn = tt * cs;
+                for (int k = 0; k < n; ++k) {
+                    double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+                    A[(size_t)k * n + p] = cs * akp - sn * akq;
+                    A[(size_t)k * n + q] = sn * akp + cs * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+                    A[(size_t)p * n + k] = cs * apk - sn * aqk;
+                    A[(size_t)q * n + k] = sn * apk + cs * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+                    V[(size_t)k * n + p] = cs * vkp - sn * vkq;
+                    V[(size_t)k * n + q] = sn * vkp + cs * vkq;
+                }
+            }
+    }
+    std::vector<int> idx(n);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::vector<double> d(n);
+    for (int i = 0; i < n; ++i) d[i] = A[(size_t)i * n + i];
+    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return d[a] < d[b]; });
+    w.resize(n);
+    std::vector<double> Vs((size_t)n * n);
+    for (int j = 0; j < n; ++j) {
+        w[j] = d[idx[j]];
+        for (int k = 0; k < n; ++k) Vs[(size_t)k * n + j] = V[(size_t)k * n + idx[j]];
+    }
+    V.swap(Vs);
+}
+
+}  // namespace
+
+struct Davidson {
+    adc_handle* h;
+    long long dim;
+    int nroots, maxspace;
+    double* V;   // [cap][dim] S-orthonormal basis
+    double* SV;  // S V
+    double* W;   // sigma(V)
+    int k = 0;
+    long long nsig = 0;
+    double sigma_seconds = 0.0;
+
+    void metric(const double* in, double* out, long long nvec, int inverse) {
+        k_metric<<<grid_for(nvec * dim), 256, 0, h->ctx.stream>>>(h->kind == ADC_EA, h->o, h->v, nvec, in, out, inverse);
+        launch_check(h->ctx);
+    }
+    void sigma(int first, int count) {
+        auto t0 = std::chrono::steady_clock::now();
+        sigma_device(h, V + (long long)first * dim, W + (long long)first * dim, count);
+        ADC_CUDA(cudaStreamSynchronize(h->ctx.stream));
+        sigma_seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        nsig += count;
+    }
+    // S-orthonormalise rows [first, first+count) of V against rows [0, first) and each other; returns kept count
+    int orthonormalise(int first, int count) {
+        Ctx& c = h->ctx;
+        int kept = 0;
+        std::vector<double> coef(first + count);
+        double* cd = c.arena.dalloc(first + count);
+        for (int r = 0; r < count; ++r) {
+            double* x = V + (long long)(first + r) * dim;
+            double* dst = V + (long long)(first + kept) * dim;
+            if (dst != x) ADC_CUDA(cudaMemcpyAsync(dst, x, dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+            int nb = first + kept;
+            for (int pass = 0; pass < 2 && nb > 0; ++pass) {
+                // coef = SV[0:nb] . dst ; dst -= coef^T V[0:nb]
+                gemm(c, false, true, 1, nb, dim, 1.0, dst, dim, 0, SV, dim, 0, 0.0, cd, nb, 0, 1);
+                gemm(c, false, false, 1, dim, nb, -1.0, cd, nb, 0, V, dim, 0, 1.0, dst, dim, 0, 1);
+            }
+            double* sdst = SV + (long long)(first + kept) * dim;
+            metric(dst, sdst, 1, 0);
+            gemm(c, false, true, 1, 1, dim, 1.0, dst, dim, 0, sdst, dim, 0, 0.0, cd, 1, 0, 1);
+            double nrm2 = 0.0;
+            ADC_CUDA(cudaMemcpyAsync(&nrm2, cd, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+            ADC_CUDA(cudaStreamSynchronize(c.stream));
+            if (!(nrm2 > 1e-20)) continue;
+            double s = 1.0 / std::sqrt(nrm2);
+            axpby(c, dim, 0.0, dst, s, dst);
+            axpby(c, dim, 0.0, sdst, s, sdst);
+            ++kept;
+        }
+        return kept;
+    }
+};
+
+static int davidson(adc_handle* h, int nroots, double tol, const double* guess, double* energies, double* specfac,
+                    double* vectors, double* stats) {
+    Ctx& c = h->ctx;
+    auto t0 = std::chrono::steady_clock::now();
+    const long long dim = h->dim();
+    const int nextra = std::max(0, h->opt.nguess_extra);
+    const int nstart = (int)std::min<long long>(dim, guess ? nroots : nroots + nextra);
+    const int maxspace = std::max(h->opt.max_space_per_root * nroots, nstart + nroots);
+    const int cap = maxspace + nroots;
+    const double rtol = h->opt.res_tol > 0 ? h->opt.res_tol : std::sqrt(tol);
+    Scope sc(c.arena);
+    Davidson d{h, dim, nroots, maxspace, nullptr, nullptr, nullptr};
+    d.V = c.arena.dalloc((size_t)cap * dim);
+    d.SV = c.arena.dalloc((size_t)cap * dim);
+    d.W = c.arena.dalloc((size_t)cap * dim);
+    double* X = c.arena.dalloc((size_t)nroots * dim);
+    double* AX = c.arena.dalloc((size_t)nroots * dim);
+    double* R = c.arena.dalloc((size_t)nroots * dim);
+    double* SR = c.arena.dalloc((size_t)nroots * dim);
+    double* Cd = c.arena.dalloc((size_t)cap * nroots);
+    double* Gd = c.arena.dalloc((size_t)cap * cap);
+    double* wd = c.arena.dalloc(nroots);
+    // guesses
+    if (guess) {
+        ADC_CUDA(cudaMemcpyAsync(d.V, guess, (size_t)nroots * dim * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    } else {
+        std::vector<double> D(dim);
+        ADC_CUDA(cudaMemcpyAsync(D.data(), h->diag, dim * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        ADC_CUDA(cudaStreamSynchronize(c.stream));
+        std::vector<long long> idx(dim);
+        std::iota(idx.begin(), idx.end(), 0LL);
+        std::partial_sort(idx.begin(), idx.begin() + nstart, idx.end(), [&](long long a, long long b) {
+            return D[a] < D[b] || (D[a] == D[b] && a < b);
+        });
+        fill(c, (long long)nstart * dim, 0.0, d.V);
+        long long* di = (long long*)c.arena.alloc(nstart * sizeof(long long));
+        ADC_CUDA(cudaMemcpyAsync(di, idx.data(), nstart * sizeof(long long), cudaMemcpyHostToDevice, c.stream));
+        k_units<<<1, std::max(32, nstart), 0, c.stream>>>(nstart, di, dim, d.V);
+        launch_check(c);
+    }
+    d.k = d.orthonormalise(0, nstart);
+    if (d.k < nroots) throw Error(ADC_ERR_ARG, "davidson: guess space too small");
+    d.sigma(0, d.k);
+    std::vector<double> wold(nroots, INFINITY), w, C, G, rn(nroots);
+    int it = 0, status = ADC_ERR_NOT_CONVERGED;
+    int maxit = std::max(1, h->opt.max_iter);
+    for (it = 1; it <= maxit; ++it) {
+        int k = d.k;
+        // G = V S W^T = SV W^T (symmetric)
+        gemm(c, false, true, k, k, dim, 1.0, d.SV, dim, 0, d.W, dim, 0, 0.0, Gd, k, 0, 1);
+        G.resize((size_t)k * k);
+        ADC_CUDA(cudaMemcpyAsync(G.data(), Gd, (size_t)k * k * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        ADC_CUDA(cudaStreamSynchronize(c.stream));
+        for (int i = 0; i < k; ++i)
+            for (int j = 0; j < i; ++j) G[(size_t)i * k + j] = G[(size_t)j * k + i] = 0.5 * (G[(size_t)i * k + j] + G[(size_t)j * k + i]);
+        jacobi_eigh(k, G, w, C);
+        // Ct[r][i] = C[i][r] for the lowest nroots
+        std::vector<double> Ct((size_t)nroots * k);
+        for (int r = 0; r < nroots; ++r)
+            for (int i = 0; i < k; ++i) Ct[(size_t)r * k + i] = C[(size_t)i * k + r];
+        ADC_CUDA(cudaMemcpyAsync(Cd, Ct.data(), Ct.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+        gemm(c, false, false, nroots, dim, k, 1.0, Cd, k, 0, d.V, dim, 0, 0.0, X, dim, 0, 1);
+        gemm(c, false, false, nroots, dim, k, 1.0, Cd, k, 0, d.W, dim, 0, 0.0, AX, dim, 0, 1);
+        // R = AX - w X
+        ADC_CUDA(cudaMemcpyAsync(R, AX, (size_t)nroots * dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+        for (int r = 0; r < nroots; ++r) axpby(c, dim, -w[r], X + (long long)r * dim, 1.0, R + (long long)r * dim);
+        d.metric(R, SR, nroots, 0);
+        std::vector<double> rr(nroots);
+        for (int r = 0; r < nroots; ++r)
+            gemm(c, false, true, 1, 1, dim, 1.0, R + (long long)r * dim, dim, 0, SR + (long long)r * dim, dim, 0, 0.0, Cd + r, 1, 0, 1);
+        ADC_CUDA(cudaMemcpyAsync(rr.data(), Cd, nroots * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        ADC_CUDA(cudaStreamSynchronize(c.stream));
+        bool all = true;
+        std::vector<int> todo;
+        for (int r = 0; r < nroots; ++r) {
+            rn[r] = std::sqrt(std::max(rr[r], 0.0));
+            bool cv = std::fabs(w[r] - wold[r]) <= tol && rn[r] <= rtol;
+            if (!std::isfinite(w[r]) || !std::isfinite(rn[r])) throw Error(ADC_ERR_CUDA, "davidson: non-finite residual");
+            if (!cv) {
+                all = false;
+                todo.push_back(r);
+            }
+            wold[r] = w[r];
+        }
+        if (all) {
+            status = ADC_OK;
+            break;
+        }
+        int nnew = (int)todo.size();
+        if (d.k + nnew > maxspace) {
+            // collapse onto the current Ritz vectors (sigma of them is AX)
+            ADC_CUDA(cudaMemcpyAsync(d.V, X, (size_t)nroots * dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+            ADC_CUDA(cudaMemcpyAsync(d.W, AX, (size_t)nroots * dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+            d.metric(d.V, d.SV, nroots, 0);
+            d.k = nroots;
+        }
+        // corrections for unconverged roots
+        std::vector<double> wt(nnew);
+        for (int j = 0; j < nnew; ++j) {
+            wt[j] = w[todo[j]];
+            ADC_CUDA(cudaMemcpyAsync(SR + (long long)j * dim, R + (long long)todo[j] * dim, dim * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, c.stream));
+        }
+        ADC_CUDA(cudaMemcpyAsync(wd, wt.data(), nnew * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+        k_precond<<<grid_for((long long)nnew * dim), 256, 0, c.stream>>>(nnew, dim, SR, wd, h->diag, d.V + (long long)d.k * dim);
+        launch_check(c);
+        int kept = d.orthonormalise(d.k, nnew);
+        if (kept == 0) {
+            status = ADC_OK;
+            break;
+        }
+        d.sigma(d.k, kept);
+        d.k += kept;
+    }
+    // outputs
+    for (int r = 0; r < nroots; ++r) energies[r] = w[r];
+    if (vectors) ADC_CUDA(cudaMemcpyAsync(vectors, X, (size_t)nroots * dim * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    if (specfac) {
+        // X_p = sum_nu T_{p,nu} (S Y~)_nu, P = 2 sum_p X_p^2  (Appendix); Ritz vectors are S-normalised
+        const long long o = h->o, v = h->v, nmo = o + v;
+        double* SX = SR;
+        d.metric(X, SX, nroots, 0);
+        double* Xp = c.arena.dalloc((size_t)nroots * nmo);
+        fill(c, (long long)nroots * nmo, 0.0, Xp);
+        double* Tpp = c.arena.dalloc((size_t)std::max(o, v) * std::max(o, v));
+        double* s1 = c.arena.dalloc((size_t)nroots * std::max(o, v));
+        double* s2 = c.arena.dalloc((size_t)nroots * (h->kind == ADC_EA ? o * v * v : o * o * v));
+        long long n1 = h->n1(), blk = dim - n1;
+        k_gather<<<grid_for(nroots * n1), 256, 0, c.stream>>>(nroots, n1, SX, dim, 0, s1, n1, 0, 0.0);
+        launch_check(c);
+        k_gather<<<grid_for(nroots * blk), 256, 0, c.stream>>>(nroots, blk, SX, dim, n1, s2, blk, 0, 0.0);
+        launch_check(c);
+        const double* t = h->t;
+        double* t1 = h->t1_2;
+        double* t1tmp = nullptr;
+        if (!t1) {
+            // second-order singles are part of T(2) also for ADC(2)
+            t1tmp = c.arena.dalloc(o * v);
+            double* Gq = c.arena.dalloc(h->naux * o * v);
+            einsum(c, "Qkc,ikdc->Qid", 1.0, tn(h->Bov, {h->naux, o, v}), tn(h->tau, {o, o, v, v}), 0.0, Gq, {h->naux, o, v});
+            einsum(c, "Qid,Qad->ia", 1.0, tn(Gq, {h->naux, o, v}), tn(h->Bvv, {h->naux, v, v}), 0.0, t1tmp, {o, v});
+            einsum(c, "kilc,klac->ia", -1.0, tn(h->ooov, {o, o, o, v}), tn(h->tau, {o, o, v, v}), 1.0, t1tmp, {o, v});
+            k_div_D1<<<grid_for(o * v), 256, 0, c.stream>>>((int)o, (int)v, h->eps, t1tmp);
+            launch_check(c);
+            t1 = t1tmp;
+        }
+        // X rows laid out [r][p] with p over all nmo orbitals (occupied first)
+        if (h->kind == ADC_EA) {
+            // T_{c,b} = d_cb - sum t_kl^cd t_kl^bd + 1/2 sum t_kl^cd t_kl^db
+            einsum(c, "klcd,klbd->cb", -1.0, tn(t, {o, o, v, v}), tn(t, {o, o, v, v}), 0.0, Tpp, {v, v});
+            einsum(c, "klcd,kldb->cb", 0.5, tn(t, {o, o, v, v}), tn(t, {o, o, v, v}), 1.0, Tpp, {v, v});
+            double* xv = c.arena.dalloc((size_t)nroots * v);
+            ADC_CUDA(cudaMemcpyAsync(xv, s1, (size_t)nroots * v * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+            einsum(c, "rb,cb->rc", 1.0, tn(s1, {nroots, v}), tn(Tpp, {v, v}), 1.0, xv, {nroots, v});
+            k_gather<<<grid_for(nroots * v), 256, 0, c.stream>>>(nroots, v, xv, v, 0, Xp, nmo, o, 0.0);
+            launch_check(c);
+            // occupied: T_{k,b} = -t_k^b(2) ; T_{k,jcd} = -t_kj^dc
+            double* xo = c.arena.dalloc((size_t)nroots * o);
+            einsum(c, "rb,kb->rk", -1.0, tn(s1, {nroots, v}), tn(t1, {o, v}), 0.0, xo, {nroots, o});
+            einsum(c, "rjcd,kjdc->rk", -1.0, tn(s2, {nroots, o, v, v}), tn(t, {o, o, v, v}), 1.0, xo, {nroots, o});
+            k_gather<<<grid_for(nroots * o), 256, 0, c.stream>>>(nroots, o, xo, o, 0, Xp, nmo, 0, 0.0);
+            launch_check(c);
+        } else {
+            // T_{k,j} = d_kj - sum t_kl^cd t_jl^cd + 1/2 sum t_kl^cd t_jl^dc
+            einsum(c, "klcd,jlcd->kj", -1.0, tn(t, {o, o, v, v}), tn(t, {o, o, v, v}), 0.0, Tpp, {o, o});
+            einsum(c, "klcd,jldc->kj", 0.5, tn(t, {o, o, v, v}), tn(t, {o, o, v, v}), 1.0, Tpp, {o, o});
+            double* xo = c.arena.dalloc((size_t)nroots * o);
+            ADC_CUDA(cudaMemcpyAsync(xo, s1, (size_t)nroots * o * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+            einsum(c, "rj,kj->rk", 1.0, tn(s1, {nroots, o}), tn(Tpp, {o, o}), 1.0, xo, {nroots, o});
+            k_gather<<<grid_for(nroots * o), 256, 0, c.stream>>>(nroots, o, xo, o, 0, Xp, nmo, 0, 0.0);
+            launch_check(c);
+            // virtual: T_{c,j} = t_j^c(2) ; T_{c,ija} = -t_ij^ac
+            double* xv = c.arena.dalloc((size_t)nroots * v);
+            einsum(c, "rj,jc->rc", 1.0, tn(s1, {nroots, o}), tn(t1, {o, v}), 0.0, xv, {nroots, v});
+            einsum(c, "rija,ijac->rc", -1.0, tn(s2, {nroots, o, o, v}), tn(t, {o, o, v, v}), 1.0, xv, {nroots, v});
+            k_gather<<<grid_for(nroots * v), 256, 0, c.stream>>>(nroots, v, xv, v, 0, Xp, nmo, o, 0.0);
+            launch_check(c);
+        }
+        std::vector<double> xh((size_t)nroots * nmo);
+        ADC_CUDA(cudaMemcpyAsync(xh.data(), Xp, xh.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        ADC_CUDA(cudaStreamSynchronize(c.stream));
+        for (int r = 0; r < nroots; ++r) {
+            double s = 0.0;
+            for (long long p = 0; p < nmo; ++p) s += xh[(size_t)r * nmo + p] * xh[(size_t)r * nmo + p];
+            specfac[r] = 2.0 * s;
+        }
+    }
+    ADC_CUDA(cudaStreamSynchronize(c.stream));
+    if (stats) {
+        double mr = 0.0;
+        for (double x : rn) mr = std::max(mr, x);
+        stats[0] = std::min(it, maxit);
+        stats[1] = (double)d.nsig;
+        stats[2] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        stats[3] = mr;
+        stats[4] = d.sigma_seconds;
+        stats[5] = stats[6] = stats[7] = 0.0;
+    }
+    return status;
+}
+
+// --------------------------------------------------------------------------
+// C ABI
+// --------------------------------------------------------------------------
+#define GUARD(h, ...)                                    \
+    try {                                                \
+        __VA_ARGS__                                      \
+    } catch (const adc::Error& e) {                      \
+        if (h) h->err = e.what();                        \
+        return e.code;                                   \
+    } catch (const std::exception& e) {                  \
+        if (h) h->err = e.what();                        \
+        return ADC_ERR_CUDA;                             \
+    }
+
+extern "C" {
+
+int adc_default_options(adc_options* opt) {
+    if (!opt) return ADC_ERR_ARG;
+    opt->precision = ADC_PREC_FP64;
+    opt->max_space_per_root = 8;
+    opt->max_iter = 100;
+    opt->nguess_extra = 2;
+    opt->res_tol = 0.0;
+    opt->aux_chunk = 0;
+    return ADC_OK;
+}
+
+int adc_setup(const double* eps, const double* Bq, int nocc, int nvir, int naux, int order, int kind,
+              const adc_options* opt, int on_device, adc_handle** out) {
+    if (!out) return ADC_ERR_ARG;
+    *out = nullptr;
+    if (!eps || !Bq || nocc < 1 || nvir < 1 || naux < 1 || (order != 2 && order != 3) || (kind != ADC_EA && kind != ADC_IP)) {
+        g_setup_error = "adc_setup: invalid argument";
+        return ADC_ERR_ARG;
+    }
+    if (opt && (opt->precision != ADC_PREC_FP64 && opt->precision != ADC_PREC_BF16X3)) {
+        g_setup_error = "adc_setup: unknown precision";
+        return ADC_ERR_ARG;
+    }
+    adc_handle* h = new adc_handle();
+    h->o = nocc;
+    h->v = nvir;
+    h->naux = naux;
+    h->order = order;
+    h->kind = kind;
+    adc_default_options(&h->opt);
+    if (opt) h->opt = *opt;
+    try {
+        setup(h, eps, Bq, on_device);
+    } catch (const adc::Error& e) {
+        g_setup_error = e.what();
+        int code = e.code;
+        delete h;
+        return code;
+    } catch (const std::exception& e) {
+        g_setup_error = e.what();
+        delete h;
+        return ADC_ERR_CUDA;
+    }
+    *out = h;
+    return ADC_OK;
+}
+
+int adc_dim(const adc_handle* h, long long* dim) {
+    if (!h || !dim) return ADC_ERR_ARG;
+    *dim = h->dim();
+    return ADC_OK;
+}
+
+int adc_set_stream(adc_handle* h, void* stream) {
+    if (!h) return ADC_ERR_ARG;
+    GUARD(h, {
+        h->ctx.stream = (cudaStream_t)stream;
+        ADC_BLAS(cublasSetStream(h->ctx.blas, h->ctx.stream));
+        return ADC_OK;
+    })
+}
+
+int adc_sigma(adc_handle* h, const double* X, double* S, int nvec, int on_device) {
+    if (!h) return ADC_ERR_ARG;
+    if (!X || !S || nvec < 1) {
+        h->err = "adc_sigma: invalid argument";
+        return ADC_ERR_ARG;
+    }
+    GUARD(h, {
+        Ctx& c = h->ctx;
+        const long long dim = h->dim();
+        if (on_device) {
+            sigma_device(h, X, S, nvec);
+        } else {
+            Scope sc(c.arena);
+            double* dX = c.arena.dalloc((size_t)nvec * dim);
+            double* dS = c.arena.dalloc((size_t)nvec * dim);
+            ADC_CUDA(cudaMemcpyAsync(dX, X, (size_t)nvec * dim * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+            sigma_device(h, dX, dS, nvec);
+            ADC_CUDA(cudaMemcpyAsync(S, dS, (size_t)nvec * dim * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        }
+        ADC_CUDA(cudaStreamSynchronize(c.stream));
+        return ADC_OK;
+    })
+}
+
+int adc_davidson(adc_handle* h, int nroots, double tol, const double* guess, double* energies, double* specfac,
+                 double* vectors, double* stats) {
+    if (!h) return ADC_ERR_ARG;
+    if (nroots < 1 || !energies || !(tol > 0) || nroots > h->dim()) {
+        h->err = "adc_davidson: invalid argument";
+        return ADC_ERR_ARG;
+    }
+    GUARD(h, {
+        int st = davidson(h, nroots, tol, guess, energies, specfac, vectors, stats);
+        if (st == ADC_ERR_NOT_CONVERGED) h->err = "adc_davidson: not converged within max_iter";
+        return st;
+    })
+}
+
+int adc_get_tensor(adc_handle* h, const char* name, double* out, long long n) {
+    if (!h || !name || !out) return ADC_ERR_ARG;
+    GUARD(h, {
+        const long long o = h->o, v = h->v;
+        const double* src = nullptr;
+        long long cnt = 0;
+        std::string s(name);
+        if (s == "M11") {
+            src = h->M11;
+            cnt = (long long)h->n1() * h->n1();
+        } else if (s == "t2") {
+            src = h->t;
+            cnt = o * o * v * v;
+        } else if (s == "t2_2") {
+            src = h->t_2;
+            cnt = o * o * v * v;
+        } else if (s == "t1_2") {
+            src = h->t1_2;
+            cnt = o * v;
+        } else if (s == "diag") {
+            src = h->diag;
+            cnt = h->dim();
+        }
+        if (!src) {
+            h->err = "adc_get_tensor: unknown or unavailable tensor " + s;
+            return ADC_ERR_ARG;
+        }
+        if (n < cnt) {
+            h->err = "adc_get_tensor: buffer too small";
+            return ADC_ERR_ARG;
+        }
+        ADC_CUDA(cudaMemcpyAsync(out, src, cnt * sizeof(double), cudaMemcpyDeviceToHost, h->ctx.stream));
+        ADC_CUDA(cudaStreamSynchronize(h->ctx.stream));
+        return ADC_OK;
+    })
+}
+
+const char* adc_last_error(const adc_handle* h) { return h ? h->err.c_str() : g_setup_error.c_str(); }
+
+void adc_destroy(adc_handle* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->ctx.stream);
+    delete h;
+}
+
+}  // extern "C"

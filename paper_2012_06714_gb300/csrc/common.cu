@@ -1,0 +1,208 @@
+// Elementwise kernels and the tensor-contraction executor used by setup and
+// the FP64 sigma path.
+#include <algorithm>
+#include <cstring>
+#include <map>
+
+#include "common.cuh"
+
+namespace adc {
+
+namespace {
+
+struct PermArgs {
+    int nd;
+    long long dout[kMaxDim];
+    long long sin[kMaxDim];  // input stride for each output axis
+};
+
+__global__ void permute_kernel(const double* __restrict__ in, double* __restrict__ out, PermArgs a, long long total,
+                               double alpha, double beta) {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        long long r = idx, off = 0;
+        for (int j = a.nd - 1; j >= 0; --j) {
+            long long cj = r % a.dout[j];
+            r /= a.dout[j];
+            off += cj * a.sin[j];
+        }
+        double v = alpha * in[off];
+        out[idx] = (beta == 0.0) ? v : v + beta * out[idx];
+    }
+}
+
+__global__ void axpby_kernel(long long n, double alpha, const double* __restrict__ x, double beta, double* __restrict__ y) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = (beta == 0.0) ? alpha * x[i] : alpha * x[i] + beta * y[i];
+}
+
+__global__ void fill_kernel(long long n, double v, double* __restrict__ y) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = v;
+}
+
+inline int grid_for(long long n) {
+    long long g = (n + 255) / 256;
+    return (int)std::min<long long>(std::max<long long>(g, 1), 152LL * 32);
+}
+
+}  // namespace
+
+void permute(Ctx& c, const double* in, const Shape& s, const int* perm, double* out, double alpha, double beta) {
+    PermArgs a;
+    a.nd = s.nd;
+    long long st[kMaxDim];
+    long long acc = 1, total = 1;
+    for (int j = s.nd - 1; j >= 0; --j) {
+        st[j] = acc;
+        acc *= s.d[j];
+    }
+    for (int j = 0; j < s.nd; ++j) {
+        a.dout[j] = s.d[perm[j]];
+        a.sin[j] = st[perm[j]];
+        total *= a.dout[j];
+    }
+    if (total == 0) return;
+    permute_kernel<<<grid_for(total), 256, 0, c.stream>>>(in, out, a, total, alpha, beta);
+    ++c.kernels;
+    ADC_CUDA(cudaGetLastError());
+}
+
+void axpby(Ctx& c, long long n, double alpha, const double* x, double beta, double* y) {
+    if (n <= 0) return;
+    axpby_kernel<<<grid_for(n), 256, 0, c.stream>>>(n, alpha, x, beta, y);
+    ++c.kernels;
+    ADC_CUDA(cudaGetLastError());
+}
+
+void fill(Ctx& c, long long n, double v, double* y) {
+    if (n <= 0) return;
+    fill_kernel<<<grid_for(n), 256, 0, c.stream>>>(n, v, y);
+    ++c.kernels;
+    ADC_CUDA(cudaGetLastError());
+}
+
+void gemm(Ctx& c, bool ta, bool tb, long long M, long long N, long long K, double alpha, const double* A, long long lda,
+          long long sA, const double* B, long long ldb, long long sB, double beta, double* C, long long ldc,
+          long long sC, long long batch) {
+    if (M <= 0 || N <= 0 || batch <= 0) return;
+    if (K <= 0) {
+        // C = beta C
+        if (ldc == N && (batch == 1 || sC == M * N)) {
+            if (beta == 0.0)
+                fill(c, M * N * batch, 0.0, C);
+            else if (beta != 1.0)
+                axpby(c, M * N * batch, 0.0, C, beta, C);
+            return;
+        }
+        throw Error(-1, "gemm: K == 0 with strided C");
+    }
+    // row-major C = op(A) op(B)  <=>  column-major C^T = op(B)^T op(A)^T
+    cublasOperation_t oa = ta ? CUBLAS_OP_T : CUBLAS_OP_N;
+    cublasOperation_t ob = tb ? CUBLAS_OP_T : CUBLAS_OP_N;
+    if (batch == 1) {
+        ADC_BLAS(cublasDgemm(c.blas, ob, oa, (int)N, (int)M, (int)K, &alpha, B, (int)ldb, A, (int)lda, &beta, C, (int)ldc));
+    } else {
+        ADC_BLAS(cublasDgemmStridedBatched(c.blas, ob, oa, (int)N, (int)M, (int)K, &alpha, B, (int)ldb, sB, A, (int)lda,
+                                           sA, &beta, C, (int)ldc, sC, (int)batch));
+    }
+}
+
+namespace {
+
+struct Spec {
+    std::string a, b, c;
+};
+
+Spec parse(const char* spec) {
+    std::string s(spec);
+    size_t comma = s.find(','), arrow = s.find("->");
+    if (comma == std::string::npos || arrow == std::string::npos || comma > arrow)
+        throw Error(-1, std::string("einsum: bad spec ") + spec);
+    return {s.substr(0, comma), s.substr(comma + 1, arrow - comma - 1), s.substr(arrow + 2)};
+}
+
+bool has(const std::string& s, char x) { return s.find(x) != std::string::npos; }
+
+// permute src (letters ls, dims) into the letter order lt; returns pointer (src if identity)
+const double* to_order(Ctx& c, const double* src, const std::string& ls, const std::map<char, long long>& dim,
+                       const std::string& lt) {
+    if (ls == lt) return src;
+    Shape sh;
+    sh.nd = (int)ls.size();
+    long long n = 1;
+    for (int j = 0; j < sh.nd; ++j) {
+        sh.d[j] = dim.at(ls[j]);
+        n *= sh.d[j];
+    }
+    int perm[kMaxDim];
+    for (int j = 0; j < sh.nd; ++j) perm[j] = (int)ls.find(lt[j]);
+    double* dst = c.arena.dalloc(n);
+    permute(c, src, sh, perm, dst, 1.0, 0.0);
+    return dst;
+}
+
+}  // namespace
+
+void einsum(Ctx& c, const char* specstr, double alpha, const T& A, const T& B, double beta, double* C,
+            const std::vector<long long>& cdims) {
+    Spec sp = parse(specstr);
+    if (sp.a.size() != A.dims.size() || sp.b.size() != B.dims.size() || sp.c.size() != cdims.size())
+        throw Error(-1, std::string("einsum: rank mismatch in ") + specstr);
+    std::map<char, long long> dim;
+    auto put = [&](const std::string& l, const std::vector<long long>& d) {
+        for (size_t j = 0; j < l.size(); ++j) {
+            auto it = dim.find(l[j]);
+            if (it != dim.end() && it->second != d[j])
+                throw Error(-1, std::string("einsum: dimension mismatch in ") + specstr);
+            dim[l[j]] = d[j];
+        }
+    };
+    put(sp.a, A.dims);
+    put(sp.b, B.dims);
+    put(sp.c, cdims);
+    std::string batch, fa, fb, con;
+    for (char x : sp.c) {
+        bool ia = has(sp.a, x), ib = has(sp.b, x);
+        if (ia && ib)
+            batch += x;
+        else if (ia)
+            fa += x;
+        else if (ib)
+            fb += x;
+        else
+            throw Error(-1, std::string("einsum: output index not in inputs: ") + specstr);
+    }
+    for (char x : sp.a) {
+        if (has(sp.c, x)) continue;
+        if (!has(sp.b, x)) throw Error(-1, std::string("einsum: summed index in one operand only: ") + specstr);
+        con += x;
+    }
+    for (char x : sp.b)
+        if (!has(sp.c, x) && !has(sp.a, x)) throw Error(-1, std::string("einsum: summed index in one operand only: ") + specstr);
+    auto prod = [&](const std::string& l) {
+        long long p = 1;
+        for (char x : l) p *= dim[x];
+        return p;
+    };
+    long long nb = prod(batch), M = prod(fa), N = prod(fb), K = prod(con);
+    Arena::Mark mk = c.arena.mark();
+    const double* Ap = to_order(c, A.p, sp.a, dim, batch + fa + con);
+    const double* Bp = to_order(c, B.p, sp.b, dim, batch + con + fb);
+    std::string tord = batch + fa + fb;
+    if (tord == sp.c) {
+        gemm(c, false, false, M, N, K, alpha, Ap, K, M * K, Bp, N, K * N, beta, C, N, M * N, nb);
+    } else {
+        double* Tm = c.arena.dalloc((size_t)(nb * M * N));
+        gemm(c, false, false, M, N, K, 1.0, Ap, K, M * K, Bp, N, K * N, 0.0, Tm, N, M * N, nb);
+        Shape sh;
+        sh.nd = (int)tord.size();
+        for (int j = 0; j < sh.nd; ++j) sh.d[j] = dim[tord[j]];
+        int perm[kMaxDim];
+        for (int j = 0; j < sh.nd; ++j) perm[j] = (int)tord.find(sp.c[j]);
+        permute(c, Tm, sh, perm, C, alpha, beta);
+    }
+    c.arena.release(mk);
+}
+
+}  // namespace adc

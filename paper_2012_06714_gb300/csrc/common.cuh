@@ -1,0 +1,127 @@
+// Shared device helpers of the ADC library: error handling, a device scratch
+// arena, an N-d permute kernel and a two-operand tensor contraction executor
+// (permute to GEMM form + cuBLAS strided-batched DGEMM + permute back).
+#pragma once
+
+#include <cublas_v2.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+namespace adc {
+
+struct Error : std::runtime_error {
+    int code;
+    Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define ADC_CUDA(x)                                                                                   \
+    do {                                                                                              \
+        cudaError_t e_ = (x);                                                                         \
+        if (e_ != cudaSuccess)                                                                        \
+            throw ::adc::Error(e_ == cudaErrorMemoryAllocation ? -2 : -3,                             \
+                               std::string(#x) + ": " + cudaGetErrorString(e_));                      \
+    } while (0)
+
+#define ADC_BLAS(x)                                                                                   \
+    do {                                                                                              \
+        cublasStatus_t s_ = (x);                                                                      \
+        if (s_ != CUBLAS_STATUS_SUCCESS)                                                              \
+            throw ::adc::Error(s_ == CUBLAS_STATUS_ALLOC_FAILED ? -2 : -3,                            \
+                               std::string(#x) + ": cublas status " + std::to_string((int)s_));       \
+    } while (0)
+
+// Device scratch: blocks are allocated on demand and kept; mark()/release()
+// give stack semantics so that repeated calls reuse the same memory.
+class Arena {
+   public:
+    ~Arena() { free_all(); }
+    struct Mark {
+        size_t block, top;
+    };
+    Mark mark() const { return {cur_, blocks_.empty() ? 0 : tops_[cur_]}; }
+    void release(Mark m) {
+        for (size_t b = m.block + 1; b < tops_.size(); ++b) tops_[b] = 0;
+        cur_ = m.block;
+        if (!tops_.empty()) tops_[cur_] = m.top;
+    }
+    void* alloc(size_t bytes) {
+        bytes = (bytes + 255) & ~size_t(255);
+        if (bytes == 0) bytes = 256;
+        while (cur_ < blocks_.size()) {
+            if (tops_[cur_] + bytes <= caps_[cur_]) {
+                void* p = (char*)blocks_[cur_] + tops_[cur_];
+                tops_[cur_] += bytes;
+                return p;
+            }
+            if (cur_ + 1 < blocks_.size()) {
+                ++cur_;
+                tops_[cur_] = 0;
+            } else
+                break;
+        }
+        size_t cap = bytes > (size_t(256) << 20) ? bytes : (size_t(256) << 20);
+        void* p = nullptr;
+        ADC_CUDA(cudaMalloc(&p, cap));
+        blocks_.push_back(p);
+        caps_.push_back(cap);
+        tops_.push_back(bytes);
+        cur_ = blocks_.size() - 1;
+        return p;
+    }
+    double* dalloc(size_t n) { return (double*)alloc(n * sizeof(double)); }
+    void free_all() {
+        for (void* p : blocks_) cudaFree(p);
+        blocks_.clear();
+        caps_.clear();
+        tops_.clear();
+        cur_ = 0;
+    }
+    size_t capacity() const {
+        size_t s = 0;
+        for (size_t c : caps_) s += c;
+        return s;
+    }
+
+   private:
+    std::vector<void*> blocks_;
+    std::vector<size_t> caps_, tops_;
+    size_t cur_ = 0;
+};
+
+struct Ctx {
+    cudaStream_t stream = 0;
+    cublasHandle_t blas = nullptr;
+    Arena arena;
+    long long kernels = 0;  // own kernel launches issued (for reporting)
+};
+
+constexpr int kMaxDim = 8;
+struct Shape {
+    int nd;
+    long long d[kMaxDim];
+};
+
+// ---- elementwise kernels --------------------------------------------------
+void permute(Ctx& c, const double* in, const Shape& in_shape, const int* perm, double* out, double alpha, double beta);
+void axpby(Ctx& c, long long n, double alpha, const double* x, double beta, double* y);  // y = a x + b y
+void fill(Ctx& c, long long n, double v, double* y);
+
+// ---- contraction executor -------------------------------------------------
+struct T {
+    const double* p;
+    std::vector<long long> dims;
+};
+// C[lc] = beta * C + alpha * sum A[la] B[lb] ; spec "la,lb->lc" with single-letter indices.
+void einsum(Ctx& c, const char* spec, double alpha, const T& A, const T& B, double beta, double* C,
+            const std::vector<long long>& cdims);
+
+// Row-major GEMM: C[MxN] = alpha op(A) op(B) + beta C, batched with strides.
+void gemm(Ctx& c, bool ta, bool tb, long long M, long long N, long long K, double alpha, const double* A, long long lda,
+          long long sA, const double* B, long long ldb, long long sB, double beta, double* C, long long ldc,
+          long long sC, long long batch);
+
+}  // namespace adc
