@@ -1,0 +1,294 @@
+#!/usr/bin/env python
+"""Benchmark of the EA-ADC(3) Davidson sigma build sigma = M X on one GB300.
+
+Workload (synthetic, the paper's molecules are not available): closed-shell
+EA-ADC(3), nocc=40, nvir=400, naux=1400, mixed precision (tensor-core BF16x3
+DF ladder), a block of 4 trial vectors per step.  Metric: sigma-build TFLOP/s
+counting the algorithmic DF-ladder work 4 naux nocc nvir^3 per trial vector
+(the dominant term; the ring and coupling terms are not counted).  Inputs are
+larger than L2 (B^Q alone is > 2 GB).  Also reported: end-to-end through the C
+ABI with host buffers, the roofline of the tensor-core kernel timed live with
+CUDA events, SM clocks sampled during the timed region, the CPU oracle on a
+bounded sample, and the time to 4 roots with the Davidson solver.
+
+--impl reference times the CPU oracle (the reference arm of this tier).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(nocc=40, nvir=400, naux=1400, order=3, kind="ea", nvec=4, nroots=4)
+METRIC = "EA-ADC(3) sigma-build TFLOP/s (DF ladder 4*naux*nocc*nvir^3 per trial vector)"
+
+
+def ladder_flops(o, v, naux, nvec):
+    return 4.0 * naux * o * v ** 3 * nvec
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("bf16_tflops", 1900.0), d.get("hbm_gbs", 6800.0), "measured"
+    return 1900.0, 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.gpu = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, x in zip(names, r[5:9]):
+                if x.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(sample_seconds=12.0):
+    """The oracle's DF ladder (numpy) on a bounded sample of the same workload."""
+    from adc_inputs import make_system
+    from oracle.spinadapted import df_ladder
+
+    w = WORKLOAD
+    o, v, naux = w["nocc"], w["nvir"], w["naux"]
+    rng = np.random.default_rng(0)
+    # B^Q_vv of the same distribution (the ladder reads only this block)
+    s = 0.3 / np.sqrt(naux)
+    Bvv = np.empty((naux, v, v))
+    for q in range(naux):
+        g = rng.standard_normal((v, v))
+        Bvv[q] = 0.5 * s * (g + g.T)
+    X = rng.standard_normal((1, v, v))
+    t0 = time.perf_counter()
+    df_ladder(Bvv, X)
+    t1 = time.perf_counter() - t0
+    nmat = max(1, int(sample_seconds / max(t1, 1e-3)))
+    X = rng.standard_normal((nmat, v, v))
+    t0 = time.perf_counter()
+    for k in range(nmat):
+        df_ladder(Bvv, X[k:k + 1])
+    dt = time.perf_counter() - t0
+    flops = 4.0 * naux * v ** 3 * nmat
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle DF ladder sum_Q B^Q Y_i B^Q for {nmat} of the {w['nvec'] * o} (vector, i) matrices "
+                      f"(nvir={v}, naux={naux}); {dt:.1f} s", "seconds": dt}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = WORKLOAD
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(sample_seconds=2.0)
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(sample_seconds=8.0))
+    v = float(np.mean([x["value"] for x in vals]))
+    cb = dict(vals[-1])
+    cb["value"] = v
+    ms = float(np.mean([x["seconds"] for x in vals])) * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "EA-ADC(3) nocc=40 nvir=400 naux=1400, CPU oracle DF ladder sample",
+                       **{k: w[k] for k in ("nocc", "nvir", "naux", "order", "kind", "nvec")}},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from adc_inputs import make_system
+    from paper_2012_06714_gb300 import ADC
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = WORKLOAD
+    o, v, naux, nvec = w["nocc"], w["nvir"], w["naux"], w["nvec"]
+    sysm = make_system(o, v, naux, seed=0)
+    eps_d = torch.from_numpy(sysm.eps).to(dev)
+    B_d = torch.from_numpy(sysm.B).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    gpu = ADC(eps_d, B_d, o, order=3, kind="ea", precision="bf16x3", res_tol=1e-5)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    del B_d
+    stream = torch.cuda.current_stream()
+    gpu.set_stream(stream.cuda_stream)
+    gen = torch.Generator(device=dev).manual_seed(1 + rank)
+    X = torch.randn((nvec, gpu.dim), device=dev, dtype=torch.float64, generator=gen) / np.sqrt(gpu.dim)
+    S = torch.empty_like(X)
+    for _ in range(max(3, args.warmup)):
+        gpu.sigma(X, out=S)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(torch.cuda.current_device())
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        gpu.sigma(X, out=S)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    flops = ladder_flops(o, v, naux, nvec)
+    value = world * flops / (ms / 1e3) / 1e12
+
+    # roofline of the tensor-core ladder kernel, timed live with CUDA events
+    gpu.kernel_timing(True)
+    nprof = 2
+    for _ in range(nprof):
+        gpu.sigma(X, out=S)
+    kt = gpu.kernel_timing(False)
+    launches_per_step = kt["kernels"] / nprof
+    bf16_peak, hbm_peak, peak_src = peaks()
+    peak = bf16_peak / 3.0  # three BF16 products per split-precision product
+    achieved = kt["algo_flops"] / (kt["ms"] / 1e3) / 1e12
+    traffic = None
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": "k_gemm_bf16x3 (both ladder GEMMs)",
+            "peak_note": f"{peak_src} BF16 dense {bf16_peak:.1f} TF/s / 3 split products",
+            "tensor_pipe_frac": kt["mma_flops"] / (kt["ms"] / 1e3) / 1e12 / bf16_peak,
+            "launches_per_step": kt["launches"] / nprof, "ms_per_launch": kt["ms"] / kt["launches"]}
+
+    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    Xh = torch.empty((nvec, gpu.dim), dtype=torch.float64, pin_memory=True)
+    Xh.copy_(X.cpu())
+    Sh = torch.empty_like(Xh).pin_memory()
+    lib = gpu._lib
+    import ctypes
+
+    def sig_host():
+        rc = lib.adc_sigma(gpu._h, ctypes.c_void_p(Xh.data_ptr()), ctypes.c_void_p(Sh.data_ptr()), nvec, 0)
+        assert rc == 0
+
+    sig_host()
+    ke = max(2, args.steps // 2)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        sig_host()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / ke
+    e2e = {"value": world * flops / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": int(Xh.numel() * 8),
+           "d2h_bytes_per_step": int(Sh.numel() * 8)}
+
+    # time to 4 roots (Davidson, mixed precision), setup included separately
+    roots = None
+    if not args.no_roots:
+        t0 = time.perf_counter()
+        e, p, _, st = gpu.davidson(w["nroots"], tol=1e-6)
+        roots = {"seconds": time.perf_counter() - t0, "setup_seconds": setup_s, "energies_eh": [float(x) for x in e],
+                 "spectroscopic_factors": [float(x) for x in p], "iterations": st["iterations"],
+                 "sigma_vectors": st["sigma_vectors"], "status": st["status"]}
+
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
+            "config": {"workload": "EA-ADC(3) sigma build, nocc=40 nvir=400 naux=1400, 4 trial vectors",
+                       "nocc": o, "nvir": v, "naux": naux, "order": 3, "kind": "ea", "nvec": nvec, "dim": gpu.dim,
+                       "l2": "inputs larger than L2 (B^Q > 2 GB)", "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "e2e": e2e, "roofline": roof, "gpu_launches": int(round(launches_per_step)), "clocks": clk,
+            "time_to_roots": roots}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line))
+    gpu.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-roots", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -61,7 +61,9 @@ extern "C" {
 #define ADC_PREC_FP64 0   /* every contraction in FP64                              */
 #define ADC_PREC_BF16X3 1 /* DF ladder (sigma and setup) on tcgen05 tensor cores:   */
                           /* split hi/lo BF16 operands, 3 products, FP32 accumulate */
-                          /* per auxiliary chunk, FP64 across chunks; the rest FP64 */
+                          /* per auxiliary chunk, FP64 across chunks; the other     */
+                          /* large contractions FP32-accurate (BF16x9 emulated      */
+                          /* GEMM), FP64 vectors, subspace and accumulation         */
 
 typedef struct adc_handle adc_handle; /* opaque */
 
@@ -128,6 +130,18 @@ int adc_davidson(adc_handle* h, int nroots, double tol, const double* guess, dou
  * intermediate does not exist at this order).
  */
 int adc_get_tensor(adc_handle* h, const char* name, double* out, long long n);
+
+/*
+ * Live timing of the tensor-core ladder kernel launches (for roofline
+ * reporting).  enable = 1 clears the record and starts bracketing every
+ * tensor-core GEMM launch on the handle's stream with CUDA events; enable = 0
+ * stops, synchronises and, if out is non-NULL, writes out[5] =
+ * {launches, total milliseconds of those launches, algorithmic flops
+ * (4 naux nocc nvir^3-type count, unpadded), tensor-core flops issued
+ * (3 split products over padded tiles), all own kernels launched meanwhile}.
+ * Errors: ADC_ERR_ARG, ADC_ERR_CUDA.
+ */
+int adc_kernel_timing(adc_handle* h, int enable, double* out);
 
 /* Message of the last error on this handle (or of the last failed adc_setup
  * when h is NULL).  Never NULL. */

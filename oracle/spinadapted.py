@@ -33,6 +33,11 @@ from __future__ import annotations
 import numpy as np
 
 
+def df_ladder(Bvv, X):
+    """sum_cd (ac|bd) X[..., c, d] with (ac|bd) = sum_Q B^Q_ac B^Q_bd (Eq. 19): sum_Q B^Q X B^Q."""
+    return np.einsum("Qac,...cd,Qdb->...ab", Bvv, X, Bvv, optimize=True)
+
+
 class SpinAdaptedADC:
     """Closed-shell DF-ADC(order) for EA (kind='ea') or IP (kind='ip')."""
 
@@ -64,7 +69,7 @@ class SpinAdaptedADC:
 
     def ladder(self, X):
         """sum_cd (ac|bd) X[..., c, d] = sum_Q (B^Q X B^Q)_ab  (vvvv never stored)."""
-        return np.einsum("Qac,...cd,Qdb->...ab", self.Bvv, X, self.Bvv, optimize=True)
+        return df_ladder(self.Bvv, X)
 
     def ovvv_contract(self, X, pattern):
         """Contractions with the (ov|vv) class through B, never forming it."""

@@ -22,6 +22,7 @@ EXPORTED = [
     "adc_sigma",
     "adc_davidson",
     "adc_get_tensor",
+    "adc_kernel_timing",
     "adc_last_error",
     "adc_destroy",
 ]
@@ -70,6 +71,7 @@ def load_library():
     lib.adc_sigma.argtypes = [P, P, P, I, I]
     lib.adc_davidson.argtypes = [P, I, D, P, P, P, P, P]
     lib.adc_get_tensor.argtypes = [P, ctypes.c_char_p, P, LL]
+    lib.adc_kernel_timing.argtypes = [P, I, P]
     lib.adc_last_error.argtypes = [P]
     lib.adc_last_error.restype = ctypes.c_char_p
     lib.adc_destroy.argtypes = [P]
@@ -169,6 +171,16 @@ class ADC:
         out = np.zeros(int(np.prod(shape)))
         self._check(self._lib.adc_get_tensor(self._h, name.encode(), out.ctypes.data, out.size))
         return out.reshape(shape)
+
+    def kernel_timing(self, enable: bool):
+        """Start (True) or stop (False) live timing of the tensor-core launches.
+
+        On stop returns dict(launches, ms, algo_flops, mma_flops, kernels)."""
+        out = np.zeros(5)
+        self._check(self._lib.adc_kernel_timing(self._h, 1 if enable else 0, out.ctypes.data))
+        if enable:
+            return None
+        return dict(launches=int(out[0]), ms=out[1], algo_flops=out[2], mma_flops=out[3], kernels=int(out[4]))
 
     def close(self):
         if getattr(self, "_h", None):

@@ -35,6 +35,7 @@ struct adc_handle {
     double *ovov = nullptr, *oovv = nullptr, *oooo = nullptr, *ooov = nullptr;
     double *t = nullptr, *tau = nullptr, *t_2 = nullptr, *t1_2 = nullptr, *M11 = nullptr, *diag = nullptr;
     LadderTC* tc = nullptr;  // tensor-core ladder state (BF16x3 operands of B^Q_vv)
+    double* Lt = nullptr;    // setup only: sum_cd (ac|bd) t_kl^cd, shared by t2(2) and the EA 1p-1p block
     std::vector<void*> owned;
     std::string err;
     long long dim() const {
@@ -275,9 +276,7 @@ static void setup_m11_ea(adc_handle* h) {
     einsum(c, "klac,kblc->ab", -1.0, tn(t2, {o, o, v, v}), tn(h->ovov, {o, v, o, v}), 1.0, X, {v, v});
     einsum(c, "klac,kclb->ab", 0.5, tn(t2, {o, o, v, v}), tn(h->ovov, {o, v, o, v}), 1.0, X, {v, v});
     // vvvv, one open line: -sum t_kl^ac [L_kl^bc - 1/2 L_kl^cb], L_kl = sum_cd (bc..) ladder of t
-    double* L = c.arena.dalloc(o * o * v * v);
-    fill(c, o * o * v * v, 0.0, L);
-    ladder(h, t, o * o, L);
+    const double* L = h->Lt;
     einsum(c, "klac,klbc->ab", -1.0, tn(t, {o, o, v, v}), tn(L, {o, o, v, v}), 1.0, X, {v, v});
     einsum(c, "klac,klcb->ab", 0.5, tn(t, {o, o, v, v}), tn(L, {o, o, v, v}), 1.0, X, {v, v});
     // ring with the open lines on the amplitudes (G_A with t_km^ac, G_B with t_km^ca):
@@ -383,6 +382,7 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
     ADC_BLAS(cublasCreate(&c.blas));
     ADC_BLAS(cublasSetStream(c.blas, c.stream));
     ADC_BLAS(cublasSetMathMode(c.blas, CUBLAS_DEFAULT_MATH));
+    c.gemm_mode = h->opt.precision == ADC_PREC_BF16X3 ? 1 : 0;
     const long long o = h->o, v = h->v, Q = h->naux, nmo = o + v;
     h->eps = h->dmalloc(nmo);
     ADC_CUDA(cudaMemcpyAsync(h->eps, eps_in, nmo * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -422,13 +422,16 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
         int swp[4] = {0, 1, 3, 2};
         permute(c, h->t, s4, swp, h->tau, -1.0, 1.0);
     }
+    Scope setup_scope(c.arena);
     if (h->order >= 3) {
-        Scope sc(c.arena);
         const double* t = h->t;
+        h->Lt = c.arena.dalloc(o * o * v * v);
+        fill(c, o * o * v * v, 0.0, h->Lt);
+        ladder(h, t, o * o, h->Lt);  // sum_cd (ac|bd) t_ij^cd
+        Scope sc(c.arena);
         h->t_2 = h->dmalloc(o * o * v * v);
         double* N = h->t_2;
-        fill(c, o * o * v * v, 0.0, N);
-        ladder(h, t, o * o, N);  // sum_cd (ac|bd) t_ij^cd
+        ADC_CUDA(cudaMemcpyAsync(N, h->Lt, o * o * v * v * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
         einsum(c, "kilj,klab->ijab", 1.0, tn(h->oooo, {o, o, o, o}), tn(t, {o, o, v, v}), 1.0, N, {o, o, v, v});
         double* W = c.arena.dalloc(o * o * v * v);
         einsum(c, "kcjb,ikac->ijab", 2.0, tn(h->ovov, {o, v, o, v}), tn(t, {o, o, v, v}), 0.0, W, {o, o, v, v});
@@ -466,6 +469,7 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
         setup_m11_ea(h);
     else
         setup_m11_ip(h);
+    h->Lt = nullptr;
     h->diag = h->dmalloc(h->dim());
     k_diag<<<grid_for(h->dim()), 256, 0, c.stream>>>(h->kind == ADC_EA, (int)o, (int)v, h->eps, h->M11, h->diag);
     launch_check(c);
@@ -1096,6 +1100,41 @@ int adc_get_tensor(adc_handle* h, const char* name, double* out, long long n) {
         }
         ADC_CUDA(cudaMemcpyAsync(out, src, cnt * sizeof(double), cudaMemcpyDeviceToHost, h->ctx.stream));
         ADC_CUDA(cudaStreamSynchronize(h->ctx.stream));
+        return ADC_OK;
+    })
+}
+
+int adc_kernel_timing(adc_handle* h, int enable, double* out) {
+    if (!h) return ADC_ERR_ARG;
+    GUARD(h, {
+        Ctx& c = h->ctx;
+        if (enable) {
+            for (auto e : c.ev_start) cudaEventDestroy(e);
+            for (auto e : c.ev_stop) cudaEventDestroy(e);
+            c.ev_start.clear();
+            c.ev_stop.clear();
+            c.algo_flops = c.mma_flops = 0.0;
+            c.kernels_at_start = c.kernels;
+            c.timing = true;
+            if (out)
+                for (int i = 0; i < 5; ++i) out[i] = 0.0;
+            return ADC_OK;
+        }
+        c.timing = false;
+        ADC_CUDA(cudaStreamSynchronize(c.stream));
+        double ms = 0.0;
+        for (size_t i = 0; i < c.ev_start.size(); ++i) {
+            float t = 0.f;
+            ADC_CUDA(cudaEventElapsedTime(&t, c.ev_start[i], c.ev_stop[i]));
+            ms += t;
+        }
+        if (out) {
+            out[0] = (double)c.ev_start.size();
+            out[1] = ms;
+            out[2] = c.algo_flops;
+            out[3] = c.mma_flops;
+            out[4] = (double)(c.kernels - c.kernels_at_start);
+        }
         return ADC_OK;
     })
 }

@@ -31,6 +31,22 @@ __global__ void permute_kernel(const double* __restrict__ in, double* __restrict
     }
 }
 
+template <typename Tin, typename Tout>
+__global__ void permute_cvt_kernel(const Tin* __restrict__ in, Tout* __restrict__ out, PermArgs a, long long total,
+                                   double alpha, double beta) {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        long long r = idx, off = 0;
+        for (int j = a.nd - 1; j >= 0; --j) {
+            long long cj = r % a.dout[j];
+            r /= a.dout[j];
+            off += cj * a.sin[j];
+        }
+        double v = alpha * (double)in[off];
+        out[idx] = (Tout)((beta == 0.0) ? v : v + beta * (double)out[idx]);
+    }
+}
+
 __global__ void axpby_kernel(long long n, double alpha, const double* __restrict__ x, double beta, double* __restrict__ y) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         y[i] = (beta == 0.0) ? alpha * x[i] : alpha * x[i] + beta * y[i];
@@ -64,6 +80,34 @@ void permute(Ctx& c, const double* in, const Shape& s, const int* perm, double* 
     }
     if (total == 0) return;
     permute_kernel<<<grid_for(total), 256, 0, c.stream>>>(in, out, a, total, alpha, beta);
+    ++c.kernels;
+    ADC_CUDA(cudaGetLastError());
+}
+
+static PermArgs perm_args(const Shape& s, const int* perm, long long& total) {
+    PermArgs a;
+    a.nd = s.nd;
+    long long st[kMaxDim];
+    long long acc = 1;
+    total = 1;
+    for (int j = s.nd - 1; j >= 0; --j) {
+        st[j] = acc;
+        acc *= s.d[j];
+    }
+    for (int j = 0; j < s.nd; ++j) {
+        a.dout[j] = s.d[perm[j]];
+        a.sin[j] = st[perm[j]];
+        total *= a.dout[j];
+    }
+    return a;
+}
+
+template <typename Tin, typename Tout>
+static void permute_cvt(Ctx& c, const Tin* in, const Shape& s, const int* perm, Tout* out, double alpha, double beta) {
+    long long total;
+    PermArgs a = perm_args(s, perm, total);
+    if (total == 0) return;
+    permute_cvt_kernel<Tin, Tout><<<grid_for(total), 256, 0, c.stream>>>(in, out, a, total, alpha, beta);
     ++c.kernels;
     ADC_CUDA(cudaGetLastError());
 }
@@ -144,6 +188,65 @@ const double* to_order(Ctx& c, const double* src, const std::string& ls, const s
 
 }  // namespace
 
+// FP32-accurate contraction: operands permuted and rounded to FP32, GEMM with
+// BF16x9 emulation (falls back to plain FP32 if the library lacks it), result
+// permuted and accumulated into the FP64 output.
+static void einsum_fp32(Ctx& c, const std::string& la, const std::string& lb, const std::string& lc,
+                        std::map<char, long long>& dim, const std::string& batch, const std::string& fa,
+                        const std::string& fb, const std::string& con, double alpha, const double* Ap, const double* Bp,
+                        double beta, double* C) {
+    auto prod = [&](const std::string& l) {
+        long long p = 1;
+        for (char x : l) p *= dim[x];
+        return p;
+    };
+    long long nb = prod(batch), M = prod(fa), N = prod(fb), K = prod(con);
+    auto conv = [&](const double* src, const std::string& ls, const std::string& lt) {
+        Shape sh;
+        sh.nd = (int)ls.size();
+        long long n = 1;
+        for (int j = 0; j < sh.nd; ++j) {
+            sh.d[j] = dim.at(ls[j]);
+            n *= sh.d[j];
+        }
+        int perm[kMaxDim];
+        for (int j = 0; j < sh.nd; ++j) perm[j] = (int)ls.find(lt[j]);
+        float* dst = (float*)c.arena.alloc(n * sizeof(float));
+        permute_cvt<double, float>(c, src, sh, perm, dst, 1.0, 0.0);
+        return dst;
+    };
+    const float* A32 = conv(Ap, la, batch + fa + con);
+    const float* B32 = conv(Bp, lb, batch + con + fb);
+    float* T32 = (float*)c.arena.alloc(nb * M * N * sizeof(float));
+    const float one = 1.0f, zero = 0.0f;
+    // row-major T[M][N] = A[M][K] B[K][N]  <=>  column-major T^T = B^T A^T
+    auto run = [&](cublasComputeType_t ct) {
+        return cublasGemmStridedBatchedEx(c.blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)N, (int)M, (int)K, &one, B32, CUDA_R_32F,
+                                          (int)N, K * N, A32, CUDA_R_32F, (int)K, M * K, &zero, T32, CUDA_R_32F, (int)N,
+                                          M * N, (int)nb, ct, CUBLAS_GEMM_DEFAULT);
+    };
+    if (c.emulation_ok != 0) {
+        cublasStatus_t st = run(CUBLAS_COMPUTE_32F_EMULATED_16BFX9);
+        if (st == CUBLAS_STATUS_SUCCESS) {
+            c.emulation_ok = 1;
+        } else if (c.emulation_ok == -1 && (st == CUBLAS_STATUS_NOT_SUPPORTED || st == CUBLAS_STATUS_INVALID_VALUE)) {
+            c.emulation_ok = 0;
+            ADC_BLAS(run(CUBLAS_COMPUTE_32F));
+        } else {
+            ADC_BLAS(st);
+        }
+    } else {
+        ADC_BLAS(run(CUBLAS_COMPUTE_32F));
+    }
+    std::string tord = batch + fa + fb;
+    Shape sh;
+    sh.nd = (int)tord.size();
+    for (int j = 0; j < sh.nd; ++j) sh.d[j] = dim[tord[j]];
+    int perm[kMaxDim];
+    for (int j = 0; j < sh.nd; ++j) perm[j] = (int)tord.find(lc[j]);
+    permute_cvt<float, double>(c, T32, sh, perm, C, alpha, beta);
+}
+
 void einsum(Ctx& c, const char* specstr, double alpha, const T& A, const T& B, double beta, double* C,
             const std::vector<long long>& cdims) {
     Spec sp = parse(specstr);
@@ -187,6 +290,11 @@ void einsum(Ctx& c, const char* specstr, double alpha, const T& A, const T& B, d
     };
     long long nb = prod(batch), M = prod(fa), N = prod(fb), K = prod(con);
     Arena::Mark mk = c.arena.mark();
+    if (c.gemm_mode == 1 && 2.0 * nb * M * N * K >= c.fp32_min_flops) {
+        einsum_fp32(c, sp.a, sp.b, sp.c, dim, batch, fa, fb, con, alpha, A.p, B.p, beta, C);
+        c.arena.release(mk);
+        return;
+    }
     const double* Ap = to_order(c, A.p, sp.a, dim, batch + fa + con);
     const double* Bp = to_order(c, B.p, sp.b, dim, batch + con + fb);
     std::string tord = batch + fa + fb;

@@ -97,6 +97,17 @@ struct Ctx {
     cublasHandle_t blas = nullptr;
     Arena arena;
     long long kernels = 0;  // own kernel launches issued (for reporting)
+    // 0: every contraction in FP64 (DGEMM).  1: contractions of >= fp32_min_flops
+    // run as FP32-accurate GEMMs (BF16x9 emulation on the tensor cores), with
+    // FP64 inputs rounded to FP32 and results accumulated into FP64.
+    int gemm_mode = 0;
+    double fp32_min_flops = 2e8;
+    int emulation_ok = -1;  // -1 unknown, 1 BF16x9 emulation available, 0 plain FP32
+    // live timing of the tensor-core GEMM launches (see adc_kernel_timing)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_start, ev_stop;
+    double algo_flops = 0.0, mma_flops = 0.0;
+    long long kernels_at_start = 0;
 };
 
 constexpr int kMaxDim = 8;

@@ -352,7 +352,7 @@ int pick_bn(int n) {
 }
 
 void launch_gemm(Ctx& c, const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh, const CUtensorMap& bl,
-                 int a_row0, int b_x0, int M, int N, int K, int BN, int m_fastest, const Epi& ep) {
+                 int a_row0, int b_x0, int M, int N, int K, int BN, int m_fastest, const Epi& ep, double algo_flops) {
     static bool attr = false;
     if (!attr) {
         ADC_CUDA(cudaFuncSetAttribute(k_gemm_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
@@ -361,9 +361,22 @@ void launch_gemm(Ctx& c, const CUtensorMap& ah, const CUtensorMap& al, const CUt
     const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
     dim3 grid = m_fastest ? dim3(mt, nt) : dim3(nt, mt);
     if (grid.y > 65535) throw Error(-1, "ladder: tile grid too large");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c.timing) {
+        ADC_CUDA(cudaEventCreate(&e0));
+        ADC_CUDA(cudaEventCreate(&e1));
+        ADC_CUDA(cudaEventRecord(e0, c.stream));
+    }
     k_gemm_bf16x3<<<grid, THREADS, SMEM_BYTES, c.stream>>>(ah, al, bh, bl, a_row0, b_x0, K, BN, m_fastest, ep);
     ++c.kernels;
     ADC_CUDA(cudaGetLastError());
+    if (c.timing) {
+        ADC_CUDA(cudaEventRecord(e1, c.stream));
+        c.ev_start.push_back(e0);
+        c.ev_stop.push_back(e1);
+        c.algo_flops += algo_flops;
+        c.mma_flops += 3.0 * 2.0 * (double)mt * BM * (double)nt * BN * (double)(((K + BK - 1) / BK) * BK);
+    }
 }
 
 }  // namespace
@@ -455,7 +468,8 @@ void ladder_tc_apply(LadderTC& L, Ctx& c, const double* X, long long nmat, doubl
             e1.vp = vp;
             e1.qn = qn;
             e1.err = L.d_err;
-            launch_gemm(c, L.mBs_hi, L.mBs_lo, mXh, mXl, q0 * v, 0, e1.M, e1.N, vp, 256, 1, e1);
+            const double algo = 2.0 * (double)qn * v * (double)nm * v * v;  // unpadded B^q X_n products
+            launch_gemm(c, L.mBs_hi, L.mBs_lo, mXh, mXl, q0 * v, 0, e1.M, e1.N, vp, 256, 1, e1, algo);
             // GEMM2: out[(n,a),b] += sum_(q,d) Z_n[a,(q,d)] B^q[d,b]
             CUtensorMap mZh = make_map(zh, nm * v, (long long)qn * vp, BM), mZl = make_map(zl, nm * v, (long long)qn * vp, BM);
             Epi e2{};
@@ -465,7 +479,7 @@ void ladder_tc_apply(LadderTC& L, Ctx& c, const double* X, long long nmat, doubl
             e2.out = out + m0 * v * v;
             e2.ldc = v;
             e2.err = L.d_err;
-            launch_gemm(c, mZh, mZl, L.mBp_hi, L.mBp_lo, 0, q0 * vp, e2.M, e2.N, qn * vp, L.bn2, 0, e2);
+            launch_gemm(c, mZh, mZl, L.mBp_hi, L.mBp_lo, 0, q0 * vp, e2.M, e2.N, qn * vp, L.bn2, 0, e2, algo);
         }
     }
     int err = 0;
