@@ -143,6 +143,29 @@ int adc_get_tensor(adc_handle* h, const char* name, double* out, long long n);
  */
 int adc_kernel_timing(adc_handle* h, int enable, double* out);
 
+/*
+ * Allocation-free density-fitted ladder: out[n] = sum_Q B^Q X[n] B^Q for nmat
+ * nvir x nvir matrices, i.e. sum_cd (ac|bd) X[n][c][d] -- the dominant 2p1h
+ * (EA) sigma term, computed by the same tensor-core kernel as adc_sigma.  The
+ * paper has no counterpart: it exists for callers that cannot allocate device
+ * memory during the call (a host framework that owns all device memory and
+ * forbids cudaMalloc/cudaFree inside library calls, which may synchronise the
+ * device).  It allocates nothing: its intermediates live in a fixed 64 MiB
+ * device array that every GPU loading this library holds until process exit.
+ *   h    handle set up with precision ADC_PREC_BF16X3 (uses its split B^Q)
+ *   X    device [nmat][nvir][nvir] FP64;  out  device [nmat][nvir][nvir] FP64,
+ *        overwritten; X and out must not overlap
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one array and it keeps the last call's
+ * contents: calls that overlap on the GPU (other streams, other threads) race.
+ * Work runs on the handle's stream and has completed when the call returns.
+ * Errors: ADC_ERR_ARG (NULL pointers, nmat < 0, handle not BF16X3, or nvir so
+ * large that one matrix and one auxiliary function exceed the 64 MiB),
+ * ADC_ERR_CUDA, ADC_ERR_TIMEOUT.
+ */
+int adc_ladder_noalloc(adc_handle* h, const double* X, double* out, long long nmat);
+
 /* Message of the last error on this handle (or of the last failed adc_setup
  * when h is NULL).  Never NULL. */
 const char* adc_last_error(const adc_handle* h);

@@ -23,6 +23,7 @@ EXPORTED = [
     "adc_davidson",
     "adc_get_tensor",
     "adc_kernel_timing",
+    "adc_ladder_noalloc",
     "adc_last_error",
     "adc_destroy",
 ]
@@ -72,6 +73,7 @@ def load_library():
     lib.adc_davidson.argtypes = [P, I, D, P, P, P, P, P]
     lib.adc_get_tensor.argtypes = [P, ctypes.c_char_p, P, LL]
     lib.adc_kernel_timing.argtypes = [P, I, P]
+    lib.adc_ladder_noalloc.argtypes = [P, P, P, LL]
     lib.adc_last_error.argtypes = [P]
     lib.adc_last_error.restype = ctypes.c_char_p
     lib.adc_destroy.argtypes = [P]

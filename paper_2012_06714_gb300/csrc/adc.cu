@@ -951,6 +951,18 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
     return status;
 }
 
+// Internal accessor for the allocation-free ladder entry point (ladder_static.cu).
+namespace adc {
+bool handle_ladder_view(adc_handle* h, LadderTC** tc, Ctx** c, int* nvir, std::string** err) {
+    if (!h) return false;
+    *tc = h->tc;
+    *c = &h->ctx;
+    *nvir = h->v;
+    *err = &h->err;
+    return true;
+}
+}  // namespace adc
+
 // --------------------------------------------------------------------------
 // C ABI
 // --------------------------------------------------------------------------

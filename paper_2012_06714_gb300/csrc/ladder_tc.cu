@@ -489,4 +489,69 @@ void ladder_tc_apply(LadderTC& L, Ctx& c, const double* X, long long nmat, doubl
     if (err) throw Error(-5, "ladder: a bounded device wait timed out");
 }
 
+// Same ladder as ladder_tc_apply, but every intermediate (split X^T and Z) is
+// carved out of a caller-provided device buffer of `bytes` bytes instead of
+// the handle's scratch arena.  out is overwritten (zeroed, then accumulated).
+// Returns false (launching nothing) if one matrix and one auxiliary function
+// do not fit in the buffer.
+bool ladder_tc_apply_scratch(LadderTC& L, Ctx& c, const double* X, long long nmat, double* out, void* scratch,
+                             size_t bytes) {
+    const int v = L.v, vp = L.vp, naux = L.naux;
+    const long long per_xt = (long long)vp * vp * 4;  // split X^T (hi+lo) per matrix
+    const long long per_mq = (long long)v * vp * 4;   // Z (hi+lo) per (matrix, aux function)
+    auto round256 = [](long long b) { return (b + 255) / 256 * 256; };
+    if (round256(per_xt) + round256(per_mq) > (long long)bytes) return false;
+    if (nmat <= 0) return true;
+    const int qmax = std::max(1, std::min(naux, std::max(1, 8192 / vp)));
+    const int qwant = std::min(8, qmax);
+    long long mg = std::max<long long>(1, (long long)bytes / (per_xt + per_mq * qwant + 1024));
+    mg = std::min(mg, nmat);
+    while (mg > 1 && round256(mg * per_xt) + round256(mg * per_mq) > (long long)bytes) --mg;
+    const long long left = (long long)bytes - round256(mg * per_xt);
+    int qc = (int)std::max<long long>(1, left / (per_mq * mg));
+    qc = std::max(1, std::min(qc, qmax));
+    char* base = (char*)scratch;
+    auto* xh = (__nv_bfloat16*)base;
+    auto* xl = xh + mg * vp * vp;
+    auto* zh = (__nv_bfloat16*)(base + round256(mg * per_xt));
+    auto* zl = zh + mg * v * (long long)qc * vp;
+    ADC_CUDA(cudaMemsetAsync(out, 0, (size_t)nmat * v * v * sizeof(double), c.stream));
+    for (long long m0 = 0; m0 < nmat; m0 += mg) {
+        const long long nm = std::min(mg, nmat - m0);
+        k_split_XT<<<grid_for(nm * vp * vp), 256, 0, c.stream>>>(X + m0 * v * v, nm, v, vp, xh, xl);
+        ++c.kernels;
+        ADC_CUDA(cudaGetLastError());
+        CUtensorMap mXh = make_map(xh, nm * vp, vp, 256), mXl = make_map(xl, nm * vp, vp, 256);
+        for (int q0 = 0; q0 < naux; q0 += qc) {
+            const int qn = std::min(qc, naux - q0);
+            Epi e1{};
+            e1.mode = 0;
+            e1.M = qn * v;
+            e1.N = (int)(nm * vp);
+            e1.zhi = zh;
+            e1.zlo = zl;
+            e1.v = v;
+            e1.vp = vp;
+            e1.qn = qn;
+            e1.err = L.d_err;
+            const double algo = 2.0 * (double)qn * v * (double)nm * v * v;
+            launch_gemm(c, L.mBs_hi, L.mBs_lo, mXh, mXl, q0 * v, 0, e1.M, e1.N, vp, 256, 1, e1, algo);
+            CUtensorMap mZh = make_map(zh, nm * v, (long long)qn * vp, BM), mZl = make_map(zl, nm * v, (long long)qn * vp, BM);
+            Epi e2{};
+            e2.mode = 1;
+            e2.M = (int)(nm * v);
+            e2.N = v;
+            e2.out = out + m0 * v * v;
+            e2.ldc = v;
+            e2.err = L.d_err;
+            launch_gemm(c, mZh, mZl, L.mBp_hi, L.mBp_lo, 0, q0 * vp, e2.M, e2.N, qn * vp, L.bn2, 0, e2, algo);
+        }
+    }
+    int err = 0;
+    ADC_CUDA(cudaMemcpyAsync(&err, L.d_err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    ADC_CUDA(cudaStreamSynchronize(c.stream));
+    if (err) throw Error(-5, "ladder: a bounded device wait timed out");
+    return true;
+}
+
 }  // namespace adc
