@@ -74,6 +74,8 @@ typedef struct {
     int nguess_extra;        /* extra guess vectors beyond nroots (default 2)         */
     double res_tol;          /* S-norm residual tolerance; <= 0 means sqrt(tol)       */
     int aux_chunk;           /* auxiliary functions per ladder chunk; 0 = automatic   */
+    int keep_per_root;       /* Ritz vectors kept per root when the space is          */
+                             /* collapsed (thick restart, default 2)                  */
 } adc_options;
 
 /* Fill *opt with the defaults listed above.  Returns ADC_OK or ADC_ERR_ARG (NULL). */

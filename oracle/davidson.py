@@ -75,15 +75,17 @@ def spectroscopic_factors(adc, Y):
     return 2.0 * np.einsum("rp,rp->r", X, X)
 
 
-def davidson(adc, nroots, tol=1e-8, max_space_per_root=8, max_iter=200, nguess_extra=2, guess=None):
+def davidson(adc, nroots, tol=1e-8, max_space_per_root=8, max_iter=200, nguess_extra=2, guess=None, keep_per_root=2,
+             res_tol=None):
     """Multi-root Davidson in the S inner product, FP64, diagonal preconditioner.
 
     Readings (the paper does not give them): guesses are unit vectors at the
     nroots + nguess_extra lowest diagonal elements (diag(M_11) and the zeroth-
     order 2p1h/2h1p energies); correction t = r / (w - D) with |w - D| kept
     >= 1e-8; a root is converged when |dw| <= tol and ||r||_S <= sqrt(tol);
-    the space is collapsed to the current Ritz vectors when it would exceed
-    max_space_per_root * nroots.
+    the space is collapsed to the lowest keep_per_root * nroots Ritz vectors
+    when it would exceed max_space_per_root * nroots (res_tol, if given,
+    replaces sqrt(tol)).
     Returns (w[nroots], Y[nroots, dim], n_iterations, n_sigma).
     """
     dim = adc.dim
@@ -99,17 +101,18 @@ def davidson(adc, nroots, tol=1e-8, max_space_per_root=8, max_iter=200, nguess_e
     W = adc.sigma(V)
     nsig = V.shape[0]
     w_old = np.full(nroots, np.inf)
-    maxspace = max(max_space_per_root * nroots, nstart + nroots)
+    maxspace = max(max_space_per_root * nroots, max(nstart, keep_per_root * nroots) + nroots)
+    rtol = np.sqrt(tol) if res_tol is None else res_tol
     for it in range(1, max_iter + 1):
         G = V @ adc.apply_S(W).T
         G = 0.5 * (G + G.T)
-        e, C = np.linalg.eigh(G)
-        e, C = e[:nroots], C[:, :nroots]
+        e_all, C_all = np.linalg.eigh(G)
+        e, C = e_all[:nroots], C_all[:, :nroots]
         X = C.T @ V
         AX = C.T @ W
         R = AX - e[:, None] * X
         rnorm = np.sqrt(np.einsum("rk,rk->r", R, adc.apply_S(R)))
-        conv = (np.abs(e - w_old) <= tol) & (rnorm <= np.sqrt(tol))
+        conv = (np.abs(e - w_old) <= tol) & (rnorm <= rtol)
         w_old = e
         if np.all(conv):
             return e, X, it, nsig
@@ -122,9 +125,9 @@ def davidson(adc, nroots, tol=1e-8, max_space_per_root=8, max_iter=200, nguess_e
             new.append(R[r] / den)
         new = np.array(new)
         if V.shape[0] + new.shape[0] > maxspace:
-            V = _s_orthonormalise(adc, X, np.zeros((0, dim)))
-            W = adc.sigma(V)
-            nsig += V.shape[0]
+            nkeep = min(V.shape[0], keep_per_root * nroots)
+            Ck = C_all[:, :nkeep]
+            V, W = Ck.T @ V, Ck.T @ W  # Ritz vectors are S-orthonormal; W stays sigma(V)
         new = _s_orthonormalise(adc, new, V)
         if new.shape[0] == 0:
             return e, X, it, nsig

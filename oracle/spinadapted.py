@@ -34,8 +34,15 @@ import numpy as np
 
 
 def df_ladder(Bvv, X):
-    """sum_cd (ac|bd) X[..., c, d] with (ac|bd) = sum_Q B^Q_ac B^Q_bd (Eq. 19): sum_Q B^Q X B^Q."""
-    return np.einsum("Qac,...cd,Qdb->...ab", Bvv, X, Bvv, optimize=True)
+    """sum_cd (ac|bd) X[..., c, d] with (ac|bd) = sum_Q B^Q_ac B^Q_bd (Eq. 19): sum_Q B^Q X B^Q.
+
+    Written as a loop over the auxiliary index so that no intermediate larger
+    than X is formed."""
+    X = np.asarray(X, dtype=np.float64)
+    out = np.zeros_like(X)
+    for BQ in Bvv:
+        out += BQ @ X @ BQ
+    return out
 
 
 class SpinAdaptedADC:
@@ -62,10 +69,10 @@ class SpinAdaptedADC:
     # ---- integrals from the DF factors (Eq. 19) ---------------------------
     def _integrals(self):
         Boo, Bov, Bvv = self.Boo, self.Bov, self.Bvv
-        self.ovov = np.einsum("Qia,Qjb->iajb", Bov, Bov)  # (ia|jb)
-        self.oovv = np.einsum("Qij,Qab->ijab", Boo, Bvv)  # (ij|ab)
-        self.oooo = np.einsum("Qij,Qkl->ijkl", Boo, Boo)  # (ij|kl)
-        self.ooov = np.einsum("Qij,Qka->ijka", Boo, Bov)  # (ij|ka)
+        self.ovov = np.einsum("Qia,Qjb->iajb", Bov, Bov, optimize=True)  # (ia|jb)
+        self.oovv = np.einsum("Qij,Qab->ijab", Boo, Bvv, optimize=True)  # (ij|ab)
+        self.oooo = np.einsum("Qij,Qkl->ijkl", Boo, Boo, optimize=True)  # (ij|kl)
+        self.ooov = np.einsum("Qij,Qka->ijka", Boo, Bov, optimize=True)  # (ij|ka)
 
     def ladder(self, X):
         """sum_cd (ac|bd) X[..., c, d] = sum_Q (B^Q X B^Q)_ab  (vvvv never stored)."""
@@ -88,18 +95,18 @@ class SpinAdaptedADC:
             return
         # second-order doubles: D t = sum_cd (ac|bd) t_ij^cd + sum_kl (ki|lj) t_kl^ab + W + W^T
         lad = self.ladder(t)
-        hh = np.einsum("kilj,klab->ijab", oooo, t)
+        hh = np.einsum("kilj,klab->ijab", oooo, t, optimize=True)
         W = (
-            2.0 * np.einsum("kcjb,ikac->ijab", ovov, t)
-            - np.einsum("kcjb,ikca->ijab", ovov, t)
-            - np.einsum("kjbc,ikac->ijab", oovv, t)
-            - np.einsum("kjac,ikcb->ijab", oovv, t)
+            2.0 * np.einsum("kcjb,ikac->ijab", ovov, t, optimize=True)
+            - np.einsum("kcjb,ikca->ijab", ovov, t, optimize=True)
+            - np.einsum("kjbc,ikac->ijab", oovv, t, optimize=True)
+            - np.einsum("kjac,ikcb->ijab", oovv, t, optimize=True)
         )
         self.t_2 = (lad + hh + W + W.transpose(1, 0, 3, 2)) / D2
         # second-order singles: D t_i^a = sum (kc|ad)(2 t_ik^dc - t_ik^cd) - sum (ki|lc)(2 t_kl^ac - t_kl^ca)
         tau = 2.0 * t - t.transpose(0, 1, 3, 2)
         s1 = self.ovvv_contract(tau, "Qkc,Qad,ikdc->ia")
-        s2 = np.einsum("kilc,klac->ia", self.ooov, tau)
+        s2 = np.einsum("kilc,klac->ia", self.ooov, tau, optimize=True)
         self.t1_2 = (s1 - s2) / D1
 
     # ---- 1p-1p / 1h-1h block (Table 1 second row; precomputed, Sec. III A) --
@@ -115,42 +122,42 @@ class SpinAdaptedADC:
             return X + X.T
 
         # second order: -sum t_kl^ac [(kb|lc) - 1/2 (kc|lb)] + (a<->b)
-        M += sym(-np.einsum("klac,kblc->ab", t, ovov) + 0.5 * np.einsum("klac,kclb->ab", t, ovov))
+        M += sym(-np.einsum("klac,kblc->ab", t, ovov, optimize=True) + 0.5 * np.einsum("klac,kclb->ab", t, ovov, optimize=True))
         if self.order < 3:
             return M
         t2, t1 = self.t_2, self.t1_2
         Bov, Bvv = self.Bov, self.Bvv
         # t1(2) terms: sum_kc t_k^c [2 (kc|ab) - (kb|ac)] + (a<->b)
-        K1 = 2.0 * np.einsum("Qkc,kc,Qab->ab", Bov, t1, Bvv) - np.einsum("Qkb,kc,Qac->ab", Bov, t1, Bvv)
+        K1 = 2.0 * np.einsum("Qkc,kc,Qab->ab", Bov, t1, Bvv, optimize=True) - np.einsum("Qkb,kc,Qac->ab", Bov, t1, Bvv, optimize=True)
         M += sym(K1)
         # t2(2) terms, same shape as second order
-        M += sym(-np.einsum("klac,kblc->ab", t2, ovov) + 0.5 * np.einsum("klac,kclb->ab", t2, ovov))
+        M += sym(-np.einsum("klac,kblc->ab", t2, ovov, optimize=True) + 0.5 * np.einsum("klac,kclb->ab", t2, ovov, optimize=True))
         # vvvv with one open line: -sum t_kl^ac [L_kl^bc - 1/2 L_kl^cb], L_kl = sum_Q B^Q t_kl B^Q
         L = self.ladder(t)
-        M += sym(-np.einsum("klac,klbc->ab", t, L) + 0.5 * np.einsum("klac,klcb->ab", t, L))
+        M += sym(-np.einsum("klac,klbc->ab", t, L, optimize=True) + 0.5 * np.einsum("klac,klcb->ab", t, L, optimize=True))
         # vvvv with both lines on the integral: sum_cd [2 (ab|cd) - (ad|cb)] (2X - X')_cd
-        X = np.einsum("klce,klde->cd", t, t)
-        Xp = np.einsum("klce,kled->cd", t, t)
+        X = np.einsum("klce,klde->cd", t, t, optimize=True)
+        Xp = np.einsum("klce,kled->cd", t, t, optimize=True)
         Z = 2.0 * X - Xp
-        M += 2.0 * np.einsum("Qab,Qcd,cd->ab", Bvv, Bvv, Z) - np.einsum("Qad,cd,Qcb->ab", Bvv, Z, Bvv)
+        M += 2.0 * np.einsum("Qab,Qcd,cd->ab", Bvv, Bvv, Z, optimize=True) - np.einsum("Qad,cd,Qcb->ab", Bvv, Z, Bvv, optimize=True)
         # ring with one open line on each amplitude / on the integral
         oovv = self.oovv  # (kl|db) -> oovv[k,l,d,b]
         Y5 = (
-            -0.5 * np.einsum("kmac,kldb,lmcd->ab", t, oovv, t)
-            + 1.0 * np.einsum("kmac,kldb,lmdc->ab", t, oovv, t)
-            + 1.0 * np.einsum("kmac,kbld,lmcd->ab", t, ovov, t)
-            - 2.0 * np.einsum("kmac,kbld,lmdc->ab", t, ovov, t)
-            + 1.0 * np.einsum("kmca,kldb,lmcd->ab", t, oovv, t)
-            - 0.5 * np.einsum("kmca,kldb,lmdc->ab", t, oovv, t)
-            - 0.5 * np.einsum("kmca,kbld,lmcd->ab", t, ovov, t)
-            + 1.0 * np.einsum("kmca,kbld,lmdc->ab", t, ovov, t)
+            -0.5 * np.einsum("kmac,kldb,lmcd->ab", t, oovv, t, optimize=True)
+            + 1.0 * np.einsum("kmac,kldb,lmdc->ab", t, oovv, t, optimize=True)
+            + 1.0 * np.einsum("kmac,kbld,lmcd->ab", t, ovov, t, optimize=True)
+            - 2.0 * np.einsum("kmac,kbld,lmdc->ab", t, ovov, t, optimize=True)
+            + 1.0 * np.einsum("kmca,kldb,lmcd->ab", t, oovv, t, optimize=True)
+            - 0.5 * np.einsum("kmca,kldb,lmdc->ab", t, oovv, t, optimize=True)
+            - 0.5 * np.einsum("kmca,kbld,lmcd->ab", t, ovov, t, optimize=True)
+            + 1.0 * np.einsum("kmca,kbld,lmdc->ab", t, ovov, t, optimize=True)
         )
         M += sym(Y5)
         # ring with both lines on the integral: -sum_kl [2 (kl|ab) - (kb|la)] (2U - U')_kl
-        U = np.einsum("kmcd,lmcd->kl", t, t)
-        Up = np.einsum("kmcd,lmdc->kl", t, t)
+        U = np.einsum("kmcd,lmcd->kl", t, t, optimize=True)
+        Up = np.einsum("kmcd,lmdc->kl", t, t, optimize=True)
         V = 2.0 * U - Up
-        M -= 2.0 * np.einsum("klab,kl->ab", oovv, V) - np.einsum("kbla,kl->ab", ovov, V)
+        M -= 2.0 * np.einsum("klab,kl->ab", oovv, V, optimize=True) - np.einsum("kbla,kl->ab", ovov, V, optimize=True)
         return M
 
     def _m11_ip(self):
@@ -163,41 +170,41 @@ class SpinAdaptedADC:
             return X + X.T
 
         # second order: sum t_il^cd [(jc|ld) - 1/2 (jd|lc)] + (i<->j)
-        M += sym(np.einsum("ilcd,jcld->ij", t, ovov) - 0.5 * np.einsum("ilcd,jdlc->ij", t, ovov))
+        M += sym(np.einsum("ilcd,jcld->ij", t, ovov, optimize=True) - 0.5 * np.einsum("ilcd,jdlc->ij", t, ovov, optimize=True))
         if self.order < 3:
             return M
         t2, t1 = self.t_2, self.t1_2
         oooo, oovv, ooov = self.oooo, self.oovv, self.ooov
         # t1(2): sum_kc t_k^c [2 (ck|ij) - (cj|ik)] + (i<->j)
-        K1 = 2.0 * np.einsum("kc,ijkc->ij", t1, ooov) - np.einsum("kc,ikjc->ij", t1, ooov)
+        K1 = 2.0 * np.einsum("kc,ijkc->ij", t1, ooov, optimize=True) - np.einsum("kc,ikjc->ij", t1, ooov, optimize=True)
         M += sym(K1)
         # t2(2): sum t2_ik^cd [(cj|dk) - 1/2 (ck|dj)] + (i<->j)
-        M += sym(np.einsum("ikcd,jckd->ij", t2, ovov) - 0.5 * np.einsum("ikcd,kcjd->ij", t2, ovov))
+        M += sym(np.einsum("ikcd,jckd->ij", t2, ovov, optimize=True) - 0.5 * np.einsum("ikcd,kcjd->ij", t2, ovov, optimize=True))
         # oooo with one open line: sum t_ik^cd (jl|km) [t_lm^cd - 1/2 t_lm^dc] + (i<->j)
         tau_h = t - 0.5 * t.transpose(0, 1, 3, 2)
-        M += sym(np.einsum("ikcd,jlkm,lmcd->ij", t, oooo, tau_h))
+        M += sym(np.einsum("ikcd,jlkm,lmcd->ij", t, oooo, tau_h, optimize=True))
         # oooo both lines on the integral: -[2 (ij|kl) - (il|kj)] (2U - U')_kl
-        U = np.einsum("kmcd,lmcd->kl", t, t)
-        Up = np.einsum("kmcd,lmdc->kl", t, t)
+        U = np.einsum("kmcd,lmcd->kl", t, t, optimize=True)
+        Up = np.einsum("kmcd,lmdc->kl", t, t, optimize=True)
         V = 2.0 * U - Up
-        M -= 2.0 * np.einsum("ijkl,kl->ij", oooo, V) - np.einsum("ilkj,kl->ij", oooo, V)
+        M -= 2.0 * np.einsum("ijkl,kl->ij", oooo, V, optimize=True) - np.einsum("ilkj,kl->ij", oooo, V, optimize=True)
         # ring with open lines on the amplitudes: integrals (cd|lj) = oovv[l,j,c,d], (cj|ld) = ovov[j,c,l,d]
         Y5 = (
-            0.5 * np.einsum("ikce,ljcd,klde->ij", t, oovv, t)
-            - 1.0 * np.einsum("ikce,ljcd,kled->ij", t, oovv, t)
-            - 1.0 * np.einsum("ikce,jcld,klde->ij", t, ovov, t)
-            + 2.0 * np.einsum("ikce,jcld,kled->ij", t, ovov, t)
-            - 1.0 * np.einsum("ikec,ljcd,klde->ij", t, oovv, t)
-            + 0.5 * np.einsum("ikec,ljcd,kled->ij", t, oovv, t)
-            + 0.5 * np.einsum("ikec,jcld,klde->ij", t, ovov, t)
-            - 1.0 * np.einsum("ikec,jcld,kled->ij", t, ovov, t)
+            0.5 * np.einsum("ikce,ljcd,klde->ij", t, oovv, t, optimize=True)
+            - 1.0 * np.einsum("ikce,ljcd,kled->ij", t, oovv, t, optimize=True)
+            - 1.0 * np.einsum("ikce,jcld,klde->ij", t, ovov, t, optimize=True)
+            + 2.0 * np.einsum("ikce,jcld,kled->ij", t, ovov, t, optimize=True)
+            - 1.0 * np.einsum("ikec,ljcd,klde->ij", t, oovv, t, optimize=True)
+            + 0.5 * np.einsum("ikec,ljcd,kled->ij", t, oovv, t, optimize=True)
+            + 0.5 * np.einsum("ikec,jcld,klde->ij", t, ovov, t, optimize=True)
+            - 1.0 * np.einsum("ikec,jcld,kled->ij", t, ovov, t, optimize=True)
         )
         M += sym(Y5)
         # ring both lines on the integral: [2 (cd|ij) - (cj|id)] (2X - X')_cd
-        X = np.einsum("klce,klde->cd", t, t)
-        Xp = np.einsum("klce,kled->cd", t, t)
+        X = np.einsum("klce,klde->cd", t, t, optimize=True)
+        Xp = np.einsum("klce,kled->cd", t, t, optimize=True)
         Z = 2.0 * X - Xp
-        M += 2.0 * np.einsum("ijcd,cd->ij", oovv, Z) - np.einsum("jcid,cd->ij", ovov, Z)
+        M += 2.0 * np.einsum("ijcd,cd->ij", oovv, Z, optimize=True) - np.einsum("jcid,cd->ij", ovov, Z, optimize=True)
         return M
 
     # ---- dimensions, metric, diagonal -------------------------------------

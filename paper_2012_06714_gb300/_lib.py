@@ -37,6 +37,7 @@ class Options(ctypes.Structure):
         ("nguess_extra", ctypes.c_int),
         ("res_tol", ctypes.c_double),
         ("aux_chunk", ctypes.c_int),
+        ("keep_per_root", ctypes.c_int),
     ]
 
 
@@ -100,7 +101,7 @@ class ADC:
     """
 
     def __init__(self, eps, B, nocc, order=3, kind="ea", precision="fp64", max_space_per_root=8, max_iter=100,
-                 nguess_extra=2, res_tol=0.0, aux_chunk=0):
+                 nguess_extra=2, res_tol=0.0, aux_chunk=0, keep_per_root=2):
         lib = load_library()
         self._lib = lib
         opt = Options()
@@ -111,6 +112,7 @@ class ADC:
         opt.nguess_extra = nguess_extra
         opt.res_tol = res_tol
         opt.aux_chunk = aux_chunk
+        opt.keep_per_root = keep_per_root
         if isinstance(eps, np.ndarray):
             eps = np.ascontiguousarray(eps, dtype=np.float64)
             B = np.ascontiguousarray(B, dtype=np.float64)

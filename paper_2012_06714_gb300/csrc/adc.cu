@@ -721,8 +721,8 @@ struct Davidson {
     // S-orthonormalise rows [first, first+count) of V against rows [0, first) and each other; returns kept count
     int orthonormalise(int first, int count) {
         Ctx& c = h->ctx;
+        Scope os(c.arena);
         int kept = 0;
-        std::vector<double> coef(first + count);
         double* cd = c.arena.dalloc(first + count);
         for (int r = 0; r < count; ++r) {
             double* x = V + (long long)(first + r) * dim;
@@ -757,7 +757,8 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
     const long long dim = h->dim();
     const int nextra = std::max(0, h->opt.nguess_extra);
     const int nstart = (int)std::min<long long>(dim, guess ? nroots : nroots + nextra);
-    const int maxspace = std::max(h->opt.max_space_per_root * nroots, nstart + nroots);
+    const int maxspace = std::max(h->opt.max_space_per_root * nroots,
+                                  std::max(nstart, std::max(1, h->opt.keep_per_root) * nroots) + nroots);
     const int cap = maxspace + nroots;
     const double rtol = h->opt.res_tol > 0 ? h->opt.res_tol : std::sqrt(tol);
     Scope sc(c.arena);
@@ -840,11 +841,21 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
         }
         int nnew = (int)todo.size();
         if (d.k + nnew > maxspace) {
-            // collapse onto the current Ritz vectors (sigma of them is AX)
-            ADC_CUDA(cudaMemcpyAsync(d.V, X, (size_t)nroots * dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
-            ADC_CUDA(cudaMemcpyAsync(d.W, AX, (size_t)nroots * dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
-            d.metric(d.V, d.SV, nroots, 0);
-            d.k = nroots;
+            // thick restart: collapse onto the lowest nkeep Ritz vectors (S-orthonormal); sigma follows linearly
+            const int nkeep = std::max(nroots, std::min(k, std::max(1, h->opt.keep_per_root) * nroots));
+            Scope rs(c.arena);
+            std::vector<double> Ck((size_t)nkeep * k);
+            for (int r = 0; r < nkeep; ++r)
+                for (int i = 0; i < k; ++i) Ck[(size_t)r * k + i] = C[(size_t)i * k + r];
+            double* Ckd = c.arena.dalloc((size_t)nkeep * k);
+            double* tmp = c.arena.dalloc((size_t)nkeep * dim);
+            ADC_CUDA(cudaMemcpyAsync(Ckd, Ck.data(), Ck.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+            gemm(c, false, false, nkeep, dim, k, 1.0, Ckd, k, 0, d.V, dim, 0, 0.0, tmp, dim, 0, 1);
+            ADC_CUDA(cudaMemcpyAsync(d.V, tmp, (size_t)nkeep * dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+            gemm(c, false, false, nkeep, dim, k, 1.0, Ckd, k, 0, d.W, dim, 0, 0.0, tmp, dim, 0, 1);
+            ADC_CUDA(cudaMemcpyAsync(d.W, tmp, (size_t)nkeep * dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+            d.metric(d.V, d.SV, nkeep, 0);
+            d.k = nkeep;
         }
         // corrections for unconverged roots
         std::vector<double> wt(nnew);
@@ -987,6 +998,7 @@ int adc_default_options(adc_options* opt) {
     opt->nguess_extra = 2;
     opt->res_tol = 0.0;
     opt->aux_chunk = 0;
+    opt->keep_per_root = 2;
     return ADC_OK;
 }
 

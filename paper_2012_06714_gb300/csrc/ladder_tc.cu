@@ -28,12 +28,14 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BK = 64;  // 64 BF16 = 128 bytes = one 128B-swizzle row
-constexpr int STAGES = 2;
+constexpr int MAX_STAGES = 4;
 constexpr int THREADS = 192;  // warp 0: TMA, warp 1: MMA + TMEM owner, warps 2-5: epilogue
-constexpr int TMEM_COLS = 256;
+constexpr int TMEM_COLS = 512;  // two accumulators of up to 256 FP32 columns
 constexpr int MAX_BN = 256;
 constexpr int A_BYTES = BM * BK * 2;
-constexpr size_t SMEM_BYTES = (size_t)STAGES * (2 * A_BYTES + 2 * MAX_BN * BK * 2) + 1024;
+// Always request (nearly) all of shared memory so that exactly one CTA, and one
+// 512-column TMEM allocation, lives on each SM.
+constexpr size_t SMEM_BYTES = 226 * 1024;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // bounded waits: 2 s
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -128,28 +130,40 @@ struct Epi {
     int* err;
 };
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+
+// Persistent GEMM C = A B^T with split-BF16 operands (three products per K step)
+// and a double-buffered TMEM accumulator.  Roles: warp 0 lane 0 issues TMA
+// loads through a ring of `stages` shared-memory stages, running ahead across
+// tiles; warp 1 owns TMEM and its lane 0 issues the MMAs; warps 2-5 drain the
+// accumulator of tile j while the MMAs of tile j+1 run into the other buffer.
 __global__ void __launch_bounds__(THREADS, 1)
     k_gemm_bf16x3(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                   const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, int a_row0, int b_x0,
-                  int K, int BN, int m_fastest, Epi ep) {
+                  int K, int BN, int stages, int m_fastest, int mt, int nt, Epi ep) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], acc_bar;
+    __shared__ uint64_t full_bar[MAX_STAGES], empty_bar[MAX_STAGES], tfull[2], tempty[2], done_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m_tile = m_fastest ? blockIdx.x : blockIdx.y;
-    const int n_tile = m_fastest ? blockIdx.y : blockIdx.x;
     const int num_k = (K + BK - 1) / BK;
     const int B_BYTES = BN * BK * 2;
     const int STAGE = 2 * A_BYTES + 2 * B_BYTES;
+    const int ntiles = mt * nt;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < stages; ++s) {
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
-        mbar_init(&acc_bar, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);  // one arrival per epilogue warp
+        }
+        mbar_init(&done_bar, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -165,24 +179,28 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            int issued = 0;
-            for (int kb = 0; kb < num_k; ++kb) {
-                const int s = kb % STAGES;
-                if (kb >= STAGES && !mbar_wait(&empty_bar[s], ((kb / STAGES) & 1) ^ 1, &abort_flag, ep.err)) break;
-                uint8_t* st = smem + (size_t)s * STAGE;
-                mbar_expect_tx(&full_bar[s], STAGE);
-                const int kx = kb * BK;
-                tma_load_2d(st, &mAh, &full_bar[s], kx, a_row0 + m_tile * BM);
-                tma_load_2d(st + A_BYTES, &mAl, &full_bar[s], kx, a_row0 + m_tile * BM);
-                tma_load_2d(st + 2 * A_BYTES, &mBh, &full_bar[s], b_x0 + kx, n_tile * BN);
-                tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mBl, &full_bar[s], b_x0 + kx, n_tile * BN);
-                ++issued;
+            long long g = 0;
+            for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x) {
+                const int m_tile = m_fastest ? t % mt : t / nt;
+                const int n_tile = m_fastest ? t / mt : t % nt;
+                for (int kb = 0; kb < num_k; ++kb, ++g) {
+                    const int s = (int)(g % stages);
+                    const uint32_t ph = (uint32_t)((g / stages) & 1);
+                    if (g >= stages && !mbar_wait(&empty_bar[s], ph ^ 1, &abort_flag, ep.err)) break;
+                    uint8_t* st = smem + (size_t)s * STAGE;
+                    mbar_expect_tx(&full_bar[s], STAGE);
+                    const int kx = kb * BK;
+                    tma_load_2d(st, &mAh, &full_bar[s], kx, a_row0 + m_tile * BM);
+                    tma_load_2d(st + A_BYTES, &mAl, &full_bar[s], kx, a_row0 + m_tile * BM);
+                    tma_load_2d(st + 2 * A_BYTES, &mBh, &full_bar[s], b_x0 + kx, n_tile * BN);
+                    tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mBl, &full_bar[s], b_x0 + kx, n_tile * BN);
+                }
             }
             if (abort_flag) {
-                // let copies already in flight land before the CTA retires (bounded)
-                for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb) {
+                // let the copies of the last `stages` issues land before the CTA retires (bounded)
+                for (long long q = (g > stages ? g - stages : 0); q < g; ++q) {
                     const uint64_t t0 = gtime();
-                    while (!mbar_try(&full_bar[kb % STAGES], (kb / STAGES) & 1) && gtime() - t0 < WAIT_NS) {
+                    while (!mbar_try(&full_bar[q % stages], (uint32_t)((q / stages) & 1)) && gtime() - t0 < WAIT_NS) {
                     }
                 }
             }
@@ -190,32 +208,50 @@ __global__ void __launch_bounds__(THREADS, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-            for (int kb = 0; kb < num_k; ++kb) {
-                const int s = kb % STAGES;
-                if (!mbar_wait(&full_bar[s], (kb / STAGES) & 1, &abort_flag, ep.err)) break;
+            long long g = 0;
+            int j = 0;
+            for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x, ++j) {
+                const int b = j & 1;
+                if (j >= 2 && !mbar_wait(&tempty[b], (uint32_t)(((j >> 1) & 1) ^ 1), &abort_flag, ep.err)) break;
                 fence_after();
-                uint8_t* st = smem + (size_t)s * STAGE;
-                const uint64_t ah = smem_desc(st), al = smem_desc(st + A_BYTES);
-                const uint64_t bh = smem_desc(st + 2 * A_BYTES), bl = smem_desc(st + 2 * A_BYTES + B_BYTES);
+                const uint32_t tacc = tmem + (uint32_t)(b * 256);
+                bool ok = true;
+                for (int kb = 0; kb < num_k; ++kb, ++g) {
+                    const int s = (int)(g % stages);
+                    if (!mbar_wait(&full_bar[s], (uint32_t)((g / stages) & 1), &abort_flag, ep.err)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    uint8_t* st = smem + (size_t)s * STAGE;
+                    const uint64_t ah = smem_desc(st), al = smem_desc(st + A_BYTES);
+                    const uint64_t bh = smem_desc(st + 2 * A_BYTES), bl = smem_desc(st + 2 * A_BYTES + B_BYTES);
 #pragma unroll
-                for (int kk = 0; kk < BK / 16; ++kk) {
-                    const uint64_t o = (uint64_t)(kk * 2);  // 16 BF16 = 32 bytes along K
-                    mma_bf16(tmem, ah + o, bh + o, idesc, (kb | kk) != 0);
-                    mma_bf16(tmem, ah + o, bl + o, idesc, 1u);
-                    mma_bf16(tmem, al + o, bh + o, idesc, 1u);
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint64_t o = (uint64_t)(kk * 2);  // 16 BF16 = 32 bytes along K
+                        mma_bf16(tacc, ah + o, bh + o, idesc, (kb | kk) != 0);
+                        mma_bf16(tacc, ah + o, bl + o, idesc, 1u);
+                        mma_bf16(tacc, al + o, bh + o, idesc, 1u);
+                    }
+                    mma_commit(&empty_bar[s]);
                 }
-                mma_commit(&empty_bar[s]);
+                if (!ok) break;
+                mma_commit(&tfull[b]);
             }
-            mma_commit(&acc_bar);  // tracks every MMA issued above, also after an abort
+            mma_commit(&done_bar);  // fires when every MMA issued above has completed
         }
     } else {
         // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (one accumulator row per thread)
-        const bool ok = mbar_wait(&acc_bar, 0, &abort_flag, ep.err);
-        fence_after();
-        if (ok) {
-            const int quarter = warp & 3;
+        const int quarter = warp & 3;
+        int j = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+            const int b = j & 1;
+            if (!mbar_wait(&tfull[b], (uint32_t)((j >> 1) & 1), &abort_flag, ep.err)) break;
+            fence_after();
+            const int m_tile = m_fastest ? t % mt : t / nt;
+            const int n_tile = m_fastest ? t / mt : t % nt;
             const int row = m_tile * BM + quarter * 32 + lane;
-            const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16);
+            const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
             for (int c0 = 0; c0 < BN; c0 += 16) {
                 float v[16];
                 tmem_ld16(tbase + (uint32_t)c0, v);
@@ -244,16 +280,16 @@ __global__ void __launch_bounds__(THREADS, 1)
                         if (col0 + i < ep.N) o[i] += (double)v[i];
                 }
             }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
         }
     }
     fence_before();
     __syncthreads();
     if (warp == 1) {
-        // every MMA has completed once acc_bar has fired; wait (bounded) if we aborted early
-        if (abort_flag) {
-            const uint64_t t0 = gtime();
-            while (!mbar_try(&acc_bar, 0) && gtime() - t0 < WAIT_NS) {
-            }
+        const uint64_t t0 = gtime();
+        while (!mbar_try(&done_bar, 0) && gtime() - t0 < WAIT_NS) {
         }
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
@@ -354,20 +390,30 @@ int pick_bn(int n) {
 void launch_gemm(Ctx& c, const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh, const CUtensorMap& bl,
                  int a_row0, int b_x0, int M, int N, int K, int BN, int m_fastest, const Epi& ep, double algo_flops) {
     static bool attr = false;
+    static int num_sms = 0;
     if (!attr) {
         ADC_CUDA(cudaFuncSetAttribute(k_gemm_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+        int dev = 0;
+        ADC_CUDA(cudaGetDevice(&dev));
+        ADC_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
         attr = true;
     }
     const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
-    dim3 grid = m_fastest ? dim3(mt, nt) : dim3(nt, mt);
-    if (grid.y > 65535) throw Error(-1, "ladder: tile grid too large");
+    const long long ntiles = (long long)mt * nt;
+    if (ntiles <= 0) return;
+    if (ntiles > (1LL << 31) - 1) throw Error(-1, "ladder: tile count too large");
+    const int stage_bytes = 2 * A_BYTES + 2 * BN * BK * 2;
+    const int stages = std::min(MAX_STAGES, (int)((SMEM_BYTES - 1024) / stage_bytes));
+    if (stages < 2) throw Error(-1, "ladder: tile too large for shared memory");
+    const int grid = (int)std::min<long long>(ntiles, num_sms);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (c.timing) {
         ADC_CUDA(cudaEventCreate(&e0));
         ADC_CUDA(cudaEventCreate(&e1));
         ADC_CUDA(cudaEventRecord(e0, c.stream));
     }
-    k_gemm_bf16x3<<<grid, THREADS, SMEM_BYTES, c.stream>>>(ah, al, bh, bl, a_row0, b_x0, K, BN, m_fastest, ep);
+    k_gemm_bf16x3<<<grid, THREADS, SMEM_BYTES, c.stream>>>(ah, al, bh, bl, a_row0, b_x0, K, BN, stages, m_fastest, mt, nt,
+                                                           ep);
     ++c.kernels;
     ADC_CUDA(cudaGetLastError());
     if (c.timing) {
