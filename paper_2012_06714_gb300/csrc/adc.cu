@@ -209,7 +209,9 @@ struct Scope {
     ~Scope() { a.release(m); }
 };
 
-T tn(const double* p, std::initializer_list<long long> d) { return T{p, std::vector<long long>(d)}; }
+T tn(const double* p, std::initializer_list<long long> d) { return T{p, std::vector<long long>(d), false}; }
+// handle-owned tensor that never changes after setup (its FP32 operand copy may be cached)
+T tc(const double* p, std::initializer_list<long long> d) { return T{p, std::vector<long long>(d), true}; }
 
 }  // namespace
 
@@ -499,12 +501,12 @@ static void sigma_ea(adc_handle* h, const double* Xin, double* Sout, long long n
     einsum(c, "nb,ab->na", 1.0, tn(y1, {n, v}), tn(h->M11, {v, v}), 0.0, s1, {n, v});
     // coupling row, first order: sum (ad|jc) Y~_jcd
     double* Wq = c.arena.dalloc(n * Q * v);
-    einsum(c, "Qjc,njcd->nQd", 1.0, tn(h->Bov, {Q, o, v}), tn(Yt, {n, o, v, v}), 0.0, Wq, {n, Q, v});
-    einsum(c, "nQd,Qda->na", 1.0, tn(Wq, {n, Q, v}), tn(h->Bvv, {Q, v, v}), 1.0, s1, {n, v});
+    einsum(c, "Qjc,njcd->nQd", 1.0, tc(h->Bov, {Q, o, v}), tn(Yt, {n, o, v, v}), 0.0, Wq, {n, Q, v});
+    einsum(c, "nQd,Qda->na", 1.0, tn(Wq, {n, Q, v}), tc(h->Bvv, {Q, v, v}), 1.0, s1, {n, v});
     // 2p1h column, first order: (cb|ia) Y_c
     double* hq = c.arena.dalloc(n * Q * v);
-    einsum(c, "nc,Qcb->nQb", 1.0, tn(y1, {n, v}), tn(h->Bvv, {Q, v, v}), 0.0, hq, {n, Q, v});
-    einsum(c, "Qia,nQb->niab", 1.0, tn(h->Bov, {Q, o, v}), tn(hq, {n, Q, v}), 0.0, S2, {n, o, v, v});
+    einsum(c, "nc,Qcb->nQb", 1.0, tn(y1, {n, v}), tc(h->Bvv, {Q, v, v}), 0.0, hq, {n, Q, v});
+    einsum(c, "Qia,nQb->niab", 1.0, tc(h->Bov, {Q, o, v}), tn(hq, {n, Q, v}), 0.0, S2, {n, o, v, v});
     // 2p1h block, zeroth order
     k_diag22<<<grid_for(n * blk), 256, 0, c.stream>>>(1, (int)o, (int)v, n, h->eps, Y2, S2);
     launch_check(c);
@@ -513,43 +515,43 @@ static void sigma_ea(adc_handle* h, const double* Xin, double* Sout, long long n
         // coupling row, second order:
         //  sum (al|jm) t_lm^dc Y~_jcd
         double* Z = c.arena.dalloc(n * o * o * o);
-        einsum(c, "lmdc,njcd->nlmj", 1.0, tn(t, {o, o, v, v}), tn(Yt, {n, o, v, v}), 0.0, Z, {n, o, o, o});
+        einsum(c, "lmdc,njcd->nlmj", 1.0, tc(t, {o, o, v, v}), tn(Yt, {n, o, v, v}), 0.0, Z, {n, o, o, o});
         double* P = c.arena.dalloc(n * Q * o);
-        einsum(c, "Qjm,nlmj->nQl", 1.0, tn(h->Boo, {Q, o, o}), tn(Z, {n, o, o, o}), 0.0, P, {n, Q, o});
-        einsum(c, "nQl,Qla->na", 1.0, tn(P, {n, Q, o}), tn(h->Bov, {Q, o, v}), 1.0, s1, {n, v});
+        einsum(c, "Qjm,nlmj->nQl", 1.0, tc(h->Boo, {Q, o, o}), tn(Z, {n, o, o, o}), 0.0, P, {n, Q, o});
+        einsum(c, "nQl,Qla->na", 1.0, tn(P, {n, Q, o}), tc(h->Bov, {Q, o, v}), 1.0, s1, {n, v});
         //  sum (ad|em)(2 t_jm^ce - t_jm^ec) Y~_jcd
         double* V = c.arena.dalloc(n * o * v * v);
-        einsum(c, "jmce,njcd->nmed", 1.0, tn(tau, {o, o, v, v}), tn(Yt, {n, o, v, v}), 0.0, V, {n, o, v, v});
-        einsum(c, "nmed,Qme->nQd", 1.0, tn(V, {n, o, v, v}), tn(h->Bov, {Q, o, v}), 0.0, Wq, {n, Q, v});
-        einsum(c, "nQd,Qda->na", 1.0, tn(Wq, {n, Q, v}), tn(h->Bvv, {Q, v, v}), 1.0, s1, {n, v});
+        einsum(c, "jmce,njcd->nmed", 1.0, tc(tau, {o, o, v, v}), tn(Yt, {n, o, v, v}), 0.0, V, {n, o, v, v});
+        einsum(c, "nmed,Qme->nQd", 1.0, tn(V, {n, o, v, v}), tc(h->Bov, {Q, o, v}), 0.0, Wq, {n, Q, v});
+        einsum(c, "nQd,Qda->na", 1.0, tn(Wq, {n, Q, v}), tc(h->Bvv, {Q, v, v}), 1.0, s1, {n, v});
         //  - sum (am|ed) [t_jm^ce Y~_jcd + t_jm^ed Y~_jdc]   (the two exchange-type terms)
-        einsum(c, "jmce,njcd->nmed", 1.0, tn(t, {o, o, v, v}), tn(Yt, {n, o, v, v}), 0.0, V, {n, o, v, v});
-        einsum(c, "jmec,njdc->nmed", 1.0, tn(t, {o, o, v, v}), tn(Yt, {n, o, v, v}), 1.0, V, {n, o, v, v});
+        einsum(c, "jmce,njcd->nmed", 1.0, tc(t, {o, o, v, v}), tn(Yt, {n, o, v, v}), 0.0, V, {n, o, v, v});
+        einsum(c, "jmec,njdc->nmed", 1.0, tc(t, {o, o, v, v}), tn(Yt, {n, o, v, v}), 1.0, V, {n, o, v, v});
         double* R = c.arena.dalloc(n * Q * o);
-        einsum(c, "nmed,Qed->nQm", 1.0, tn(V, {n, o, v, v}), tn(h->Bvv, {Q, v, v}), 0.0, R, {n, Q, o});
-        einsum(c, "nQm,Qma->na", -1.0, tn(R, {n, Q, o}), tn(h->Bov, {Q, o, v}), 1.0, s1, {n, v});
+        einsum(c, "nmed,Qed->nQm", 1.0, tn(V, {n, o, v, v}), tc(h->Bvv, {Q, v, v}), 0.0, R, {n, Q, o});
+        einsum(c, "nQm,Qma->na", -1.0, tn(R, {n, Q, o}), tc(h->Bov, {Q, o, v}), 1.0, s1, {n, v});
         // 2p1h column, second order:
         //  sum_lm (cl|im) t_lm^ba Y_c
         double* p = c.arena.dalloc(n * Q * o);
-        einsum(c, "nc,Qlc->nQl", 1.0, tn(y1, {n, v}), tn(h->Bov, {Q, o, v}), 0.0, p, {n, Q, o});
+        einsum(c, "nc,Qlc->nQl", 1.0, tn(y1, {n, v}), tc(h->Bov, {Q, o, v}), 0.0, p, {n, Q, o});
         double* Pl = c.arena.dalloc(n * o * o * o);
-        einsum(c, "nQl,Qim->nlim", 1.0, tn(p, {n, Q, o}), tn(h->Boo, {Q, o, o}), 0.0, Pl, {n, o, o, o});
-        einsum(c, "nlim,lmba->niab", 1.0, tn(Pl, {n, o, o, o}), tn(t, {o, o, v, v}), 1.0, S2, {n, o, v, v});
+        einsum(c, "nQl,Qim->nlim", 1.0, tn(p, {n, Q, o}), tc(h->Boo, {Q, o, o}), 0.0, Pl, {n, o, o, o});
+        einsum(c, "nlim,lmba->niab", 1.0, tn(Pl, {n, o, o, o}), tc(t, {o, o, v, v}), 1.0, S2, {n, o, v, v});
         //  sum_me (cb|em)(2 t_im^ae - t_im^ea) Y_c
         double* q = c.arena.dalloc(n * o * v * v);
-        einsum(c, "nQb,Qme->nbme", 1.0, tn(hq, {n, Q, v}), tn(h->Bov, {Q, o, v}), 0.0, q, {n, v, o, v});
-        einsum(c, "nbme,imae->niab", 1.0, tn(q, {n, v, o, v}), tn(tau, {o, o, v, v}), 1.0, S2, {n, o, v, v});
+        einsum(c, "nQb,Qme->nbme", 1.0, tn(hq, {n, Q, v}), tc(h->Bov, {Q, o, v}), 0.0, q, {n, v, o, v});
+        einsum(c, "nbme,imae->niab", 1.0, tn(q, {n, v, o, v}), tc(tau, {o, o, v, v}), 1.0, S2, {n, o, v, v});
         //  - sum_me (cm|eb) t_im^ae Y_c - sum_me (cm|ea) t_im^eb Y_c
-        einsum(c, "nQm,Qeb->nmeb", 1.0, tn(p, {n, Q, o}), tn(h->Bvv, {Q, v, v}), 0.0, q, {n, o, v, v});
-        einsum(c, "nmeb,imae->niab", -1.0, tn(q, {n, o, v, v}), tn(t, {o, o, v, v}), 1.0, S2, {n, o, v, v});
-        einsum(c, "nmea,imeb->niab", -1.0, tn(q, {n, o, v, v}), tn(t, {o, o, v, v}), 1.0, S2, {n, o, v, v});
+        einsum(c, "nQm,Qeb->nmeb", 1.0, tn(p, {n, Q, o}), tc(h->Bvv, {Q, v, v}), 0.0, q, {n, o, v, v});
+        einsum(c, "nmeb,imae->niab", -1.0, tn(q, {n, o, v, v}), tc(t, {o, o, v, v}), 1.0, S2, {n, o, v, v});
+        einsum(c, "nmea,imeb->niab", -1.0, tn(q, {n, o, v, v}), tc(t, {o, o, v, v}), 1.0, S2, {n, o, v, v});
         // 2p1h block, first order: ladder sum_cd (ac|bd) Y_icd (vvvv never stored)
         ladder(h, Y2, n * o, S2);
         //  - (ac|ji) Y_jcb + 2 (ai|jc) Y_jcb - (ai|jc) Y_jbc - (bd|ji) Y_jad
-        einsum(c, "jiac,njcb->niab", -1.0, tn(h->oovv, {o, o, v, v}), tn(Y2, {n, o, v, v}), 1.0, S2, {n, o, v, v});
-        einsum(c, "iajc,njcb->niab", 2.0, tn(h->ovov, {o, v, o, v}), tn(Y2, {n, o, v, v}), 1.0, S2, {n, o, v, v});
-        einsum(c, "iajc,njbc->niab", -1.0, tn(h->ovov, {o, v, o, v}), tn(Y2, {n, o, v, v}), 1.0, S2, {n, o, v, v});
-        einsum(c, "jibd,njad->niab", -1.0, tn(h->oovv, {o, o, v, v}), tn(Y2, {n, o, v, v}), 1.0, S2, {n, o, v, v});
+        einsum(c, "jiac,njcb->niab", -1.0, tc(h->oovv, {o, o, v, v}), tn(Y2, {n, o, v, v}), 1.0, S2, {n, o, v, v});
+        einsum(c, "iajc,njcb->niab", 2.0, tc(h->ovov, {o, v, o, v}), tn(Y2, {n, o, v, v}), 1.0, S2, {n, o, v, v});
+        einsum(c, "iajc,njbc->niab", -1.0, tc(h->ovov, {o, v, o, v}), tn(Y2, {n, o, v, v}), 1.0, S2, {n, o, v, v});
+        einsum(c, "jibd,njad->niab", -1.0, tc(h->oovv, {o, o, v, v}), tn(Y2, {n, o, v, v}), 1.0, S2, {n, o, v, v});
     }
     k_gather<<<grid_for(n * v), 256, 0, c.stream>>>(n, v, s1, v, 0, Sout, dim, 0, 0.0);
     launch_check(c);
@@ -575,12 +577,12 @@ static void sigma_ip(adc_handle* h, const double* Xin, double* Sout, long long n
     launch_check(c);
     // coupling row, first order: -(ki|ja) Y~_jka
     double* G = c.arena.dalloc(n * Q * o);
-    einsum(c, "Qja,njka->nQk", 1.0, tn(h->Bov, {Q, o, v}), tn(Yt, {n, o, o, v}), 0.0, G, {n, Q, o});
-    einsum(c, "nQk,Qki->ni", -1.0, tn(G, {n, Q, o}), tn(h->Boo, {Q, o, o}), 0.0, s1, {n, o});
+    einsum(c, "Qja,njka->nQk", 1.0, tc(h->Bov, {Q, o, v}), tn(Yt, {n, o, o, v}), 0.0, G, {n, Q, o});
+    einsum(c, "nQk,Qki->ni", -1.0, tn(G, {n, Q, o}), tc(h->Boo, {Q, o, o}), 0.0, s1, {n, o});
     // 2h1p column, first order: -(ki|ja) Y_i
     double* g = c.arena.dalloc(n * Q * o);
-    einsum(c, "ni,Qki->nQk", 1.0, tn(y1, {n, o}), tn(h->Boo, {Q, o, o}), 0.0, g, {n, Q, o});
-    einsum(c, "nQk,Qja->njka", -1.0, tn(g, {n, Q, o}), tn(h->Bov, {Q, o, v}), 0.0, S2, {n, o, o, v});
+    einsum(c, "ni,Qki->nQk", 1.0, tn(y1, {n, o}), tc(h->Boo, {Q, o, o}), 0.0, g, {n, Q, o});
+    einsum(c, "nQk,Qja->njka", -1.0, tn(g, {n, Q, o}), tc(h->Bov, {Q, o, v}), 0.0, S2, {n, o, o, v});
     k_diag22<<<grid_for(n * blk), 256, 0, c.stream>>>(0, (int)o, (int)v, n, h->eps, Y2, S2);
     launch_check(c);
     if (h->order >= 3) {
@@ -588,37 +590,37 @@ static void sigma_ip(adc_handle* h, const double* Xin, double* Sout, long long n
         // coupling row, second order
         //  - sum (ad|ie) t_jk^de Y~_jka
         double* Z = c.arena.dalloc(n * v * v * v);
-        einsum(c, "jkde,njka->ndea", 1.0, tn(t, {o, o, v, v}), tn(Yt, {n, o, o, v}), 0.0, Z, {n, v, v, v});
+        einsum(c, "jkde,njka->ndea", 1.0, tc(t, {o, o, v, v}), tn(Yt, {n, o, o, v}), 0.0, Z, {n, v, v, v});
         double* Hq = c.arena.dalloc(n * Q * v);
-        einsum(c, "ndea,Qad->nQe", 1.0, tn(Z, {n, v, v, v}), tn(h->Bvv, {Q, v, v}), 0.0, Hq, {n, Q, v});
-        einsum(c, "nQe,Qie->ni", -1.0, tn(Hq, {n, Q, v}), tn(h->Bov, {Q, o, v}), 1.0, s1, {n, o});
+        einsum(c, "ndea,Qad->nQe", 1.0, tn(Z, {n, v, v, v}), tc(h->Bvv, {Q, v, v}), 0.0, Hq, {n, Q, v});
+        einsum(c, "nQe,Qie->ni", -1.0, tn(Hq, {n, Q, v}), tc(h->Bov, {Q, o, v}), 1.0, s1, {n, o});
         //  - sum (ik|lc)(2 t_jl^ac - t_jl^ca) Y~_jka + sum (ic|lk) t_jl^ac Y~_jka + sum (ic|lj) t_kl^ca Y~_jka
         double* G2 = c.arena.dalloc(n * o * o * v);
-        einsum(c, "jlac,njka->nklc", 1.0, tn(tau, {o, o, v, v}), tn(Yt, {n, o, o, v}), 0.0, G2, {n, o, o, v});
-        einsum(c, "iklc,nklc->ni", -1.0, tn(h->ooov, {o, o, o, v}), tn(G2, {n, o, o, v}), 1.0, s1, {n, o});
-        einsum(c, "jlac,njka->nlkc", 1.0, tn(t, {o, o, v, v}), tn(Yt, {n, o, o, v}), 0.0, G2, {n, o, o, v});
-        einsum(c, "lkic,nlkc->ni", 1.0, tn(h->ooov, {o, o, o, v}), tn(G2, {n, o, o, v}), 1.0, s1, {n, o});
-        einsum(c, "klca,njka->nljc", 1.0, tn(t, {o, o, v, v}), tn(Yt, {n, o, o, v}), 0.0, G2, {n, o, o, v});
-        einsum(c, "ljic,nljc->ni", 1.0, tn(h->ooov, {o, o, o, v}), tn(G2, {n, o, o, v}), 1.0, s1, {n, o});
+        einsum(c, "jlac,njka->nklc", 1.0, tc(tau, {o, o, v, v}), tn(Yt, {n, o, o, v}), 0.0, G2, {n, o, o, v});
+        einsum(c, "iklc,nklc->ni", -1.0, tc(h->ooov, {o, o, o, v}), tn(G2, {n, o, o, v}), 1.0, s1, {n, o});
+        einsum(c, "jlac,njka->nlkc", 1.0, tc(t, {o, o, v, v}), tn(Yt, {n, o, o, v}), 0.0, G2, {n, o, o, v});
+        einsum(c, "lkic,nlkc->ni", 1.0, tc(h->ooov, {o, o, o, v}), tn(G2, {n, o, o, v}), 1.0, s1, {n, o});
+        einsum(c, "klca,njka->nljc", 1.0, tc(t, {o, o, v, v}), tn(Yt, {n, o, o, v}), 0.0, G2, {n, o, o, v});
+        einsum(c, "ljic,nljc->ni", 1.0, tc(h->ooov, {o, o, o, v}), tn(G2, {n, o, o, v}), 1.0, s1, {n, o});
         // 2h1p column, second order (same tensor, applied to Y_i)
         double* bq = c.arena.dalloc(n * Q * v);
-        einsum(c, "ni,Qie->nQe", 1.0, tn(y1, {n, o}), tn(h->Bov, {Q, o, v}), 0.0, bq, {n, Q, v});
+        einsum(c, "ni,Qie->nQe", 1.0, tn(y1, {n, o}), tc(h->Bov, {Q, o, v}), 0.0, bq, {n, Q, v});
         double* w = c.arena.dalloc(n * v * v * v);
-        einsum(c, "nQe,Qad->nead", 1.0, tn(bq, {n, Q, v}), tn(h->Bvv, {Q, v, v}), 0.0, w, {n, v, v, v});
-        einsum(c, "nead,jkde->njka", -1.0, tn(w, {n, v, v, v}), tn(t, {o, o, v, v}), 1.0, S2, {n, o, o, v});
+        einsum(c, "nQe,Qad->nead", 1.0, tn(bq, {n, Q, v}), tc(h->Bvv, {Q, v, v}), 0.0, w, {n, v, v, v});
+        einsum(c, "nead,jkde->njka", -1.0, tn(w, {n, v, v, v}), tc(t, {o, o, v, v}), 1.0, S2, {n, o, o, v});
         double* m = c.arena.dalloc(n * o * o * v);
-        einsum(c, "ni,iklc->nklc", 1.0, tn(y1, {n, o}), tn(h->ooov, {o, o, o, v}), 0.0, m, {n, o, o, v});
-        einsum(c, "nklc,jlac->njka", -1.0, tn(m, {n, o, o, v}), tn(tau, {o, o, v, v}), 1.0, S2, {n, o, o, v});
-        einsum(c, "ni,lkic->nlkc", 1.0, tn(y1, {n, o}), tn(h->ooov, {o, o, o, v}), 0.0, m, {n, o, o, v});
-        einsum(c, "nlkc,jlac->njka", 1.0, tn(m, {n, o, o, v}), tn(t, {o, o, v, v}), 1.0, S2, {n, o, o, v});
-        einsum(c, "ni,ljic->nljc", 1.0, tn(y1, {n, o}), tn(h->ooov, {o, o, o, v}), 0.0, m, {n, o, o, v});
-        einsum(c, "nljc,klca->njka", 1.0, tn(m, {n, o, o, v}), tn(t, {o, o, v, v}), 1.0, S2, {n, o, o, v});
+        einsum(c, "ni,iklc->nklc", 1.0, tn(y1, {n, o}), tc(h->ooov, {o, o, o, v}), 0.0, m, {n, o, o, v});
+        einsum(c, "nklc,jlac->njka", -1.0, tn(m, {n, o, o, v}), tc(tau, {o, o, v, v}), 1.0, S2, {n, o, o, v});
+        einsum(c, "ni,lkic->nlkc", 1.0, tn(y1, {n, o}), tc(h->ooov, {o, o, o, v}), 0.0, m, {n, o, o, v});
+        einsum(c, "nlkc,jlac->njka", 1.0, tn(m, {n, o, o, v}), tc(t, {o, o, v, v}), 1.0, S2, {n, o, o, v});
+        einsum(c, "ni,ljic->nljc", 1.0, tn(y1, {n, o}), tc(h->ooov, {o, o, o, v}), 0.0, m, {n, o, o, v});
+        einsum(c, "nljc,klca->njka", 1.0, tn(m, {n, o, o, v}), tc(t, {o, o, v, v}), 1.0, S2, {n, o, o, v});
         // 2h1p block, first order: -(ki|lj) Y_kla + (ki|ab) Y_kjb - 2 (ia|kb) Y_kjb + (ia|kb) Y_jkb + (kj|ab) Y_ikb
-        einsum(c, "kilj,nkla->nija", -1.0, tn(h->oooo, {o, o, o, o}), tn(Y2, {n, o, o, v}), 1.0, S2, {n, o, o, v});
-        einsum(c, "kiab,nkjb->nija", 1.0, tn(h->oovv, {o, o, v, v}), tn(Y2, {n, o, o, v}), 1.0, S2, {n, o, o, v});
-        einsum(c, "iakb,nkjb->nija", -2.0, tn(h->ovov, {o, v, o, v}), tn(Y2, {n, o, o, v}), 1.0, S2, {n, o, o, v});
-        einsum(c, "iakb,njkb->nija", 1.0, tn(h->ovov, {o, v, o, v}), tn(Y2, {n, o, o, v}), 1.0, S2, {n, o, o, v});
-        einsum(c, "kjab,nikb->nija", 1.0, tn(h->oovv, {o, o, v, v}), tn(Y2, {n, o, o, v}), 1.0, S2, {n, o, o, v});
+        einsum(c, "kilj,nkla->nija", -1.0, tc(h->oooo, {o, o, o, o}), tn(Y2, {n, o, o, v}), 1.0, S2, {n, o, o, v});
+        einsum(c, "kiab,nkjb->nija", 1.0, tc(h->oovv, {o, o, v, v}), tn(Y2, {n, o, o, v}), 1.0, S2, {n, o, o, v});
+        einsum(c, "iakb,nkjb->nija", -2.0, tc(h->ovov, {o, v, o, v}), tn(Y2, {n, o, o, v}), 1.0, S2, {n, o, o, v});
+        einsum(c, "iakb,njkb->nija", 1.0, tc(h->ovov, {o, v, o, v}), tn(Y2, {n, o, o, v}), 1.0, S2, {n, o, o, v});
+        einsum(c, "kjab,nikb->nija", 1.0, tc(h->oovv, {o, o, v, v}), tn(Y2, {n, o, o, v}), 1.0, S2, {n, o, o, v});
     }
     // negate (M_IP = -M_-) and add the 1h-1h block (already negated)
     einsum(c, "nj,ij->ni", 1.0, tn(y1, {n, o}), tn(h->M11, {o, o}), -1.0, s1, {n, o});

@@ -194,14 +194,14 @@ const double* to_order(Ctx& c, const double* src, const std::string& ls, const s
 static void einsum_fp32(Ctx& c, const std::string& la, const std::string& lb, const std::string& lc,
                         std::map<char, long long>& dim, const std::string& batch, const std::string& fa,
                         const std::string& fb, const std::string& con, double alpha, const double* Ap, const double* Bp,
-                        double beta, double* C) {
+                        double beta, double* C, bool constA, bool constB) {
     auto prod = [&](const std::string& l) {
         long long p = 1;
         for (char x : l) p *= dim[x];
         return p;
     };
     long long nb = prod(batch), M = prod(fa), N = prod(fb), K = prod(con);
-    auto conv = [&](const double* src, const std::string& ls, const std::string& lt) {
+    auto conv = [&](const double* src, const std::string& ls, const std::string& lt, bool constant) {
         Shape sh;
         sh.nd = (int)ls.size();
         long long n = 1;
@@ -210,13 +210,30 @@ static void einsum_fp32(Ctx& c, const std::string& la, const std::string& lb, co
             n *= sh.d[j];
         }
         int perm[kMaxDim];
-        for (int j = 0; j < sh.nd; ++j) perm[j] = (int)ls.find(lt[j]);
-        float* dst = (float*)c.arena.alloc(n * sizeof(float));
+        std::string key;
+        for (int j = 0; j < sh.nd; ++j) {
+            perm[j] = (int)ls.find(lt[j]);
+            key += (char)('0' + perm[j]);
+            key += ':';
+            key += std::to_string(sh.d[j]);
+            key += ',';
+        }
+        float* dst;
+        if (constant) {
+            auto it = c.f32cache.find({src, key});
+            if (it != c.f32cache.end()) return (const float*)it->second;
+            void* p = nullptr;
+            ADC_CUDA(cudaMalloc(&p, n * sizeof(float)));
+            dst = (float*)p;
+            c.f32cache[{src, key}] = dst;
+        } else {
+            dst = (float*)c.arena.alloc(n * sizeof(float));
+        }
         permute_cvt<double, float>(c, src, sh, perm, dst, 1.0, 0.0);
-        return dst;
+        return (const float*)dst;
     };
-    const float* A32 = conv(Ap, la, batch + fa + con);
-    const float* B32 = conv(Bp, lb, batch + con + fb);
+    const float* A32 = conv(Ap, la, batch + fa + con, constA);
+    const float* B32 = conv(Bp, lb, batch + con + fb, constB);
     float* T32 = (float*)c.arena.alloc(nb * M * N * sizeof(float));
     const float one = 1.0f, zero = 0.0f;
     // row-major T[M][N] = A[M][K] B[K][N]  <=>  column-major T^T = B^T A^T
@@ -291,7 +308,7 @@ void einsum(Ctx& c, const char* specstr, double alpha, const T& A, const T& B, d
     long long nb = prod(batch), M = prod(fa), N = prod(fb), K = prod(con);
     Arena::Mark mk = c.arena.mark();
     if (c.gemm_mode == 1 && 2.0 * nb * M * N * K >= c.fp32_min_flops) {
-        einsum_fp32(c, sp.a, sp.b, sp.c, dim, batch, fa, fb, con, alpha, A.p, B.p, beta, C);
+        einsum_fp32(c, sp.a, sp.b, sp.c, dim, batch, fa, fb, con, alpha, A.p, B.p, beta, C, A.constant, B.constant);
         c.arena.release(mk);
         return;
     }

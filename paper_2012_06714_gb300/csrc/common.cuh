@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -108,6 +109,13 @@ struct Ctx {
     std::vector<cudaEvent_t> ev_start, ev_stop;
     double algo_flops = 0.0, mma_flops = 0.0;
     long long kernels_at_start = 0;
+    // FP32 copies (in GEMM operand order) of operands marked constant, reused across calls
+    std::map<std::pair<const void*, std::string>, float*> f32cache;
+    ~Ctx() {
+        for (auto& kv : f32cache) cudaFree(kv.second);
+        for (auto e : ev_start) cudaEventDestroy(e);
+        for (auto e : ev_stop) cudaEventDestroy(e);
+    }
 };
 
 constexpr int kMaxDim = 8;
@@ -125,6 +133,7 @@ void fill(Ctx& c, long long n, double v, double* y);
 struct T {
     const double* p;
     std::vector<long long> dims;
+    bool constant = false;  // contents never change while the handle lives (FP32 copy may be cached)
 };
 // C[lc] = beta * C + alpha * sum A[la] B[lb] ; spec "la,lb->lc" with single-letter indices.
 void einsum(Ctx& c, const char* spec, double alpha, const T& A, const T& B, double beta, double* C,
