@@ -59,11 +59,13 @@ extern "C" {
 #define ADC_IP (-1)
 
 #define ADC_PREC_FP64 0   /* every contraction in FP64                              */
-#define ADC_PREC_BF16X3 1 /* DF ladder (sigma and setup) on tcgen05 tensor cores:   */
-                          /* split hi/lo BF16 operands, 3 products, FP32 accumulate */
-                          /* per auxiliary chunk, FP64 across chunks; the other     */
-                          /* large contractions FP32-accurate (BF16x9 emulated      */
-                          /* GEMM), FP64 vectors, subspace and accumulation         */
+#define ADC_PREC_BF16X3 1 /* DF ladder on tcgen05 tensor cores: Davidson sigma with  */
+                          /* hi/lo BF16 operands (3 products), the setup ladder of  */
+                          /* the amplitudes with hi/mid/lo planes (6 products);     */
+                          /* FP32 accumulation within an auxiliary chunk, FP64      */
+                          /* across chunks; the large other contractions FP32-      */
+                          /* accurate (BF16x9 emulated GEMM); FP64 vectors, subspace*/
+                          /* and accumulation; converged roots refined (refine)     */
 
 typedef struct adc_handle adc_handle; /* opaque */
 
@@ -76,6 +78,13 @@ typedef struct {
     int aux_chunk;           /* auxiliary functions per ladder chunk; 0 = automatic   */
     int keep_per_root;       /* Ritz vectors kept per root when the space is          */
                              /* collapsed (thick restart, default 2)                  */
+    int contractions;        /* non-ladder contractions: -1 follow precision (default)*/
+                             /* 0 FP64 DGEMM, 1 FP32-accurate emulated GEMM           */
+    int refine;              /* BF16X3 only: 1 (default) re-evaluates sigma of the    */
+                             /* converged roots once with the accurate ladder (three  */
+                             /* planes, FP32 partial sums promoted every 64-deep K    */
+                             /* block) and FP64 for every other contraction, then     */
+                             /* Rayleigh-Ritz in their span; 0 skips it               */
 } adc_options;
 
 /* Fill *opt with the defaults listed above.  Returns ADC_OK or ADC_ERR_ARG (NULL). */
@@ -118,7 +127,9 @@ int adc_sigma(adc_handle* h, const double* X, double* S, int nvec, int on_device
  *   specfac   host [nroots] or NULL
  *   vectors   host [nroots][dim] (S-normalised eigenvectors) or NULL
  *   stats     host double[8] or NULL: {iterations, sigma vectors, seconds,
- *             max S-norm residual, sigma seconds, 0, 0, 0}
+ *             max S-norm residual, sigma seconds, max |energy change| of the
+ *             final refinement, refinement seconds, 0}; with refinement the
+ *             residual is that of the refined pairs under the accurate sigma
  * Errors: ADC_ERR_ARG, ADC_ERR_OOM, ADC_ERR_CUDA, ADC_ERR_NOT_CONVERGED.
  */
 int adc_davidson(adc_handle* h, int nroots, double tol, const double* guess, double* energies, double* specfac,

@@ -38,6 +38,8 @@ class Options(ctypes.Structure):
         ("res_tol", ctypes.c_double),
         ("aux_chunk", ctypes.c_int),
         ("keep_per_root", ctypes.c_int),
+        ("contractions", ctypes.c_int),
+        ("refine", ctypes.c_int),
     ]
 
 
@@ -101,7 +103,7 @@ class ADC:
     """
 
     def __init__(self, eps, B, nocc, order=3, kind="ea", precision="fp64", max_space_per_root=8, max_iter=100,
-                 nguess_extra=2, res_tol=0.0, aux_chunk=0, keep_per_root=2):
+                 nguess_extra=2, res_tol=0.0, aux_chunk=0, keep_per_root=2, contractions=-1, refine=1):
         lib = load_library()
         self._lib = lib
         opt = Options()
@@ -113,6 +115,8 @@ class ADC:
         opt.res_tol = res_tol
         opt.aux_chunk = aux_chunk
         opt.keep_per_root = keep_per_root
+        opt.contractions = contractions
+        opt.refine = refine
         if isinstance(eps, np.ndarray):
             eps = np.ascontiguousarray(eps, dtype=np.float64)
             B = np.ascontiguousarray(B, dtype=np.float64)
@@ -166,7 +170,7 @@ class ADC:
         rc = self._lib.adc_davidson(self._h, nroots, tol, None if g is None else g.ctypes.data, e.ctypes.data,
                                     p.ctypes.data, None if vec is None else vec.ctypes.data, st.ctypes.data)
         stats = dict(iterations=int(st[0]), sigma_vectors=int(st[1]), seconds=st[2], max_residual=st[3],
-                     sigma_seconds=st[4], status=rc)
+                     sigma_seconds=st[4], refine_shift=st[5], refine_seconds=st[6], status=rc)
         if rc not in (ADC_OK, ADC_ERR_NOT_CONVERGED):
             self._check(rc)
         return e, p, vec, stats

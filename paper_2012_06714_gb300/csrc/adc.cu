@@ -35,6 +35,12 @@ struct adc_handle {
     double *ovov = nullptr, *oovv = nullptr, *oooo = nullptr, *ooov = nullptr;
     double *t = nullptr, *tau = nullptr, *t_2 = nullptr, *t1_2 = nullptr, *M11 = nullptr, *diag = nullptr;
     LadderTC* tc = nullptr;  // tensor-core ladder state (BF16x3 operands of B^Q_vv)
+    // tensor-core ladder arithmetic: Davidson sigma, the setup ladder of t, and
+    // the final refinement of converged roots
+    // (sigma: partial sums promoted every 16 K blocks, drift <= ~3e-6 relative;
+    // setup and refinement: every K block, drift ~4e-7)
+    LadderMode lm_sigma{2, 0, 16}, lm_setup{2, 1, 1}, lm_refine{2, 1, 1};
+    bool refining = false;  // sigma evaluates with lm_refine
     double* Lt = nullptr;    // setup only: sum_cd (ac|bd) t_kl^cd, shared by t2(2) and the EA 1p-1p block
     std::vector<void*> owned;
     std::string err;
@@ -219,11 +225,11 @@ T tc(const double* p, std::initializer_list<long long> d) { return T{p, std::vec
 // DF ladder: out[n] += sum_Q B^Q_vv X_n B^Q_vv for nmat v x v matrices
 //   (sum_cd (ac|bd) X_n[c,d]; the vvvv integral is never formed)
 // --------------------------------------------------------------------------
-static void ladder(adc_handle* h, const double* X, long long nmat, double* out) {
+static void ladder(adc_handle* h, const double* X, long long nmat, double* out, const LadderMode& md) {
     Ctx& c = h->ctx;
     const long long v = h->v;
-    if (h->opt.precision == ADC_PREC_BF16X3 && h->tc) {
-        ladder_tc_apply(*h->tc, c, X, nmat, out);
+    if (h->opt.precision != ADC_PREC_FP64 && h->tc) {
+        ladder_tc_apply(*h->tc, c, X, nmat, out, md);
         return;
     }
     Scope sc(c.arena);
@@ -384,7 +390,7 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
     ADC_BLAS(cublasCreate(&c.blas));
     ADC_BLAS(cublasSetStream(c.blas, c.stream));
     ADC_BLAS(cublasSetMathMode(c.blas, CUBLAS_DEFAULT_MATH));
-    c.gemm_mode = h->opt.precision == ADC_PREC_BF16X3 ? 1 : 0;
+    c.gemm_mode = h->opt.contractions >= 0 ? (h->opt.contractions ? 1 : 0) : (h->opt.precision != ADC_PREC_FP64 ? 1 : 0);
     const long long o = h->o, v = h->v, Q = h->naux, nmo = o + v;
     h->eps = h->dmalloc(nmo);
     ADC_CUDA(cudaMemcpyAsync(h->eps, eps_in, nmo * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -403,7 +409,8 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
                                        c.stream));
         }
     }
-    if (h->opt.precision == ADC_PREC_BF16X3) h->tc = ladder_tc_create(c, h->Bvv, (int)Q, (int)v, h->opt.aux_chunk);
+    if (h->opt.precision != ADC_PREC_FP64)
+        h->tc = ladder_tc_create(c, h->Bvv, (int)Q, (int)v, h->opt.aux_chunk);
     // integrals (Eq. 19)
     h->ovov = h->dmalloc(o * v * o * v);
     h->oovv = h->dmalloc(o * o * v * v);
@@ -429,7 +436,7 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
         const double* t = h->t;
         h->Lt = c.arena.dalloc(o * o * v * v);
         fill(c, o * o * v * v, 0.0, h->Lt);
-        ladder(h, t, o * o, h->Lt);  // sum_cd (ac|bd) t_ij^cd
+        ladder(h, t, o * o, h->Lt, h->lm_setup);  // sum_cd (ac|bd) t_ij^cd (it feeds M_11 directly)
         Scope sc(c.arena);
         h->t_2 = h->dmalloc(o * o * v * v);
         double* N = h->t_2;
@@ -546,7 +553,7 @@ static void sigma_ea(adc_handle* h, const double* Xin, double* Sout, long long n
         einsum(c, "nmeb,imae->niab", -1.0, tn(q, {n, o, v, v}), tc(t, {o, o, v, v}), 1.0, S2, {n, o, v, v});
         einsum(c, "nmea,imeb->niab", -1.0, tn(q, {n, o, v, v}), tc(t, {o, o, v, v}), 1.0, S2, {n, o, v, v});
         // 2p1h block, first order: ladder sum_cd (ac|bd) Y_icd (vvvv never stored)
-        ladder(h, Y2, n * o, S2);
+        ladder(h, Y2, n * o, S2, h->refining ? h->lm_refine : h->lm_sigma);
         //  - (ac|ji) Y_jcb + 2 (ai|jc) Y_jcb - (ai|jc) Y_jbc - (bd|ji) Y_jad
         einsum(c, "jiac,njcb->niab", -1.0, tc(h->oovv, {o, o, v, v}), tn(Y2, {n, o, v, v}), 1.0, S2, {n, o, v, v});
         einsum(c, "iajc,njcb->niab", 2.0, tc(h->ovov, {o, v, o, v}), tn(Y2, {n, o, v, v}), 1.0, S2, {n, o, v, v});
@@ -877,6 +884,81 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
         d.sigma(d.k, kept);
         d.k += kept;
     }
+    // Final refinement (mixed precision): sigma of the Ritz vectors once more
+    // with the accurate ladder arithmetic (lm_refine) and FP64 for every other
+    // contraction, then Rayleigh-Ritz in their span.  The Davidson residual
+    // makes the vector error first order, its energy error second order, so
+    // the refined energies carry the accurate operator's error only.
+    double refine_shift = 0.0, refine_sec = 0.0;
+    if (h->opt.precision != ADC_PREC_FP64 && h->opt.refine) {
+        auto tr = std::chrono::steady_clock::now();
+        const int saved = c.gemm_mode;
+        h->refining = true;
+        c.gemm_mode = 0;
+        try {
+            sigma_device(h, X, AX, nroots);
+        } catch (...) {
+            h->refining = false;
+            c.gemm_mode = saved;
+            throw;
+        }
+        h->refining = false;
+        c.gemm_mode = saved;
+        const int n = nroots;
+        d.metric(X, SR, n, 0);
+        gemm(c, false, true, n, n, dim, 1.0, SR, dim, 0, AX, dim, 0, 0.0, Gd, n, 0, 1);          // X S sigma(X)^T
+        gemm(c, false, true, n, n, dim, 1.0, SR, dim, 0, X, dim, 0, 0.0, Gd + n * n, n, 0, 1);   // X S X^T
+        std::vector<double> GO((size_t)2 * n * n);
+        ADC_CUDA(cudaMemcpyAsync(GO.data(), Gd, GO.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        ADC_CUDA(cudaStreamSynchronize(c.stream));
+        std::vector<double> Gs((size_t)n * n), Os((size_t)n * n), ow, U, wr, Z;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                Gs[(size_t)i * n + j] = 0.5 * (GO[(size_t)i * n + j] + GO[(size_t)j * n + i]);
+                Os[(size_t)i * n + j] = 0.5 * (GO[(size_t)n * n + i * n + j] + GO[(size_t)n * n + j * n + i]);
+            }
+        // Loewdin: O^-1/2 G O^-1/2 = Z diag(w) Z^T, coefficients O^-1/2 Z
+        jacobi_eigh(n, Os, ow, U);
+        if (!(ow[0] > 1e-8)) throw Error(ADC_ERR_CUDA, "davidson: refinement basis is singular");
+        std::vector<double> Oi((size_t)n * n, 0.0), T1((size_t)n * n, 0.0), Gt((size_t)n * n, 0.0);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j)
+                for (int k2 = 0; k2 < n; ++k2)
+                    Oi[(size_t)i * n + j] += U[(size_t)i * n + k2] * U[(size_t)j * n + k2] / std::sqrt(ow[k2]);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j)
+                for (int k2 = 0; k2 < n; ++k2) T1[(size_t)i * n + j] += Gs[(size_t)i * n + k2] * Oi[(size_t)k2 * n + j];
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j)
+                for (int k2 = 0; k2 < n; ++k2) Gt[(size_t)i * n + j] += Oi[(size_t)i * n + k2] * T1[(size_t)k2 * n + j];
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < i; ++j) Gt[(size_t)i * n + j] = Gt[(size_t)j * n + i] = 0.5 * (Gt[(size_t)i * n + j] + Gt[(size_t)j * n + i]);
+        jacobi_eigh(n, Gt, wr, Z);
+        std::vector<double> Crt((size_t)n * n, 0.0);  // Crt[r][i] = (O^-1/2 Z)[i][r]
+        for (int r = 0; r < n; ++r)
+            for (int i = 0; i < n; ++i)
+                for (int k2 = 0; k2 < n; ++k2) Crt[(size_t)r * n + i] += Oi[(size_t)i * n + k2] * Z[(size_t)k2 * n + r];
+        ADC_CUDA(cudaMemcpyAsync(Cd, Crt.data(), Crt.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+        gemm(c, false, false, n, dim, n, 1.0, Cd, n, 0, X, dim, 0, 0.0, R, dim, 0, 1);
+        gemm(c, false, false, n, dim, n, 1.0, Cd, n, 0, AX, dim, 0, 0.0, SR, dim, 0, 1);
+        ADC_CUDA(cudaMemcpyAsync(X, R, (size_t)n * dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+        ADC_CUDA(cudaMemcpyAsync(AX, SR, (size_t)n * dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+        // residuals of the refined pairs under the accurate operator
+        ADC_CUDA(cudaMemcpyAsync(R, AX, (size_t)n * dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+        for (int r = 0; r < n; ++r) axpby(c, dim, -wr[r], X + (long long)r * dim, 1.0, R + (long long)r * dim);
+        d.metric(R, SR, n, 0);
+        for (int r = 0; r < n; ++r)
+            gemm(c, false, true, 1, 1, dim, 1.0, R + (long long)r * dim, dim, 0, SR + (long long)r * dim, dim, 0, 0.0, Cd + r, 1, 0, 1);
+        std::vector<double> rr(n);
+        ADC_CUDA(cudaMemcpyAsync(rr.data(), Cd, n * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        ADC_CUDA(cudaStreamSynchronize(c.stream));
+        for (int r = 0; r < n; ++r) {
+            refine_shift = std::max(refine_shift, std::fabs(wr[r] - w[r]));
+            w[r] = wr[r];
+            rn[r] = std::sqrt(std::max(rr[r], 0.0));
+        }
+        refine_sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - tr).count();
+    }
     // outputs
     for (int r = 0; r < nroots; ++r) energies[r] = w[r];
     if (vectors) ADC_CUDA(cudaMemcpyAsync(vectors, X, (size_t)nroots * dim * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
@@ -959,7 +1041,9 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
         stats[2] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         stats[3] = mr;
         stats[4] = d.sigma_seconds;
-        stats[5] = stats[6] = stats[7] = 0.0;
+        stats[5] = refine_shift;
+        stats[6] = refine_sec;
+        stats[7] = 0.0;
     }
     return status;
 }
@@ -1001,6 +1085,8 @@ int adc_default_options(adc_options* opt) {
     opt->res_tol = 0.0;
     opt->aux_chunk = 0;
     opt->keep_per_root = 2;
+    opt->contractions = -1;
+    opt->refine = 1;
     return ADC_OK;
 }
 

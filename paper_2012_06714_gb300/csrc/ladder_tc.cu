@@ -5,8 +5,12 @@
 // Per auxiliary chunk q in [q0, q0+qn) two K-major GEMMs run back to back:
 //   GEMM1  Z[(q,a),(n,d)] = sum_c B^q[a,c] X_n[c,d]        (A = Bs, B = X^T)
 //   GEMM2  out[(n,a),b]  += sum_(q,d) Z_n[a,(q,d)] B^q[d,b] (A = Z,  B = Bp)
-// (B^q symmetric).  Every operand x is split as x = hi + lo with hi, lo in
-// BF16; each product uses hi*hi + hi*lo + lo*hi.  GEMM1 writes Z already split
+// (B^q symmetric).  Every operand x is split into BF16 planes: x = hi + lo
+// (two planes, products hi*hi + hi*lo + lo*hi: "BF16x3", 16 significand bits,
+// used in sigma) or x = hi + mid + lo (three planes, the six products of total
+// order <= 2: "BF16x6", 24 significand bits, used for the one-off ladder of
+// the amplitudes in setup, which feeds the 1p-1p block directly).
+// GEMM1 writes Z already split
 // and laid out as GEMM2's K-major A operand; GEMM2 accumulates in FP32 over
 // one chunk and adds into the FP64 output, so FP64 carries the sum over chunks.
 //
@@ -18,6 +22,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 #include <mutex>
 
 #include "ladder_tc.cuh"
@@ -29,9 +34,9 @@ namespace {
 constexpr int BM = 128;
 constexpr int BK = 64;  // 64 BF16 = 128 bytes = one 128B-swizzle row
 constexpr int MAX_STAGES = 4;
-constexpr int THREADS = 192;  // warp 0: TMA, warp 1: MMA + TMEM owner, warps 2-5: epilogue
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;  // warp 0: TMA, warp 1: MMA + TMEM owner, warps 2-9: epilogue
 constexpr int TMEM_COLS = 512;  // two accumulators of up to 256 FP32 columns
-constexpr int MAX_BN = 256;
 constexpr int A_BYTES = BM * BK * 2;
 // Always request (nearly) all of shared memory so that exactly one CTA, and one
 // 512-column TMEM allocation, lives on each SM.
@@ -61,18 +66,34 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// try_wait that lets the hardware suspend the thread (up to the hint, in ns)
+// until the phase completes, instead of spinning on issue slots.
+__device__ __forceinline__ bool mbar_try_sleep(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity), "r"(20000u)
+        : "memory");
+    return ok != 0;
+}
 // Bounded wait: false on timeout (raises the CTA abort flag and the global
-// error flag) or when another role of the CTA has already aborted.
+// error flag) or when another role of the CTA has already aborted.  The abort
+// flag and the clock are checked every 16 tries only.
 __device__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag, int* err) {
     if (mbar_try(b, parity)) return true;
     const uint64_t t0 = gtime();
-    while (true) {
-        if (mbar_try(b, parity)) return true;
-        if (*abort_flag) return false;
-        if (gtime() - t0 > WAIT_NS) {
-            *abort_flag = 1;
-            atomicExch(err, 1);
-            return false;
+    for (uint32_t n = 1;; ++n) {
+        if (mbar_try_sleep(b, parity)) return true;
+        if ((n & 15u) == 0) {
+            if (*abort_flag) return false;
+            if (gtime() - t0 > WAIT_NS) {
+                *abort_flag = 1;
+                atomicExch(err, 1);
+                return false;
+            }
         }
     }
 }
@@ -106,6 +127,21 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
+__device__ __forceinline__ void tmem_ld32_add(uint32_t taddr, float* acc) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+        "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i] += __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     uint32_t r[16];
     asm volatile(
@@ -121,12 +157,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 struct Epi {
     int mode;  // 0: split store of Z (GEMM1), 1: FP64 accumulate (GEMM2)
     int M, N;
-    // mode 0: row r = (q, a), col j = (n, dp); Z[((n*v + a)*qn + q)*vp + dp]
-    __nv_bfloat16 *zhi, *zlo;
+    // mode 0: row r = (q, a), col j = (n, dp); Z[((n*v + a)*qn + q)*vp + dp], one array per plane
+    __nv_bfloat16* z[3];
     int v, vp, qn;
     // mode 1: out[r*ldc + j] += acc
     double* out;
     long long ldc;
+    int vec;  // out rows 16-byte aligned (vector loads and stores)
     int* err;
 };
 
@@ -134,15 +171,28 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
 }
 
-// Persistent GEMM C = A B^T with split-BF16 operands (three products per K step)
-// and a double-buffered TMEM accumulator.  Roles: warp 0 lane 0 issues TMA
-// loads through a ring of `stages` shared-memory stages, running ahead across
-// tiles; warp 1 owns TMEM and its lane 0 issues the MMAs; warps 2-5 drain the
-// accumulator of tile j while the MMAs of tile j+1 run into the other buffer.
+struct Maps {
+    CUtensorMap a[3];  // A operand planes (hi, mid/lo, lo)
+    CUtensorMap b[3];  // B operand planes
+};
+
+// Persistent GEMM C = A B^T with split-BF16 operands.  Roles: warp 0 lane 0
+// issues TMA loads through a ring of `stages` shared-memory stages, running
+// ahead across tiles; warp 1 owns TMEM and its lane 0 issues the MMAs; warps
+// 2-9 are the epilogue.
+//
+// Accumulation.  The tensor core's FP32 accumulate truncates, so a long
+// accumulation in one TMEM accumulator drifts toward zero by about a quarter
+// ulp per MMA (measured: 2e-5 relative over a 4160-deep chunk).  The MMAs of a
+// tile are therefore issued in short epochs of `ekb` K blocks, alternating
+// between two TMEM accumulators; the epilogue warps add every epoch into FP32
+// registers with round-to-nearest (unbiased) while the next epoch runs, and
+// write the tile once after its last epoch.  Epilogue warp w covers TMEM lane
+// quarter (w % 4) and one half of the tile's columns.
+// (ten warps: three share a sub-partition's 16K registers, so at most 168 per thread)
 __global__ void __launch_bounds__(THREADS, 1)
-    k_gemm_bf16x3(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
-                  const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, int a_row0, int b_x0,
-                  int K, int BN, int stages, int m_fastest, int mt, int nt, Epi ep) {
+    k_gemm_bf16x3(const __grid_constant__ Maps maps, int planes, int a_row0, int b_x0, int K, int BN, int stages,
+                  int m_fastest, int mt, int nt, int ekb, Epi ep) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ uint64_t full_bar[MAX_STAGES], empty_bar[MAX_STAGES], tfull[2], tempty[2], done_bar;
@@ -150,8 +200,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     __shared__ int abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int num_k = (K + BK - 1) / BK;
+    const int epochs = (num_k + ekb - 1) / ekb;  // per tile
     const int B_BYTES = BN * BK * 2;
-    const int STAGE = 2 * A_BYTES + 2 * B_BYTES;
+    const int STAGE = planes * (A_BYTES + B_BYTES);  // [A planes][B planes]
     const int ntiles = mt * nt;
 
     if (threadIdx.x == 0) {
@@ -161,7 +212,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 4);  // one arrival per epilogue warp
+            mbar_init(&tempty[b], EPI_WARPS);  // one arrival per epilogue warp
         }
         mbar_init(&done_bar, 1);
         abort_flag = 0;
@@ -190,10 +241,17 @@ __global__ void __launch_bounds__(THREADS, 1)
                     uint8_t* st = smem + (size_t)s * STAGE;
                     mbar_expect_tx(&full_bar[s], STAGE);
                     const int kx = kb * BK;
-                    tma_load_2d(st, &mAh, &full_bar[s], kx, a_row0 + m_tile * BM);
-                    tma_load_2d(st + A_BYTES, &mAl, &full_bar[s], kx, a_row0 + m_tile * BM);
-                    tma_load_2d(st + 2 * A_BYTES, &mBh, &full_bar[s], b_x0 + kx, n_tile * BN);
-                    tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mBl, &full_bar[s], b_x0 + kx, n_tile * BN);
+                    // plane indices are compile-time constants so that the tensor maps stay in the parameter space
+                    uint8_t* sb = st + planes * A_BYTES;
+                    const int ya = a_row0 + m_tile * BM, yb = n_tile * BN;
+                    tma_load_2d(st, &maps.a[0], &full_bar[s], kx, ya);
+                    tma_load_2d(sb, &maps.b[0], &full_bar[s], b_x0 + kx, yb);
+                    tma_load_2d(st + A_BYTES, &maps.a[1], &full_bar[s], kx, ya);
+                    tma_load_2d(sb + B_BYTES, &maps.b[1], &full_bar[s], b_x0 + kx, yb);
+                    if (planes == 3) {
+                        tma_load_2d(st + 2 * A_BYTES, &maps.a[2], &full_bar[s], kx, ya);
+                        tma_load_2d(sb + 2 * B_BYTES, &maps.b[2], &full_bar[s], b_x0 + kx, yb);
+                    }
                 }
             }
             if (abort_flag) {
@@ -208,81 +266,165 @@ __global__ void __launch_bounds__(THREADS, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-            long long g = 0;
-            int j = 0;
-            for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x, ++j) {
-                const int b = j & 1;
-                if (j >= 2 && !mbar_wait(&tempty[b], (uint32_t)(((j >> 1) & 1) ^ 1), &abort_flag, ep.err)) break;
-                fence_after();
-                const uint32_t tacc = tmem + (uint32_t)(b * 256);
-                bool ok = true;
+            long long g = 0;   // stage uses
+            long long e = 0;   // epochs issued by this CTA (across tiles)
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok && !abort_flag; t += gridDim.x) {
+                int left = 0;  // K blocks left in the current epoch (epochs are whole K blocks)
+                uint32_t tacc = 0;
                 for (int kb = 0; kb < num_k; ++kb, ++g) {
                     const int s = (int)(g % stages);
                     if (!mbar_wait(&full_bar[s], (uint32_t)((g / stages) & 1), &abort_flag, ep.err)) {
                         ok = false;
                         break;
                     }
+                    uint32_t first = 1u;
+                    if (left == 0) {
+                        // new epoch: wait until the epilogue has drained this buffer's previous epoch
+                        const int b = (int)(e & 1);
+                        if (e >= 2 && !mbar_wait(&tempty[b], (uint32_t)(((e >> 1) & 1) ^ 1), &abort_flag, ep.err)) {
+                            ok = false;
+                            break;
+                        }
+                        tacc = tmem + (uint32_t)(b * 256);
+                        left = ekb;
+                        first = 0u;
+                    }
                     fence_after();
                     uint8_t* st = smem + (size_t)s * STAGE;
-                    const uint64_t ah = smem_desc(st), al = smem_desc(st + A_BYTES);
-                    const uint64_t bh = smem_desc(st + 2 * A_BYTES), bl = smem_desc(st + 2 * A_BYTES + B_BYTES);
+                    const uint64_t a0 = smem_desc(st), a1 = smem_desc(st + A_BYTES);
+                    const uint64_t b0 = smem_desc(st + planes * A_BYTES), b1 = smem_desc(st + planes * A_BYTES + B_BYTES);
+                    if (planes == 3) {
+                        const uint64_t a2 = smem_desc(st + 2 * A_BYTES), b2 = smem_desc(st + planes * A_BYTES + 2 * B_BYTES);
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk) {
-                        const uint64_t o = (uint64_t)(kk * 2);  // 16 BF16 = 32 bytes along K
-                        mma_bf16(tacc, ah + o, bh + o, idesc, (kb | kk) != 0);
-                        mma_bf16(tacc, ah + o, bl + o, idesc, 1u);
-                        mma_bf16(tacc, al + o, bh + o, idesc, 1u);
+                        for (int kk = 0; kk < BK / 16; ++kk) {
+                            const uint64_t o = (uint64_t)(kk * 2);  // 16 BF16 = 32 bytes along K
+                            mma_bf16(tacc, a0 + o, b0 + o, idesc, kk == 0 ? first : 1u);
+                            mma_bf16(tacc, a0 + o, b1 + o, idesc, 1u);
+                            mma_bf16(tacc, a1 + o, b0 + o, idesc, 1u);
+                            mma_bf16(tacc, a0 + o, b2 + o, idesc, 1u);
+                            mma_bf16(tacc, a2 + o, b0 + o, idesc, 1u);
+                            mma_bf16(tacc, a1 + o, b1 + o, idesc, 1u);
+                        }
+                    } else {
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk) {
+                            const uint64_t o = (uint64_t)(kk * 2);
+                            mma_bf16(tacc, a0 + o, b0 + o, idesc, kk == 0 ? first : 1u);
+                            mma_bf16(tacc, a0 + o, b1 + o, idesc, 1u);
+                            mma_bf16(tacc, a1 + o, b0 + o, idesc, 1u);
+                        }
                     }
                     mma_commit(&empty_bar[s]);
+                    if (--left == 0 || kb == num_k - 1) {
+                        mma_commit(&tfull[e & 1]);
+                        ++e;
+                        left = 0;
+                    }
                 }
-                if (!ok) break;
-                mma_commit(&tfull[b]);
             }
             mma_commit(&done_bar);  // fires when every MMA issued above has completed
         }
     } else {
-        // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (one accumulator row per thread)
-        const int quarter = warp & 3;
-        int j = 0;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
-            const int b = j & 1;
-            if (!mbar_wait(&tfull[b], (uint32_t)((j >> 1) & 1), &abort_flag, ep.err)) break;
-            fence_after();
+        const int ew = warp - 2;
+        const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
+        const int half = ew >> 2;      // column half of the tile
+        // The halves split on a 16-column boundary, [0, h0) and [h0, BN): both
+        // widths are multiples of 16 (BN is) and at most 128.
+        const int h0 = ((BN >> 1) + 15) & ~15;
+        const int cbeg = half ? h0 : 0, cw = half ? BN - h0 : h0;
+        long long e = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             const int m_tile = m_fastest ? t % mt : t / nt;
             const int n_tile = m_fastest ? t / mt : t % nt;
             const int row = m_tile * BM + quarter * 32 + lane;
-            const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
-            for (int c0 = 0; c0 < BN; c0 += 16) {
-                float v[16];
-                tmem_ld16(tbase + (uint32_t)c0, v);
-                const int col0 = n_tile * BN + c0;
-                if (row >= ep.M || col0 >= ep.N) continue;
+            const int colt = n_tile * BN + cbeg;  // first output column of this warp
+            float acc[128];
+#pragma unroll
+            for (int i = 0; i < 128; ++i) acc[i] = 0.0f;
+            for (int ep_i = 0; ep_i < epochs; ++ep_i, ++e) {
+                if (ep.mode == 1 && ep_i == epochs - 1 && row < ep.M) {
+                    // pull this thread's FP64 output segment into L2 while the last epoch runs
+                    const double* o = ep.out + (long long)row * ep.ldc + colt;
+                    for (int c0 = 0; c0 < cw; c0 += 16)
+                        if (colt + c0 < ep.N) asm volatile("prefetch.global.L2 [%0];" ::"l"(o + c0));
+                }
+                const int b = (int)(e & 1);
+                if (!mbar_wait(&tfull[b], (uint32_t)((e >> 1) & 1), &abort_flag, ep.err)) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256 + cbeg);
+                // 32-column loads (one wait each), then a 16-column tail
+#pragma unroll
+                for (int c0 = 0; c0 < 128; c0 += 32)
+                    if (c0 + 32 <= cw) tmem_ld32_add(tbase + (uint32_t)c0, acc + c0);
+#pragma unroll
+                for (int c0 = 0; c0 < 128; c0 += 16) {
+                    if (c0 >= (cw & ~31) && c0 < cw) {
+                        float v[16];
+                        tmem_ld16(tbase + (uint32_t)c0, v);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) acc[c0 + i] += v[i];
+                    }
+                }
+                fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[b]);
+            }
+            if (!ok) break;
+            if (row >= ep.M) continue;
+#pragma unroll
+            for (int c0 = 0; c0 < 128; c0 += 16) {
+                const int col0 = colt + c0;
+                if (c0 >= cw || col0 >= ep.N) continue;
                 if (ep.mode == 0) {
+                    // 16 columns never straddle a matrix (vp is a multiple of 32, col0 of 16):
+                    // one full 32-byte sector per plane
                     const int q = row / ep.v, a = row - q * ep.v;
                     const int n = col0 / ep.vp, dp = col0 - n * ep.vp;
                     const long long z = (((long long)n * ep.v + a) * ep.qn + q) * ep.vp + dp;
-                    __align__(16) __nv_bfloat16 hi[16], lo[16];
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        hi[i] = __float2bfloat16_rn(v[i]);
-                        lo[i] = __float2bfloat16_rn(v[i] - __bfloat162float(hi[i]));
+                    for (int h8 = 0; h8 < 16; h8 += 8) {
+                        __align__(16) __nv_bfloat16 pl[3][8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            float r = acc[c0 + h8 + i];
+#pragma unroll
+                            for (int p = 0; p < 3; ++p) {
+                                pl[p][i] = __float2bfloat16_rn(r);
+                                r -= __bfloat162float(pl[p][i]);
+                            }
+                        }
+#pragma unroll
+                        for (int p = 0; p < 3; ++p)
+                            if (p < planes) *(uint4*)(ep.z[p] + z + h8) = *(const uint4*)pl[p];
                     }
-                    uint4* dh = (uint4*)(ep.zhi + z);
-                    uint4* dl = (uint4*)(ep.zlo + z);
-                    dh[0] = ((uint4*)hi)[0];
-                    dh[1] = ((uint4*)hi)[1];
-                    dl[0] = ((uint4*)lo)[0];
-                    dl[1] = ((uint4*)lo)[1];
                 } else {
                     double* o = ep.out + (long long)row * ep.ldc + col0;
+                    if (ep.vec && col0 + 16 <= ep.N) {
+                        // 8 columns at a time: four 16-byte loads in flight before the stores
 #pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        if (col0 + i < ep.N) o[i] += (double)v[i];
+                        for (int h8 = 0; h8 < 16; h8 += 8) {
+                            double2 x[4];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) x[i] = ((const double2*)(o + h8))[i];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                x[i].x += (double)acc[c0 + h8 + 2 * i];
+                                x[i].y += (double)acc[c0 + h8 + 2 * i + 1];
+                                ((double2*)(o + h8))[i] = x[i];
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            if (col0 + i < ep.N) o[i] += (double)acc[c0 + i];
+                    }
                 }
             }
-            fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[b]);
         }
     }
     fence_before();
@@ -297,35 +439,44 @@ __global__ void __launch_bounds__(THREADS, 1)
 }
 
 // ---- operand preparation (FP64 -> split BF16) --------------------------------
-__device__ __forceinline__ void split2(double x, __nv_bfloat16& h, __nv_bfloat16& l) {
-    h = __double2bfloat16(x);
-    l = __double2bfloat16(x - (double)__bfloat162float(h));
+// x = p0 + p1 (+ p2) with every plane in BF16 (successive remainders)
+__device__ __forceinline__ void splitp(double x, int planes, __nv_bfloat16* p0, __nv_bfloat16* p1, __nv_bfloat16* p2) {
+    const __nv_bfloat16 h = __double2bfloat16(x);
+    double r = x - (double)__bfloat162float(h);
+    const __nv_bfloat16 m = __double2bfloat16(r);
+    *p0 = h;
+    *p1 = m;
+    if (planes == 3) *p2 = __double2bfloat16(r - (double)__bfloat162float(m));
 }
 #define GRID_STRIDE(i, n) for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
 
+struct Planes {
+    __nv_bfloat16* p[3];
+};
+
 // Bs[(Q,a)][cp] = B^Q[a][c] (c < v), zero pad
-__global__ void k_split_Bs(const double* __restrict__ B, int naux, int v, int vp, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+__global__ void k_split_Bs(const double* __restrict__ B, int naux, int v, int vp, int planes, Planes o) {
     long long n = (long long)naux * v * vp;
     GRID_STRIDE(x, n) {
         int cp = x % vp;
         long long qa = x / vp;
         double val = cp < v ? B[qa * v + cp] : 0.0;
-        split2(val, hi[x], lo[x]);
+        splitp(val, planes, o.p[0] + x, o.p[1] + x, o.p[2] + x);
     }
 }
 // Bp[b][(Q,dp)] = B^Q[d][b] (= B^Q[b][d]), zero pad
-__global__ void k_split_Bp(const double* __restrict__ B, int naux, int v, int vp, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+__global__ void k_split_Bp(const double* __restrict__ B, int naux, int v, int vp, int planes, Planes o) {
     long long n = (long long)v * naux * vp;
     GRID_STRIDE(x, n) {
         int dp = x % vp;
         long long r = x / vp;
         int Q = r % naux, b = r / naux;
         double val = dp < v ? B[((long long)Q * v + b) * v + dp] : 0.0;
-        split2(val, hi[x], lo[x]);
+        splitp(val, planes, o.p[0] + x, o.p[1] + x, o.p[2] + x);
     }
 }
 // XT[(m,d)][cp] = X_m[c][d] (c, d < v), zero pad; m < nmat
-__global__ void k_split_XT(const double* __restrict__ X, long long nmat, int v, int vp, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+__global__ void k_split_XT(const double* __restrict__ X, long long nmat, int v, int vp, int planes, Planes o) {
     long long n = nmat * vp * vp;
     GRID_STRIDE(x, n) {
         int cp = x % vp;
@@ -333,7 +484,7 @@ __global__ void k_split_XT(const double* __restrict__ X, long long nmat, int v, 
         int d = r % vp;
         long long m = r / vp;
         double val = (cp < v && d < v) ? X[(m * v + cp) * v + d] : 0.0;
-        split2(val, hi[x], lo[x]);
+        splitp(val, planes, o.p[0] + x, o.p[1] + x, o.p[2] + x);
     }
 }
 
@@ -373,22 +524,26 @@ CUtensorMap make_map(const void* base, long long rows, long long cols, int box_r
     return m;
 }
 
-int pick_bn(int n) {
-    // smallest padded width; prefer the wider tile on ties
-    int best = 256;
-    long long best_pad = ((n + 255) / 256) * 256LL;
-    for (int bn = 240; bn >= 64; bn -= 16) {
-        long long pad = ((long long)(n + bn - 1) / bn) * bn;
-        if (pad < best_pad) {
-            best_pad = pad;
+// Tile width for N = n columns: minimises n-tiles x per-MMA time, where an
+// M=128, N=bn, K=16 BF16 MMA takes bn/2 tensor cycles but must read 4 KB (A)
+// + 32*bn bytes (B) of shared memory at 128 B/cycle; ties go to the wider tile.
+int pick_bn(int n, int maxbn) {
+    int best = maxbn;
+    double best_cost = 1e300;
+    for (int bn = maxbn; bn >= 16; bn -= 16) {
+        const double nt = (double)((n + bn - 1) / bn);
+        const double cost = nt * std::max(bn / 2.0, 32.0 + bn / 4.0);
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
             best = bn;
         }
     }
     return best;
 }
 
-void launch_gemm(Ctx& c, const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh, const CUtensorMap& bl,
-                 int a_row0, int b_x0, int M, int N, int K, int BN, int m_fastest, const Epi& ep, double algo_flops) {
+// ekb: accumulation epoch in K blocks (0 = one epoch per tile)
+void launch_gemm(Ctx& c, const Maps& maps, int planes, int a_row0, int b_x0, int M, int N, int K, int BN, int m_fastest,
+                 int ekb, const Epi& ep, double algo_flops) {
     static bool attr = false;
     static int num_sms = 0;
     if (!attr) {
@@ -402,7 +557,7 @@ void launch_gemm(Ctx& c, const CUtensorMap& ah, const CUtensorMap& al, const CUt
     const long long ntiles = (long long)mt * nt;
     if (ntiles <= 0) return;
     if (ntiles > (1LL << 31) - 1) throw Error(-1, "ladder: tile count too large");
-    const int stage_bytes = 2 * A_BYTES + 2 * BN * BK * 2;
+    const int stage_bytes = planes * (A_BYTES + BN * BK * 2);
     const int stages = std::min(MAX_STAGES, (int)((SMEM_BYTES - 1024) / stage_bytes));
     if (stages < 2) throw Error(-1, "ladder: tile too large for shared memory");
     const int grid = (int)std::min<long long>(ntiles, num_sms);
@@ -412,8 +567,10 @@ void launch_gemm(Ctx& c, const CUtensorMap& ah, const CUtensorMap& al, const CUt
         ADC_CUDA(cudaEventCreate(&e1));
         ADC_CUDA(cudaEventRecord(e0, c.stream));
     }
-    k_gemm_bf16x3<<<grid, THREADS, SMEM_BYTES, c.stream>>>(ah, al, bh, bl, a_row0, b_x0, K, BN, stages, m_fastest, mt, nt,
-                                                           ep);
+    // epoch length in K blocks (MMAs per epoch = ekb * 4 * (3 or 6 products))
+    if (ekb <= 0) ekb = (K + BK - 1) / BK;
+    k_gemm_bf16x3<<<grid, THREADS, SMEM_BYTES, c.stream>>>(maps, planes, a_row0, b_x0, K, BN, stages, m_fastest, mt,
+                                                           nt, ekb, ep);
     ++c.kernels;
     ADC_CUDA(cudaGetLastError());
     if (c.timing) {
@@ -421,25 +578,30 @@ void launch_gemm(Ctx& c, const CUtensorMap& ah, const CUtensorMap& al, const CUt
         c.ev_start.push_back(e0);
         c.ev_stop.push_back(e1);
         c.algo_flops += algo_flops;
-        c.mma_flops += 3.0 * 2.0 * (double)mt * BM * (double)nt * BN * (double)(((K + BK - 1) / BK) * BK);
+        c.mma_flops += (planes == 3 ? 6.0 : 3.0) * 2.0 * (double)mt * BM * (double)nt * BN * (double)(((K + BK - 1) / BK) * BK);
     }
 }
 
 }  // namespace
 
 struct LadderTC {
-    int naux = 0, v = 0, vp = 0, chunk = 0, bn2 = 256;
-    __nv_bfloat16 *Bs_hi = nullptr, *Bs_lo = nullptr, *Bp_hi = nullptr, *Bp_lo = nullptr;
-    CUtensorMap mBs_hi, mBs_lo, mBp_hi, mBp_lo;
+    int naux = 0, v = 0, vp = 0, chunk = 0;
+    int bn2[4] = {256, 256, 256, 256};  // GEMM2 tile width by plane count (2 or 3)
+    __nv_bfloat16 *Bs[3] = {}, *Bp[3] = {};  // three BF16 planes of B^Q in the GEMM1-A and GEMM2-B layouts
+    CUtensorMap mBs[3], mBp2[3], mBp3[3];     // GEMM2-B maps exist for both tile widths
     int* d_err = nullptr;
     ~LadderTC() {
-        cudaFree(Bs_hi);
-        cudaFree(Bs_lo);
-        cudaFree(Bp_hi);
-        cudaFree(Bp_lo);
+        for (int p = 0; p < 3; ++p) {
+            cudaFree(Bs[p]);
+            cudaFree(Bp[p]);
+        }
         cudaFree(d_err);
     }
 };
+
+namespace {
+constexpr int BN1[4] = {0, 0, 256, 128};  // GEMM1 tile width by plane count (two stages must fit)
+}
 
 LadderTC* ladder_tc_create(Ctx& c, const double* Bvv, int naux, int v, int aux_chunk) {
     auto* L = new LadderTC();
@@ -448,23 +610,28 @@ LadderTC* ladder_tc_create(Ctx& c, const double* Bvv, int naux, int v, int aux_c
         L->v = v;
         L->vp = (v + 31) / 32 * 32;
         L->chunk = aux_chunk;
-        L->bn2 = pick_bn(v);
+        L->bn2[2] = pick_bn(v, 256);
+        L->bn2[3] = pick_bn(v, 128);
         const long long nB = (long long)naux * v * L->vp;
-        ADC_CUDA(cudaMalloc(&L->Bs_hi, nB * 2));
-        ADC_CUDA(cudaMalloc(&L->Bs_lo, nB * 2));
-        ADC_CUDA(cudaMalloc(&L->Bp_hi, nB * 2));
-        ADC_CUDA(cudaMalloc(&L->Bp_lo, nB * 2));
+        Planes ps{}, pp{};
+        for (int p = 0; p < 3; ++p) {
+            ADC_CUDA(cudaMalloc(&L->Bs[p], nB * 2));
+            ADC_CUDA(cudaMalloc(&L->Bp[p], nB * 2));
+            ps.p[p] = L->Bs[p];
+            pp.p[p] = L->Bp[p];
+        }
         ADC_CUDA(cudaMalloc(&L->d_err, sizeof(int)));
         ADC_CUDA(cudaMemsetAsync(L->d_err, 0, sizeof(int), c.stream));
-        k_split_Bs<<<grid_for(nB), 256, 0, c.stream>>>(Bvv, naux, v, L->vp, L->Bs_hi, L->Bs_lo);
+        k_split_Bs<<<grid_for(nB), 256, 0, c.stream>>>(Bvv, naux, v, L->vp, 3, ps);
         ++c.kernels;
-        k_split_Bp<<<grid_for(nB), 256, 0, c.stream>>>(Bvv, naux, v, L->vp, L->Bp_hi, L->Bp_lo);
+        k_split_Bp<<<grid_for(nB), 256, 0, c.stream>>>(Bvv, naux, v, L->vp, 3, pp);
         ++c.kernels;
         ADC_CUDA(cudaGetLastError());
-        L->mBs_hi = make_map(L->Bs_hi, (long long)naux * v, L->vp, BM);
-        L->mBs_lo = make_map(L->Bs_lo, (long long)naux * v, L->vp, BM);
-        L->mBp_hi = make_map(L->Bp_hi, v, (long long)naux * L->vp, L->bn2);
-        L->mBp_lo = make_map(L->Bp_lo, v, (long long)naux * L->vp, L->bn2);
+        for (int p = 0; p < 3; ++p) {
+            L->mBs[p] = make_map(L->Bs[p], (long long)naux * v, L->vp, BM);
+            L->mBp2[p] = make_map(L->Bp[p], v, (long long)naux * L->vp, L->bn2[2]);
+            L->mBp3[p] = make_map(L->Bp[p], v, (long long)naux * L->vp, L->bn2[3]);
+        }
     } catch (...) {
         delete L;
         throw;
@@ -474,77 +641,103 @@ LadderTC* ladder_tc_create(Ctx& c, const double* Bvv, int naux, int v, int aux_c
 
 void ladder_tc_destroy(LadderTC* L) { delete L; }
 
-void ladder_tc_apply(LadderTC& L, Ctx& c, const double* X, long long nmat, double* out) {
-    const int v = L.v, vp = L.vp, naux = L.naux;
-    if (nmat <= 0) return;
-    // Scratch budget for Z (hi+lo): ~1 GiB.  Matrices are processed in groups
-    // small enough that a chunk holds >= 8 auxiliary functions (long K in GEMM2,
-    // fewer FP64 read-modify-write passes over the output); K2 <= 8192.
-    const long long budget = 1LL << 30;
-    const int qmax = std::max(1, std::min(naux, std::max(1, 8192 / vp)));
-    const int qwant = L.chunk > 0 ? std::min(L.chunk, qmax) : std::min(8, qmax);
-    const long long per_mq = (long long)v * vp * 4;  // Z bytes per (matrix, aux function)
-    long long mg = std::max<long long>(1, budget / (per_mq * qwant));
-    mg = std::min(mg, nmat);
-    Arena::Mark mk = c.arena.mark();
-    const long long nXT = mg * vp * vp;
-    auto* xh = (__nv_bfloat16*)c.arena.alloc(nXT * 2);
-    auto* xl = (__nv_bfloat16*)c.arena.alloc(nXT * 2);
-    int qc = L.chunk > 0 ? std::min(L.chunk, qmax) : (int)std::max<long long>(1, budget / (per_mq * mg));
-    qc = std::max(1, std::min(qc, qmax));
-    const long long nZ = mg * v * (long long)qc * vp;
-    auto* zh = (__nv_bfloat16*)c.arena.alloc(nZ * 2);
-    auto* zl = (__nv_bfloat16*)c.arena.alloc(nZ * 2);
+namespace {
+
+// The chunk loop shared by both entry points: groups of mg matrices, chunks of
+// qc auxiliary functions; scratch xt (split X^T planes of one group) and zt (Z planes).
+void run_ladder(LadderTC& L, Ctx& c, const double* X, long long nmat, double* out, const LadderMode& md, Planes xt,
+                Planes zt, long long mg, int qc) {
+    const int v = L.v, vp = L.vp, naux = L.naux, planes = md.planes;
+    const int bn1 = BN1[planes], bn2 = L.bn2[planes];
     for (long long m0 = 0; m0 < nmat; m0 += mg) {
         const long long nm = std::min(mg, nmat - m0);
-        k_split_XT<<<grid_for(nm * vp * vp), 256, 0, c.stream>>>(X + m0 * v * v, nm, v, vp, xh, xl);
+        k_split_XT<<<grid_for(nm * vp * vp), 256, 0, c.stream>>>(X + m0 * v * v, nm, v, vp, planes, xt);
         ++c.kernels;
         ADC_CUDA(cudaGetLastError());
-        CUtensorMap mXh = make_map(xh, nm * vp, vp, 256), mXl = make_map(xl, nm * vp, vp, 256);
+        Maps m1;
+        for (int p = 0; p < planes; ++p) {
+            m1.a[p] = L.mBs[p];
+            m1.b[p] = make_map(xt.p[p], nm * vp, vp, bn1);
+        }
         for (int q0 = 0; q0 < naux; q0 += qc) {
             const int qn = std::min(qc, naux - q0);
+            const double algo = 2.0 * (double)qn * v * (double)nm * v * v;  // unpadded B^q X_n products
             // GEMM1: Z[(q,a),(n,d)] = sum_c B^q[a,c] X_n[c,d]
             Epi e1{};
             e1.mode = 0;
             e1.M = qn * v;
             e1.N = (int)(nm * vp);
-            e1.zhi = zh;
-            e1.zlo = zl;
+            for (int p = 0; p < 3; ++p) e1.z[p] = zt.p[p];
             e1.v = v;
             e1.vp = vp;
             e1.qn = qn;
             e1.err = L.d_err;
-            const double algo = 2.0 * (double)qn * v * (double)nm * v * v;  // unpadded B^q X_n products
-            launch_gemm(c, L.mBs_hi, L.mBs_lo, mXh, mXl, q0 * v, 0, e1.M, e1.N, vp, 256, 1, e1, algo);
+            launch_gemm(c, m1, planes, q0 * v, 0, e1.M, e1.N, vp, bn1, 1, md.epoch1, e1, algo);
             // GEMM2: out[(n,a),b] += sum_(q,d) Z_n[a,(q,d)] B^q[d,b]
-            CUtensorMap mZh = make_map(zh, nm * v, (long long)qn * vp, BM), mZl = make_map(zl, nm * v, (long long)qn * vp, BM);
+            Maps m2;
+            for (int p = 0; p < planes; ++p) {
+                m2.a[p] = make_map(zt.p[p], nm * v, (long long)qn * vp, BM);
+                m2.b[p] = planes == 3 ? L.mBp3[p] : L.mBp2[p];
+            }
             Epi e2{};
             e2.mode = 1;
             e2.M = (int)(nm * v);
             e2.N = v;
             e2.out = out + m0 * v * v;
             e2.ldc = v;
+            e2.vec = ((uintptr_t)e2.out % 16 == 0) && (v % 2 == 0);
             e2.err = L.d_err;
-            launch_gemm(c, mZh, mZl, L.mBp_hi, L.mBp_lo, 0, q0 * vp, e2.M, e2.N, qn * vp, L.bn2, 0, e2, algo);
+            launch_gemm(c, m2, planes, 0, q0 * vp, e2.M, e2.N, qn * vp, bn2, 0, md.epoch2, e2, algo);
         }
     }
+}
+
+void check_err(LadderTC& L, Ctx& c) {
     int err = 0;
     ADC_CUDA(cudaMemcpyAsync(&err, L.d_err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     ADC_CUDA(cudaStreamSynchronize(c.stream));
-    c.arena.release(mk);
     if (err) throw Error(-5, "ladder: a bounded device wait timed out");
 }
 
-// Same ladder as ladder_tc_apply, but every intermediate (split X^T and Z) is
-// carved out of a caller-provided device buffer of `bytes` bytes instead of
-// the handle's scratch arena.  out is overwritten (zeroed, then accumulated).
-// Returns false (launching nothing) if one matrix and one auxiliary function
-// do not fit in the buffer.
+}  // namespace
+
+void ladder_tc_apply(LadderTC& L, Ctx& c, const double* X, long long nmat, double* out, const LadderMode& md) {
+    const int v = L.v, vp = L.vp, naux = L.naux, planes = md.planes;
+    if (nmat <= 0) return;
+    if (planes != 2 && planes != 3) throw Error(-1, "ladder: planes must be 2 or 3");
+    if (md.epoch1 < 0 || md.epoch2 < 0) throw Error(-1, "ladder: negative epoch length");
+    // Scratch budget for Z (all planes): ~1 GiB.  Matrices are processed in
+    // groups small enough that a chunk holds >= 8 auxiliary functions (long K
+    // in GEMM2, fewer FP64 read-modify-write passes over the output); K2 <= 8192.
+    const long long budget = 1LL << 30;
+    const int qmax = std::max(1, std::min(naux, std::max(1, 8192 / vp)));
+    const int qwant = L.chunk > 0 ? std::min(L.chunk, qmax) : std::min(8, qmax);
+    const long long per_mq = (long long)v * vp * 2 * planes;  // Z bytes per (matrix, aux function)
+    long long mg = std::max<long long>(1, budget / (per_mq * qwant));
+    mg = std::min(mg, nmat);
+    int qc = L.chunk > 0 ? std::min(L.chunk, qmax) : (int)std::max<long long>(1, budget / (per_mq * mg));
+    qc = std::max(1, std::min(qc, qmax));
+    Arena::Mark mk = c.arena.mark();
+    Planes xt{}, zt{};
+    for (int p = 0; p < planes; ++p) {
+        xt.p[p] = (__nv_bfloat16*)c.arena.alloc(mg * vp * vp * 2);
+        zt.p[p] = (__nv_bfloat16*)c.arena.alloc(mg * v * (long long)qc * vp * 2);
+    }
+    run_ladder(L, c, X, nmat, out, md, xt, zt, mg, qc);
+    check_err(L, c);
+    c.arena.release(mk);
+}
+
+// Same ladder (two planes, one accumulation epoch per tile, as in sigma), but every intermediate (split X^T
+// and Z) is carved out of a caller-provided device buffer of `bytes` bytes
+// instead of the handle's scratch arena.  out is overwritten (zeroed, then
+// accumulated).  Returns false (launching nothing) if one matrix and one
+// auxiliary function do not fit in the buffer.
 bool ladder_tc_apply_scratch(LadderTC& L, Ctx& c, const double* X, long long nmat, double* out, void* scratch,
                              size_t bytes) {
-    const int v = L.v, vp = L.vp, naux = L.naux;
-    const long long per_xt = (long long)vp * vp * 4;  // split X^T (hi+lo) per matrix
-    const long long per_mq = (long long)v * vp * 4;   // Z (hi+lo) per (matrix, aux function)
+    const int v = L.v, vp = L.vp, naux = L.naux, planes = 2;
+    const long long per_xt = (long long)vp * vp * 2 * planes;  // split X^T per matrix
+    const long long per_mq = (long long)v * vp * 2 * planes;   // Z per (matrix, aux function)
     auto round256 = [](long long b) { return (b + 255) / 256 * 256; };
     if (round256(per_xt) + round256(per_mq) > (long long)bytes) return false;
     if (nmat <= 0) return true;
@@ -557,46 +750,14 @@ bool ladder_tc_apply_scratch(LadderTC& L, Ctx& c, const double* X, long long nma
     int qc = (int)std::max<long long>(1, left / (per_mq * mg));
     qc = std::max(1, std::min(qc, qmax));
     char* base = (char*)scratch;
-    auto* xh = (__nv_bfloat16*)base;
-    auto* xl = xh + mg * vp * vp;
-    auto* zh = (__nv_bfloat16*)(base + round256(mg * per_xt));
-    auto* zl = zh + mg * v * (long long)qc * vp;
+    Planes xt{}, zt{};
+    xt.p[0] = (__nv_bfloat16*)base;
+    xt.p[1] = xt.p[0] + mg * vp * vp;
+    zt.p[0] = (__nv_bfloat16*)(base + round256(mg * per_xt));
+    zt.p[1] = zt.p[0] + mg * v * (long long)qc * vp;
     ADC_CUDA(cudaMemsetAsync(out, 0, (size_t)nmat * v * v * sizeof(double), c.stream));
-    for (long long m0 = 0; m0 < nmat; m0 += mg) {
-        const long long nm = std::min(mg, nmat - m0);
-        k_split_XT<<<grid_for(nm * vp * vp), 256, 0, c.stream>>>(X + m0 * v * v, nm, v, vp, xh, xl);
-        ++c.kernels;
-        ADC_CUDA(cudaGetLastError());
-        CUtensorMap mXh = make_map(xh, nm * vp, vp, 256), mXl = make_map(xl, nm * vp, vp, 256);
-        for (int q0 = 0; q0 < naux; q0 += qc) {
-            const int qn = std::min(qc, naux - q0);
-            Epi e1{};
-            e1.mode = 0;
-            e1.M = qn * v;
-            e1.N = (int)(nm * vp);
-            e1.zhi = zh;
-            e1.zlo = zl;
-            e1.v = v;
-            e1.vp = vp;
-            e1.qn = qn;
-            e1.err = L.d_err;
-            const double algo = 2.0 * (double)qn * v * (double)nm * v * v;
-            launch_gemm(c, L.mBs_hi, L.mBs_lo, mXh, mXl, q0 * v, 0, e1.M, e1.N, vp, 256, 1, e1, algo);
-            CUtensorMap mZh = make_map(zh, nm * v, (long long)qn * vp, BM), mZl = make_map(zl, nm * v, (long long)qn * vp, BM);
-            Epi e2{};
-            e2.mode = 1;
-            e2.M = (int)(nm * v);
-            e2.N = v;
-            e2.out = out + m0 * v * v;
-            e2.ldc = v;
-            e2.err = L.d_err;
-            launch_gemm(c, mZh, mZl, L.mBp_hi, L.mBp_lo, 0, q0 * vp, e2.M, e2.N, qn * vp, L.bn2, 0, e2, algo);
-        }
-    }
-    int err = 0;
-    ADC_CUDA(cudaMemcpyAsync(&err, L.d_err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
-    ADC_CUDA(cudaStreamSynchronize(c.stream));
-    if (err) throw Error(-5, "ladder: a bounded device wait timed out");
+    run_ladder(L, c, X, nmat, out, LadderMode{planes, 0, 0}, xt, zt, mg, qc);
+    check_err(L, c);
     return true;
 }
 

@@ -1,18 +1,29 @@
 // Tensor-core (tcgen05 / TMEM, sm_103a) density-fitted ladder:
 //   out[n] += sum_Q B^Q X_n B^Q      (sum_cd (ac|bd) X_n[c,d], Eq. 19)
-// with split-precision BF16 operands (x = x_hi + x_lo, three products
-// hi*hi + hi*lo + lo*hi), FP32 accumulation in tensor memory within one
+// with split-precision BF16 operands (planes = 2: x = hi + lo, three products;
+// planes = 3: x = hi + mid + lo, six products), FP32 accumulation within one
 // auxiliary chunk and FP64 accumulation across chunks.
 #pragma once
 #include "common.cuh"
 
 namespace adc {
 
+// Arithmetic of one ladder evaluation.  The tensor core's FP32 accumulation
+// truncates, so a long accumulation in tensor memory drifts toward zero
+// (about a quarter ulp per MMA).  epoch1 / epoch2 bound the K blocks (64 deep)
+// accumulated in tensor memory before the partial sum is added, rounded to
+// nearest, into FP32 registers (GEMM1: K = nvir, GEMM2: K = chunk * nvir);
+// 0 means the whole K range of a tile in one accumulator.
+struct LadderMode {
+    int planes;  // 2 or 3
+    int epoch1, epoch2;
+};
+
 struct LadderTC;  // owns the BF16 hi/lo copies of B^Q_vv in the GEMM layouts
 
 LadderTC* ladder_tc_create(Ctx& c, const double* Bvv, int naux, int nvir, int aux_chunk);
 void ladder_tc_destroy(LadderTC* L);
-void ladder_tc_apply(LadderTC& L, Ctx& c, const double* X, long long nmat, double* out);
+void ladder_tc_apply(LadderTC& L, Ctx& c, const double* X, long long nmat, double* out, const LadderMode& md);
 bool ladder_tc_apply_scratch(LadderTC& L, Ctx& c, const double* X, long long nmat, double* out, void* scratch,
                              size_t bytes);
 
