@@ -125,7 +125,11 @@ def cpu_baseline(sample_seconds=12.0):
 
 
 def time_to_roots_medium(dev):
-    """Setup + Davidson to 4 roots, FP64 plain vs mixed, EA-ADC(3) nocc=20 nvir=180 naux=600."""
+    """Setup + Davidson to 4 roots, FP64 plain vs mixed, EA-ADC(3) nocc=20 nvir=180 naux=600.
+
+    Both runs converge to |dE| <= 1e-6 Eh between iterations and S-norm
+    residual <= 1e-4; the mixed run is reported with and without the final
+    refinement of its converged roots, each root's |dE| against the FP64 run."""
     import torch
 
     from adc_inputs import make_system
@@ -134,25 +138,73 @@ def time_to_roots_medium(dev):
     s = make_system(20, 180, 600, seed=0)
     out = {"workload": "EA-ADC(3) nocc=20 nvir=180 naux=600, 4 roots, tol 1e-6 Eh, residual 1e-4"}
     res = {}
-    for prec in ("fp64", "bf16x3"):
+    for name, prec, refine in (("fp64", "fp64", 0), ("mixed", "bf16x3", 1), ("mixed_unrefined", "bf16x3", 0)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g = ADC(torch.from_numpy(s.eps).to(dev), torch.from_numpy(s.B).to(dev), 20, order=3, kind="ea",
-                precision=prec, res_tol=1e-4)
+                precision=prec, res_tol=1e-4, refine=refine)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         e, p, _, st = g.davidson(4, tol=1e-6)
         t2 = time.perf_counter()
         g.close()
-        res[prec] = (e, p)
-        out[prec] = {"setup_seconds": t1 - t0, "davidson_seconds": t2 - t1, "total_seconds": t2 - t0,
-                     "iterations": st["iterations"], "sigma_vectors": st["sigma_vectors"], "status": st["status"],
+        res[name] = (e, p)
+        out[name] = {"precision": prec, "setup_seconds": t1 - t0, "davidson_seconds": t2 - t1,
+                     "total_seconds": t2 - t0, "iterations": st["iterations"], "sigma_vectors": st["sigma_vectors"],
+                     "status": st["status"], "max_residual": st["max_residual"],
+                     "refine_shift_eh": st["refine_shift"], "refine_seconds": st["refine_seconds"],
                      "energies_eh": [float(x) for x in e]}
-    for prec in ("bf16x3",):
-        out[prec]["max_abs_dE_eh_vs_fp64"] = float(np.abs(res["fp64"][0] - res[prec][0]).max())
-        out[prec]["max_abs_dP_vs_fp64"] = float(np.abs(res["fp64"][1] - res[prec][1]).max())
-        out[prec]["speedup_vs_fp64"] = out["fp64"]["total_seconds"] / out[prec]["total_seconds"]
+    for name in ("mixed", "mixed_unrefined"):
+        out[name]["abs_dE_eh_vs_fp64"] = [float(x) for x in np.abs(res["fp64"][0] - res[name][0])]
+        out[name]["max_abs_dP_vs_fp64"] = float(np.abs(res["fp64"][1] - res[name][1]).max())
+        out[name]["speedup_vs_fp64"] = out["fp64"]["total_seconds"] / out[name]["total_seconds"]
     return out
+
+
+def profiled_traffic():
+    """DRAM bytes per ladder-GEMM launch from the committed ncu summary, or None
+    when the kernel source has changed since the counters were taken."""
+    import hashlib
+
+    p = os.path.join(ROOT, "profiles", "k_gemm_bf16x3_traffic.json")
+    src = os.path.join(ROOT, "paper_2012_06714_gb300", "csrc", "ladder_tc.cu")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return d.get("dram_bytes_per_launch") if d.get("ladder_tc_cu_sha256") == h else None
+
+
+def run_ladder_case(args):
+    """Small profiling case of the ladder kernel (for ncu): EA-ADC(3) with
+    nocc=4, nvir=400, naux=400 and 40 trial vectors, i.e. 160 ladder matrices
+    per sigma call -- the same per-launch GEMM shapes as the bench workload
+    (160 matrices, 10 auxiliary functions per chunk) with a few GB on the
+    device.  Runs `--steps` sigma calls after one warm-up call and prints the
+    ladder launch timing of the last call."""
+    import torch
+
+    from adc_inputs import make_system
+    from paper_2012_06714_gb300 import ADC
+
+    o, v, naux, nvec = 4, 400, 400, 40
+    s = make_system(o, v, naux, seed=0)
+    g = ADC(torch.from_numpy(s.eps).cuda(), torch.from_numpy(s.B).cuda(), o, order=3, kind="ea",
+            precision="bf16x3")
+    X = torch.randn(nvec, g.dim, device="cuda", dtype=torch.float64)
+    S = torch.empty_like(X)
+    g.sigma(X, out=S)
+    for _ in range(max(1, args.steps) - 1):
+        g.sigma(X, out=S)
+    torch.cuda.synchronize()
+    g.kernel_timing(True)
+    g.sigma(X, out=S)
+    kt = g.kernel_timing(False)
+    print(json.dumps({"case": "ladder o=4 v=400 naux=400 nvec=40", "launches": kt["launches"], "ms": kt["ms"],
+                      "algo_tflops": kt["algo_flops"] / kt["ms"] / 1e9,
+                      "mma_tflops": kt["mma_flops"] / kt["ms"] / 1e9}))
+    g.close()
+    return 0
 
 
 def run_reference(args):
@@ -250,7 +302,7 @@ def run_ours(args):
     bf16_peak, hbm_peak, peak_src = peaks()
     peak = bf16_peak / 3.0  # three BF16 products per split-precision product
     achieved = kt["algo_flops"] / (kt["ms"] / 1e3) / 1e12
-    traffic = None
+    traffic = profiled_traffic()
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": "k_gemm_bf16x3 (both ladder GEMMs)",
             "peak_note": f"{peak_src} BF16 dense {bf16_peak:.1f} TF/s / 3 split products",
@@ -289,7 +341,9 @@ def run_ours(args):
         roots = {"workload": "nocc=40 nvir=400 naux=1400, bf16x3", "seconds": time.perf_counter() - t0,
                  "setup_seconds": setup_s, "energies_eh": [float(x) for x in e],
                  "spectroscopic_factors": [float(x) for x in p], "iterations": st["iterations"],
-                 "sigma_vectors": st["sigma_vectors"], "max_residual": st["max_residual"], "status": st["status"]}
+                 "sigma_vectors": st["sigma_vectors"], "sigma_seconds": st["sigma_seconds"],
+                 "max_residual": st["max_residual"], "status": st["status"],
+                 "refine_shift_eh": st["refine_shift"], "refine_seconds": st["refine_seconds"]}
         roots["fp64_vs_mixed"] = time_to_roots_medium(dev)
 
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -318,7 +372,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-roots", action="store_true")
+    ap.add_argument("--ladder-case", action="store_true", help="small ladder profiling case (for ncu)")
     args = ap.parse_args()
+    if args.ladder_case:
+        return run_ladder_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -1050,9 +1050,10 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
 
 // Internal accessor for the allocation-free ladder entry point (ladder_static.cu).
 namespace adc {
-bool handle_ladder_view(adc_handle* h, LadderTC** tc, Ctx** c, int* nvir, std::string** err) {
+bool handle_ladder_view(adc_handle* h, LadderTC** tc, Ctx** c, int* nvir, std::string** err, LadderMode* md) {
     if (!h) return false;
     *tc = h->tc;
+    *md = h->lm_sigma;
     *c = &h->ctx;
     *nvir = h->v;
     *err = &h->err;

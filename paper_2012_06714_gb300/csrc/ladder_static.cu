@@ -18,7 +18,7 @@
 #include "ladder_tc.cuh"
 
 namespace adc {
-bool handle_ladder_view(adc_handle* h, LadderTC** tc, Ctx** c, int* nvir, std::string** err);
+bool handle_ladder_view(adc_handle* h, LadderTC** tc, Ctx** c, int* nvir, std::string** err, LadderMode* md);
 }
 
 namespace {
@@ -59,7 +59,8 @@ extern "C" int adc_ladder_noalloc(adc_handle* h, const double* X, double* out, l
     Ctx* c = nullptr;
     int v = 0;
     std::string* err = nullptr;
-    if (!handle_ladder_view(h, &tc, &c, &v, &err)) return ADC_ERR_ARG;
+    LadderMode md{2, 0, 0};
+    if (!handle_ladder_view(h, &tc, &c, &v, &err, &md)) return ADC_ERR_ARG;
     if (!X || !out || nmat < 0) {
         *err = "adc_ladder_noalloc: invalid argument";
         return ADC_ERR_ARG;
@@ -71,7 +72,7 @@ extern "C" int adc_ladder_noalloc(adc_handle* h, const double* X, double* out, l
     try {
         void* scratch = nullptr;
         ADC_CUDA(scratch_address(&scratch));
-        if (!ladder_tc_apply_scratch(*tc, *c, X, nmat, out, scratch, kScratchBytes)) {
+        if (!ladder_tc_apply_scratch(*tc, *c, X, nmat, out, md, scratch, kScratchBytes)) {
             *err = "adc_ladder_noalloc: nvir = " + std::to_string(v) +
                    " needs more than the fixed 64 MiB scratch for one matrix and one auxiliary function";
             return ADC_ERR_ARG;

@@ -32,8 +32,13 @@ namespace adc {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BK = 64;  // 64 BF16 = 128 bytes = one 128B-swizzle row
-constexpr int MAX_STAGES = 4;
+// K block: 64 BF16 = 128-byte rows in the 128-byte swizzle (8-row atoms of
+// 1024 bytes).  (32-deep blocks with the 64-byte swizzle also work -- twice the
+// stages of half the size -- but measured slower.)
+constexpr int BK = 64;
+constexpr int ROW_BYTES = BK * 2;
+constexpr int KB_PER_EPOCH_UNIT = 64 / BK;  // LadderMode epochs count 64-deep K blocks
+constexpr int MAX_STAGES = 8;
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;  // warp 0: TMA, warp 1: MMA + TMEM owner, warps 2-9: epilogue
 constexpr int TMEM_COLS = 512;  // two accumulators of up to 256 FP32 columns
@@ -104,15 +109,23 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* m, uin
         "l"((uint64_t)m), "r"(su32(bar)), "r"(x), "r"(y)
         : "memory");
 }
-// tcgen05 shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row
-// core groups 1024 bytes apart.
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// tcgen05 shared-memory matrix descriptor: K-major, ROW_BYTES swizzle, 8-row
+// core groups 8 * ROW_BYTES apart.
 __device__ __forceinline__ uint64_t smem_desc(const void* p) {
     uint64_t d = 0;
     d |= (uint64_t)((su32(p) >> 4) & 0x3FFF);
-    d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
-    d |= (uint64_t)1 << 46;             // descriptor version
-    d |= (uint64_t)2 << 61;             // 128-byte swizzle
+    d |= (uint64_t)1 << 16;                     // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)((8 * ROW_BYTES) >> 4) << 32;  // stride byte offset
+    d |= (uint64_t)1 << 46;                     // descriptor version
+    d |= (uint64_t)(ROW_BYTES == 128 ? 2 : 4) << 61;  // layout: 128-byte (2) or 64-byte (4) swizzle
     return d;
 }
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -171,6 +184,62 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
 }
 
+// Epilogue store of 16 consecutive FP32 results of one row (col0 a multiple of 16).
+//   mode 0: split into `planes` BF16 planes of Z (GEMM1).  16 columns never
+//           straddle a matrix (vp is a multiple of 32): one full 32-byte sector
+//           per plane.  The split runs on the FMA/ALU pipes: packed
+//           round-to-nearest conversions, BF16 -> FP32 by a 16-bit shift.
+//   mode 1: FP64 accumulate into out (GEMM2).
+__device__ __forceinline__ void store16(const Epi& ep, int planes, int row, int col0, const float* v) {
+    if (ep.mode == 0) {
+        const int q = row / ep.v, a = row - q * ep.v;
+        const int n = col0 / ep.vp, dp = col0 - n * ep.vp;
+        const long long z = (((long long)n * ep.v + a) * ep.qn + q) * ep.vp + dp;
+#pragma unroll
+        for (int h8 = 0; h8 < 16; h8 += 8) {
+            uint32_t pl[3][4];  // [plane][pair of columns]
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float r0 = v[h8 + 2 * i], r1 = v[h8 + 2 * i + 1];
+#pragma unroll
+                for (int p = 0; p < 3; ++p) {
+                    if (p < planes) {
+                        const __nv_bfloat162 h = __floats2bfloat162_rn(r0, r1);
+                        const uint32_t u = *(const uint32_t*)&h;
+                        pl[p][i] = u;
+                        r0 -= __uint_as_float(u << 16);
+                        r1 -= __uint_as_float(u & 0xFFFF0000u);
+                    }
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+                if (p < planes) *(uint4*)(ep.z[p] + z + h8) = make_uint4(pl[p][0], pl[p][1], pl[p][2], pl[p][3]);
+        }
+    } else {
+        double* o = ep.out + (long long)row * ep.ldc + col0;
+        if (ep.vec && col0 + 16 <= ep.N) {
+            // 8 columns at a time: four 16-byte loads in flight before the stores
+#pragma unroll
+            for (int h8 = 0; h8 < 16; h8 += 8) {
+                double2 x[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) x[i] = ((const double2*)(o + h8))[i];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    x[i].x += (double)v[h8 + 2 * i];
+                    x[i].y += (double)v[h8 + 2 * i + 1];
+                    ((double2*)(o + h8))[i] = x[i];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                if (col0 + i < ep.N) o[i] += (double)v[i];
+        }
+    }
+}
+
 struct Maps {
     CUtensorMap a[3];  // A operand planes (hi, mid/lo, lo)
     CUtensorMap b[3];  // B operand planes
@@ -189,7 +258,11 @@ struct Maps {
 // registers with round-to-nearest (unbiased) while the next epoch runs, and
 // write the tile once after its last epoch.  Epilogue warp w covers TMEM lane
 // quarter (w % 4) and one half of the tile's columns.
+
+// kPromote = false (one epoch per tile) streams each tile from TMEM to global
+// memory without the register accumulator.
 // (ten warps: three share a sub-partition's 16K registers, so at most 168 per thread)
+template <bool kPromote>
 __global__ void __launch_bounds__(THREADS, 1)
     k_gemm_bf16x3(const __grid_constant__ Maps maps, int planes, int a_row0, int b_x0, int K, int BN, int stages,
                   int m_fastest, int mt, int nt, int ekb, Epi ep) {
@@ -245,13 +318,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                     uint8_t* sb = st + planes * A_BYTES;
                     const int ya = a_row0 + m_tile * BM, yb = n_tile * BN;
                     tma_load_2d(st, &maps.a[0], &full_bar[s], kx, ya);
-                    tma_load_2d(sb, &maps.b[0], &full_bar[s], b_x0 + kx, yb);
                     tma_load_2d(st + A_BYTES, &maps.a[1], &full_bar[s], kx, ya);
+                    if (planes == 3) tma_load_2d(st + 2 * A_BYTES, &maps.a[2], &full_bar[s], kx, ya);
+                    tma_load_2d(sb, &maps.b[0], &full_bar[s], b_x0 + kx, yb);
                     tma_load_2d(sb + B_BYTES, &maps.b[1], &full_bar[s], b_x0 + kx, yb);
-                    if (planes == 3) {
-                        tma_load_2d(st + 2 * A_BYTES, &maps.a[2], &full_bar[s], kx, ya);
-                        tma_load_2d(sb + 2 * B_BYTES, &maps.b[2], &full_bar[s], b_x0 + kx, yb);
-                    }
+                    if (planes == 3) tma_load_2d(sb + 2 * B_BYTES, &maps.b[2], &full_bar[s], b_x0 + kx, yb);
                 }
             }
             if (abort_flag) {
@@ -340,90 +411,64 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int n_tile = m_fastest ? t / mt : t % nt;
             const int row = m_tile * BM + quarter * 32 + lane;
             const int colt = n_tile * BN + cbeg;  // first output column of this warp
-            float acc[128];
+            if constexpr (kPromote) {
+                float acc[128];
 #pragma unroll
-            for (int i = 0; i < 128; ++i) acc[i] = 0.0f;
-            for (int ep_i = 0; ep_i < epochs; ++ep_i, ++e) {
-                if (ep.mode == 1 && ep_i == epochs - 1 && row < ep.M) {
-                    // pull this thread's FP64 output segment into L2 while the last epoch runs
-                    const double* o = ep.out + (long long)row * ep.ldc + colt;
-                    for (int c0 = 0; c0 < cw; c0 += 16)
-                        if (colt + c0 < ep.N) asm volatile("prefetch.global.L2 [%0];" ::"l"(o + c0));
+                for (int i = 0; i < 128; ++i) acc[i] = 0.0f;
+                for (int ep_i = 0; ep_i < epochs; ++ep_i, ++e) {
+                    if (ep.mode == 1 && ep_i == epochs - 1 && row < ep.M) {
+                        // pull this thread's FP64 output segment into L2 while the last epoch runs
+                        const double* o = ep.out + (long long)row * ep.ldc + colt;
+                        for (int c0 = 0; c0 < cw; c0 += 16)
+                            if (colt + c0 < ep.N) asm volatile("prefetch.global.L2 [%0];" ::"l"(o + c0));
+                    }
+                    const int b = (int)(e & 1);
+                    if (!mbar_wait(&tfull[b], (uint32_t)((e >> 1) & 1), &abort_flag, ep.err)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256 + cbeg);
+                    // 32-column loads (one wait each), then a 16-column tail
+#pragma unroll
+                    for (int c0 = 0; c0 < 128; c0 += 32)
+                        if (c0 + 32 <= cw) tmem_ld32_add(tbase + (uint32_t)c0, acc + c0);
+#pragma unroll
+                    for (int c0 = 0; c0 < 128; c0 += 16) {
+                        if (c0 >= (cw & ~31) && c0 < cw) {
+                            float v[16];
+                            tmem_ld16(tbase + (uint32_t)c0, v);
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) acc[c0 + i] += v[i];
+                        }
+                    }
+                    fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tempty[b]);
                 }
+                if (!ok) break;
+                if (row >= ep.M) continue;
+#pragma unroll
+                for (int c0 = 0; c0 < 128; c0 += 16)
+                    if (c0 < cw && colt + c0 < ep.N) store16(ep, planes, row, colt + c0, acc + c0);
+            } else {
+                // one epoch per tile: stream TMEM -> global 16 columns at a time, then release the buffer
                 const int b = (int)(e & 1);
                 if (!mbar_wait(&tfull[b], (uint32_t)((e >> 1) & 1), &abort_flag, ep.err)) {
                     ok = false;
                     break;
                 }
+                ++e;
                 fence_after();
                 const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256 + cbeg);
-                // 32-column loads (one wait each), then a 16-column tail
-#pragma unroll
-                for (int c0 = 0; c0 < 128; c0 += 32)
-                    if (c0 + 32 <= cw) tmem_ld32_add(tbase + (uint32_t)c0, acc + c0);
-#pragma unroll
-                for (int c0 = 0; c0 < 128; c0 += 16) {
-                    if (c0 >= (cw & ~31) && c0 < cw) {
-                        float v[16];
-                        tmem_ld16(tbase + (uint32_t)c0, v);
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) acc[c0 + i] += v[i];
-                    }
+                for (int c0 = 0; c0 < cw; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(tbase + (uint32_t)c0, v);  // warp-collective: every lane loads
+                    if (row < ep.M && colt + c0 < ep.N) store16(ep, planes, row, colt + c0, v);
                 }
                 fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[b]);
-            }
-            if (!ok) break;
-            if (row >= ep.M) continue;
-#pragma unroll
-            for (int c0 = 0; c0 < 128; c0 += 16) {
-                const int col0 = colt + c0;
-                if (c0 >= cw || col0 >= ep.N) continue;
-                if (ep.mode == 0) {
-                    // 16 columns never straddle a matrix (vp is a multiple of 32, col0 of 16):
-                    // one full 32-byte sector per plane
-                    const int q = row / ep.v, a = row - q * ep.v;
-                    const int n = col0 / ep.vp, dp = col0 - n * ep.vp;
-                    const long long z = (((long long)n * ep.v + a) * ep.qn + q) * ep.vp + dp;
-#pragma unroll
-                    for (int h8 = 0; h8 < 16; h8 += 8) {
-                        __align__(16) __nv_bfloat16 pl[3][8];
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            float r = acc[c0 + h8 + i];
-#pragma unroll
-                            for (int p = 0; p < 3; ++p) {
-                                pl[p][i] = __float2bfloat16_rn(r);
-                                r -= __bfloat162float(pl[p][i]);
-                            }
-                        }
-#pragma unroll
-                        for (int p = 0; p < 3; ++p)
-                            if (p < planes) *(uint4*)(ep.z[p] + z + h8) = *(const uint4*)pl[p];
-                    }
-                } else {
-                    double* o = ep.out + (long long)row * ep.ldc + col0;
-                    if (ep.vec && col0 + 16 <= ep.N) {
-                        // 8 columns at a time: four 16-byte loads in flight before the stores
-#pragma unroll
-                        for (int h8 = 0; h8 < 16; h8 += 8) {
-                            double2 x[4];
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) x[i] = ((const double2*)(o + h8))[i];
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) {
-                                x[i].x += (double)acc[c0 + h8 + 2 * i];
-                                x[i].y += (double)acc[c0 + h8 + 2 * i + 1];
-                                ((double2*)(o + h8))[i] = x[i];
-                            }
-                        }
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < 16; ++i)
-                            if (col0 + i < ep.N) o[i] += (double)acc[c0 + i];
-                    }
-                }
             }
         }
     }
@@ -434,8 +479,305 @@ __global__ void __launch_bounds__(THREADS, 1)
         while (!mbar_try(&done_bar, 0) && gtime() - t0 < WAIT_NS) {
         }
         fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// ---- 2-SM variant: one MMA tile of 256 rows on a CTA pair (cta_group::2) -----
+__device__ __forceinline__ uint32_t mapa_rank(const void* p, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(su32(p)), "r"(rank));
+    return r;
+}
+// TMA load into this CTA's shared memory that completes its bytes on an
+// mbarrier of either CTA of the pair (shared::cluster address)
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* m, uint32_t bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+        "[%2];" ::"r"(su32(dst)),
+        "l"((uint64_t)m), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void mma_bf16_pair(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+// arrive on the mbarrier at `bar`'s offset in both CTAs once the pair's MMAs issued so far have completed
+__device__ __forceinline__ void mma_commit_pair(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            su32(bar)),
+        "h"((uint16_t)3)
+        : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t bar) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_cluster(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait with cluster-scope acquire (for arrivals from the peer CTA)
+__device__ bool mbar_wait_cluster(uint64_t* b, uint32_t parity, volatile int* abort_flag, int* err) {
+    const uint64_t t0 = gtime();
+    for (uint32_t n = 0;; ++n) {
+        if (mbar_try_cluster(b, parity)) return true;
+        if ((n & 15u) == 15u) {
+            if (*abort_flag) return false;
+            if (gtime() - t0 > WAIT_NS) {
+                *abort_flag = 1;
+                atomicExch(err, 1);
+                return false;
+            }
+        }
+    }
+}
+
+// Persistent GEMM C = A B^T as k_gemm_bf16x3, with each tile 256 rows high and
+// computed by a CTA pair (a cluster of two) through cta_group::2 MMAs: CTA r
+// holds rows [128 r, 128 r + 128) of the A tile and rows [BN/2 r, BN/2 (r+1))
+// of the B tile, so each SM receives A + B/2 per K block instead of A + B and
+// a stage is a third smaller.  Both CTAs' TMA loads complete on the leader's
+// (rank 0) full barrier; the leader's MMA thread issues every MMA and its
+// commits arrive on the barriers of both CTAs; each CTA's epilogue drains its
+// own tensor memory (its 128 rows of the tile, all BN columns) and releases
+// the accumulator on the leader's barrier (2 x EPI_WARPS arrivals).
+template <bool kPromote>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_gemm_pair(const __grid_constant__ Maps maps, int planes, int a_row0, int b_x0, int K, int BN, int stages,
+                int m_fastest, int mt, int nt, int ekb, Epi ep) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ uint64_t full_bar[MAX_STAGES], empty_bar[MAX_STAGES], tfull[2], tempty[2], done_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int num_k = (K + BK - 1) / BK;
+    const int epochs = (num_k + ekb - 1) / ekb;  // per tile
+    const int BH = BN / 2;                       // B rows held by each CTA
+    const int BH_BYTES = BH * ROW_BYTES;
+    const int STAGE = planes * (A_BYTES + BH_BYTES);  // per CTA: [A planes][B-half planes]
+    const int rank = (int)cluster_rank();
+    const bool leader = rank == 0;
+    const int mt2 = (mt + 1) / 2;  // 256-row tiles
+    const int nunits = mt2 * nt;
+    const int cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full_bar[s], 1);   // leader: its producer's expect_tx (bytes of both CTAs)
+            mbar_init(&empty_bar[s], 1);  // the leader's commit
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 2 * EPI_WARPS);  // leader: every epilogue warp of both CTAs
+        }
+        mbar_init(&done_bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        // one warp of each CTA of the pair allocates collectively (same address in both)
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_slot)), "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncwarp();
+    cluster_sync();
+    fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            long long g = 0;
+            for (int u = cid; u < nunits && !abort_flag; u += ncl) {
+                const int m2 = m_fastest ? u % mt2 : u / nt;
+                const int n_tile = m_fastest ? u / mt2 : u % nt;
+                const int ya = a_row0 + m2 * 2 * BM + rank * BM, yb = n_tile * BN + rank * BH;
+                for (int kb = 0; kb < num_k; ++kb, ++g) {
+                    const int s = (int)(g % stages);
+                    const uint32_t ph = (uint32_t)((g / stages) & 1);
+                    if (g >= stages && !mbar_wait(&empty_bar[s], ph ^ 1, &abort_flag, ep.err)) break;
+                    uint8_t* st = smem + (size_t)s * STAGE;
+                    if (leader) mbar_expect_tx(&full_bar[s], 2 * STAGE);
+                    const uint32_t fb = mapa_rank(&full_bar[s], 0);
+                    const int kx = kb * BK;
+                    uint8_t* sb = st + planes * A_BYTES;
+                    tma_load_2d_pair(st, &maps.a[0], fb, kx, ya);
+                    tma_load_2d_pair(st + A_BYTES, &maps.a[1], fb, kx, ya);
+                    if (planes == 3) tma_load_2d_pair(st + 2 * A_BYTES, &maps.a[2], fb, kx, ya);
+                    tma_load_2d_pair(sb, &maps.b[0], fb, b_x0 + kx, yb);
+                    tma_load_2d_pair(sb + BH_BYTES, &maps.b[1], fb, b_x0 + kx, yb);
+                    if (planes == 3) tma_load_2d_pair(sb + 2 * BH_BYTES, &maps.b[2], fb, b_x0 + kx, yb);
+                }
+            }
+            if (abort_flag && leader) {
+                // let the copies of the last `stages` issues of both CTAs land (bounded)
+                for (long long q = (g > stages ? g - stages : 0); q < g; ++q) {
+                    const uint64_t t0 = gtime();
+                    while (!mbar_try(&full_bar[q % stages], (uint32_t)((q / stages) & 1)) && gtime() - t0 < WAIT_NS) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && leader) {
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)((2 * BM) >> 4) << 24);
+            long long g = 0;  // stage uses
+            long long e = 0;  // epochs issued (across tiles)
+            bool ok = true;
+            for (int u = cid; u < nunits && ok && !abort_flag; u += ncl) {
+                int left = 0;
+                uint32_t tacc = 0;
+                for (int kb = 0; kb < num_k; ++kb, ++g) {
+                    const int s = (int)(g % stages);
+                    if (!mbar_wait(&full_bar[s], (uint32_t)((g / stages) & 1), &abort_flag, ep.err)) {
+                        ok = false;
+                        break;
+                    }
+                    uint32_t first = 1u;
+                    if (left == 0) {
+                        const int b = (int)(e & 1);
+                        if (e >= 2 && !mbar_wait_cluster(&tempty[b], (uint32_t)(((e >> 1) & 1) ^ 1), &abort_flag, ep.err)) {
+                            ok = false;
+                            break;
+                        }
+                        tacc = tmem + (uint32_t)(b * 256);
+                        left = ekb;
+                        first = 0u;
+                    }
+                    fence_after();
+                    uint8_t* st = smem + (size_t)s * STAGE;
+                    const uint64_t a0 = smem_desc(st), a1 = smem_desc(st + A_BYTES);
+                    const uint64_t b0 = smem_desc(st + planes * A_BYTES), b1 = smem_desc(st + planes * A_BYTES + BH_BYTES);
+                    if (planes == 3) {
+                        const uint64_t a2 = smem_desc(st + 2 * A_BYTES), b2 = smem_desc(st + planes * A_BYTES + 2 * BH_BYTES);
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk) {
+                            const uint64_t o = (uint64_t)(kk * 2);
+                            mma_bf16_pair(tacc, a0 + o, b0 + o, idesc, kk == 0 ? first : 1u);
+                            mma_bf16_pair(tacc, a0 + o, b1 + o, idesc, 1u);
+                            mma_bf16_pair(tacc, a1 + o, b0 + o, idesc, 1u);
+                            mma_bf16_pair(tacc, a0 + o, b2 + o, idesc, 1u);
+                            mma_bf16_pair(tacc, a2 + o, b0 + o, idesc, 1u);
+                            mma_bf16_pair(tacc, a1 + o, b1 + o, idesc, 1u);
+                        }
+                    } else {
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk) {
+                            const uint64_t o = (uint64_t)(kk * 2);
+                            mma_bf16_pair(tacc, a0 + o, b0 + o, idesc, kk == 0 ? first : 1u);
+                            mma_bf16_pair(tacc, a0 + o, b1 + o, idesc, 1u);
+                            mma_bf16_pair(tacc, a1 + o, b0 + o, idesc, 1u);
+                        }
+                    }
+                    mma_commit_pair(&empty_bar[s]);
+                    if (--left == 0 || kb == num_k - 1) {
+                        mma_commit_pair(&tfull[e & 1]);
+                        ++e;
+                        left = 0;
+                    }
+                }
+            }
+            mma_commit_pair(&done_bar);  // fires in both CTAs when every MMA issued above has completed
+        }
+    } else {
+        const int ew = warp - 2;
+        const int quarter = warp & 3;
+        const int half = ew >> 2;
+        const int h0 = ((BN >> 1) + 15) & ~15;
+        const int cbeg = half ? h0 : 0, cw = half ? BN - h0 : h0;
+        const uint32_t tempty_l[2] = {mapa_rank(&tempty[0], 0), mapa_rank(&tempty[1], 0)};
+        long long e = 0;
+        bool ok = true;
+        for (int u = cid; u < nunits && ok; u += ncl) {
+            const int m2 = m_fastest ? u % mt2 : u / nt;
+            const int n_tile = m_fastest ? u / mt2 : u % nt;
+            const int row = m2 * 2 * BM + rank * BM + quarter * 32 + lane;  // rows past M are skipped
+            const int colt = n_tile * BN + cbeg;
+            if constexpr (kPromote) {
+                float acc[128];
+#pragma unroll
+                for (int i = 0; i < 128; ++i) acc[i] = 0.0f;
+                for (int ep_i = 0; ep_i < epochs; ++ep_i, ++e) {
+                    if (ep.mode == 1 && ep_i == epochs - 1 && row < ep.M) {
+                        const double* o = ep.out + (long long)row * ep.ldc + colt;
+                        for (int c0 = 0; c0 < cw; c0 += 16)
+                            if (colt + c0 < ep.N) asm volatile("prefetch.global.L2 [%0];" ::"l"(o + c0));
+                    }
+                    const int b = (int)(e & 1);
+                    if (!mbar_wait(&tfull[b], (uint32_t)((e >> 1) & 1), &abort_flag, ep.err)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256 + cbeg);
+#pragma unroll
+                    for (int c0 = 0; c0 < 128; c0 += 32)
+                        if (c0 + 32 <= cw) tmem_ld32_add(tbase + (uint32_t)c0, acc + c0);
+#pragma unroll
+                    for (int c0 = 0; c0 < 128; c0 += 16) {
+                        if (c0 >= (cw & ~31) && c0 < cw) {
+                            float v[16];
+                            tmem_ld16(tbase + (uint32_t)c0, v);
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) acc[c0 + i] += v[i];
+                        }
+                    }
+                    fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive_remote(tempty_l[b]);
+                }
+                if (!ok) break;
+                if (row >= ep.M) continue;
+#pragma unroll
+                for (int c0 = 0; c0 < 128; c0 += 16)
+                    if (c0 < cw && colt + c0 < ep.N) store16(ep, planes, row, colt + c0, acc + c0);
+            } else {
+                const int b = (int)(e & 1);
+                if (!mbar_wait(&tfull[b], (uint32_t)((e >> 1) & 1), &abort_flag, ep.err)) {
+                    ok = false;
+                    break;
+                }
+                ++e;
+                fence_after();
+                const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256 + cbeg);
+                for (int c0 = 0; c0 < cw; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(tbase + (uint32_t)c0, v);
+                    if (row < ep.M && colt + c0 < ep.N) store16(ep, planes, row, colt + c0, v);
+                }
+                fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_remote(tempty_l[b]);
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        const uint64_t t0 = gtime();
+        while (!mbar_try_cluster(&done_bar, 0) && gtime() - t0 < WAIT_NS) {
+        }
+        fence_after();
+    }
+    // the leader's MMAs have completed in both CTAs; neither CTA leaves while
+    // the other may still signal its barriers or read its shared memory
+    __syncwarp();
+    cluster_sync();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
 // ---- operand preparation (FP64 -> split BF16) --------------------------------
@@ -509,7 +851,7 @@ EncodeFn encode_fn() {
     return fn;
 }
 
-// 2-D BF16 tensor [rows][cols] (cols contiguous), box {64, box_rows}, 128-byte swizzle
+// 2-D BF16 tensor [rows][cols] (cols contiguous), box {BK, box_rows}, ROW_BYTES swizzle
 CUtensorMap make_map(const void* base, long long rows, long long cols, int box_rows) {
     if (((uintptr_t)base & 15) || (cols * 2) % 16) throw Error(-1, "tensor map: misaligned operand");
     CUtensorMap m;
@@ -518,7 +860,9 @@ CUtensorMap make_map(const void* base, long long rows, long long cols, int box_r
     cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
     CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             ROW_BYTES == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) throw Error(-3, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
     return m;
@@ -527,6 +871,8 @@ CUtensorMap make_map(const void* base, long long rows, long long cols, int box_r
 // Tile width for N = n columns: minimises n-tiles x per-MMA time, where an
 // M=128, N=bn, K=16 BF16 MMA takes bn/2 tensor cycles but must read 4 KB (A)
 // + 32*bn bytes (B) of shared memory at 128 B/cycle; ties go to the wider tile.
+// bn is a multiple of 16 (so that each CTA's half of the B tile in pair mode
+// is whole 8-row swizzle atoms).
 int pick_bn(int n, int maxbn) {
     int best = maxbn;
     double best_cost = 1e300;
@@ -541,13 +887,18 @@ int pick_bn(int n, int maxbn) {
     return best;
 }
 
-// ekb: accumulation epoch in K blocks (0 = one epoch per tile)
+// ekb: accumulation epoch in 64-deep K blocks (0 = one epoch per tile);
+// pair: 256-row tiles on CTA pairs (k_gemm_pair), else 128-row tiles per CTA
 void launch_gemm(Ctx& c, const Maps& maps, int planes, int a_row0, int b_x0, int M, int N, int K, int BN, int m_fastest,
-                 int ekb, const Epi& ep, double algo_flops) {
+                 int ekb, bool pair, const Epi& ep, double algo_flops) {
     static bool attr = false;
-    static int num_sms = 0;
+    static int num_sms = 0, max_pairs = 0;
+    if (BN % 16 || BN < 16 || BN > 256) throw Error(-1, "ladder: tile width must be a multiple of 16 in [16, 256]");
     if (!attr) {
-        ADC_CUDA(cudaFuncSetAttribute(k_gemm_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+        ADC_CUDA(cudaFuncSetAttribute(k_gemm_bf16x3<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+        ADC_CUDA(cudaFuncSetAttribute(k_gemm_bf16x3<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+        ADC_CUDA(cudaFuncSetAttribute(k_gemm_pair<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+        ADC_CUDA(cudaFuncSetAttribute(k_gemm_pair<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
         int dev = 0;
         ADC_CUDA(cudaGetDevice(&dev));
         ADC_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
@@ -557,20 +908,50 @@ void launch_gemm(Ctx& c, const Maps& maps, int planes, int a_row0, int b_x0, int
     const long long ntiles = (long long)mt * nt;
     if (ntiles <= 0) return;
     if (ntiles > (1LL << 31) - 1) throw Error(-1, "ladder: tile count too large");
-    const int stage_bytes = planes * (A_BYTES + BN * BK * 2);
+    const int stage_bytes = planes * (A_BYTES + (pair ? BN / 2 : BN) * ROW_BYTES);
     const int stages = std::min(MAX_STAGES, (int)((SMEM_BYTES - 1024) / stage_bytes));
     if (stages < 2) throw Error(-1, "ladder: tile too large for shared memory");
-    const int grid = (int)std::min<long long>(ntiles, num_sms);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute cl[1];
+    cl[0].id = cudaLaunchAttributeClusterDimension;
+    cl[0].val.clusterDim.x = 2;
+    cl[0].val.clusterDim.y = 1;
+    cl[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.stream = c.stream;
+    cfg.attrs = cl;
+    cfg.numAttrs = 1;
+    int grid;
+    if (!pair) {
+        grid = (int)std::min<long long>(ntiles, num_sms);
+    } else {
+        if (!max_pairs) {
+            cfg.gridDim = dim3((unsigned)(num_sms / 2 * 2));
+            ADC_CUDA(cudaOccupancyMaxActiveClusters(&max_pairs, (void*)k_gemm_pair<true>, &cfg));
+            if (max_pairs < 1) throw Error(-3, "ladder: no CTA pair fits on the device");
+        }
+        const long long units = (long long)((mt + 1) / 2) * nt;  // 256-row tiles
+        grid = (int)std::min<long long>(units, max_pairs) * 2;
+    }
+    cfg.gridDim = dim3((unsigned)grid);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (c.timing) {
         ADC_CUDA(cudaEventCreate(&e0));
         ADC_CUDA(cudaEventCreate(&e1));
         ADC_CUDA(cudaEventRecord(e0, c.stream));
     }
-    // epoch length in K blocks (MMAs per epoch = ekb * 4 * (3 or 6 products))
-    if (ekb <= 0) ekb = (K + BK - 1) / BK;
-    k_gemm_bf16x3<<<grid, THREADS, SMEM_BYTES, c.stream>>>(maps, planes, a_row0, b_x0, K, BN, stages, m_fastest, mt,
-                                                           nt, ekb, ep);
+    // epoch length in the kernel's K blocks (MMAs per epoch = ekb * BK/16 * (3 or 6 products))
+    ekb = ekb <= 0 ? (K + BK - 1) / BK : ekb * KB_PER_EPOCH_UNIT;
+    // one accumulation epoch per tile: the streaming epilogue without register accumulation
+    const bool promote = ekb < (K + BK - 1) / BK;
+    if (pair) {
+        auto kp = promote ? k_gemm_pair<true> : k_gemm_pair<false>;
+        ADC_CUDA(cudaLaunchKernelEx(&cfg, kp, maps, planes, a_row0, b_x0, K, BN, stages, m_fastest, mt, nt, ekb, ep));
+    } else {
+        auto kern = promote ? k_gemm_bf16x3<true> : k_gemm_bf16x3<false>;
+        kern<<<grid, THREADS, SMEM_BYTES, c.stream>>>(maps, planes, a_row0, b_x0, K, BN, stages, m_fastest, mt, nt, ekb, ep);
+    }
     ++c.kernels;
     ADC_CUDA(cudaGetLastError());
     if (c.timing) {
@@ -586,6 +967,7 @@ void launch_gemm(Ctx& c, const Maps& maps, int planes, int a_row0, int b_x0, int
 
 struct LadderTC {
     int naux = 0, v = 0, vp = 0, chunk = 0;
+    bool pair1 = true, pair2 = true;    // 2-SM tiles (cta_group::2 on CTA pairs) for GEMM1 / GEMM2
     int bn2[4] = {256, 256, 256, 256};  // GEMM2 tile width by plane count (2 or 3)
     __nv_bfloat16 *Bs[3] = {}, *Bp[3] = {};  // three BF16 planes of B^Q in the GEMM1-A and GEMM2-B layouts
     CUtensorMap mBs[3], mBp2[3], mBp3[3];     // GEMM2-B maps exist for both tile widths
@@ -629,8 +1011,9 @@ LadderTC* ladder_tc_create(Ctx& c, const double* Bvv, int naux, int v, int aux_c
         ADC_CUDA(cudaGetLastError());
         for (int p = 0; p < 3; ++p) {
             L->mBs[p] = make_map(L->Bs[p], (long long)naux * v, L->vp, BM);
-            L->mBp2[p] = make_map(L->Bp[p], v, (long long)naux * L->vp, L->bn2[2]);
-            L->mBp3[p] = make_map(L->Bp[p], v, (long long)naux * L->vp, L->bn2[3]);
+            // GEMM2-B boxes: one CTA's half of the tile in pair mode
+            L->mBp2[p] = make_map(L->Bp[p], v, (long long)naux * L->vp, L->pair2 ? L->bn2[2] / 2 : L->bn2[2]);
+            L->mBp3[p] = make_map(L->Bp[p], v, (long long)naux * L->vp, L->pair2 ? L->bn2[3] / 2 : L->bn2[3]);
         }
     } catch (...) {
         delete L;
@@ -657,7 +1040,7 @@ void run_ladder(LadderTC& L, Ctx& c, const double* X, long long nmat, double* ou
         Maps m1;
         for (int p = 0; p < planes; ++p) {
             m1.a[p] = L.mBs[p];
-            m1.b[p] = make_map(xt.p[p], nm * vp, vp, bn1);
+            m1.b[p] = make_map(xt.p[p], nm * vp, vp, L.pair1 ? bn1 / 2 : bn1);
         }
         for (int q0 = 0; q0 < naux; q0 += qc) {
             const int qn = std::min(qc, naux - q0);
@@ -672,7 +1055,7 @@ void run_ladder(LadderTC& L, Ctx& c, const double* X, long long nmat, double* ou
             e1.vp = vp;
             e1.qn = qn;
             e1.err = L.d_err;
-            launch_gemm(c, m1, planes, q0 * v, 0, e1.M, e1.N, vp, bn1, 1, md.epoch1, e1, algo);
+            launch_gemm(c, m1, planes, q0 * v, 0, e1.M, e1.N, vp, bn1, 1, md.epoch1, L.pair1, e1, algo);
             // GEMM2: out[(n,a),b] += sum_(q,d) Z_n[a,(q,d)] B^q[d,b]
             Maps m2;
             for (int p = 0; p < planes; ++p) {
@@ -687,7 +1070,7 @@ void run_ladder(LadderTC& L, Ctx& c, const double* X, long long nmat, double* ou
             e2.ldc = v;
             e2.vec = ((uintptr_t)e2.out % 16 == 0) && (v % 2 == 0);
             e2.err = L.d_err;
-            launch_gemm(c, m2, planes, 0, q0 * vp, e2.M, e2.N, qn * vp, bn2, 0, md.epoch2, e2, algo);
+            launch_gemm(c, m2, planes, 0, q0 * vp, e2.M, e2.N, qn * vp, bn2, 0, md.epoch2, L.pair2, e2, algo);
         }
     }
 }
@@ -728,14 +1111,15 @@ void ladder_tc_apply(LadderTC& L, Ctx& c, const double* X, long long nmat, doubl
     c.arena.release(mk);
 }
 
-// Same ladder (two planes, one accumulation epoch per tile, as in sigma), but every intermediate (split X^T
+// Same ladder (two planes, sigma's accumulation epochs), but every intermediate (split X^T
 // and Z) is carved out of a caller-provided device buffer of `bytes` bytes
 // instead of the handle's scratch arena.  out is overwritten (zeroed, then
 // accumulated).  Returns false (launching nothing) if one matrix and one
 // auxiliary function do not fit in the buffer.
-bool ladder_tc_apply_scratch(LadderTC& L, Ctx& c, const double* X, long long nmat, double* out, void* scratch,
-                             size_t bytes) {
+bool ladder_tc_apply_scratch(LadderTC& L, Ctx& c, const double* X, long long nmat, double* out, const LadderMode& md,
+                             void* scratch, size_t bytes) {
     const int v = L.v, vp = L.vp, naux = L.naux, planes = 2;
+    if (md.planes != 2) throw Error(-1, "ladder: the fixed-scratch path takes two planes");
     const long long per_xt = (long long)vp * vp * 2 * planes;  // split X^T per matrix
     const long long per_mq = (long long)v * vp * 2 * planes;   // Z per (matrix, aux function)
     auto round256 = [](long long b) { return (b + 255) / 256 * 256; };
@@ -756,7 +1140,7 @@ bool ladder_tc_apply_scratch(LadderTC& L, Ctx& c, const double* X, long long nma
     zt.p[0] = (__nv_bfloat16*)(base + round256(mg * per_xt));
     zt.p[1] = zt.p[0] + mg * v * (long long)qc * vp;
     ADC_CUDA(cudaMemsetAsync(out, 0, (size_t)nmat * v * v * sizeof(double), c.stream));
-    run_ladder(L, c, X, nmat, out, LadderMode{planes, 0, 0}, xt, zt, mg, qc);
+    run_ladder(L, c, X, nmat, out, md, xt, zt, mg, qc);
     check_err(L, c);
     return true;
 }

@@ -24,7 +24,7 @@ struct LadderTC;  // owns the BF16 hi/lo copies of B^Q_vv in the GEMM layouts
 LadderTC* ladder_tc_create(Ctx& c, const double* Bvv, int naux, int nvir, int aux_chunk);
 void ladder_tc_destroy(LadderTC* L);
 void ladder_tc_apply(LadderTC& L, Ctx& c, const double* X, long long nmat, double* out, const LadderMode& md);
-bool ladder_tc_apply_scratch(LadderTC& L, Ctx& c, const double* X, long long nmat, double* out, void* scratch,
-                             size_t bytes);
+bool ladder_tc_apply_scratch(LadderTC& L, Ctx& c, const double* X, long long nmat, double* out, const LadderMode& md,
+                             void* scratch, size_t bytes);
 
 }  // namespace adc
