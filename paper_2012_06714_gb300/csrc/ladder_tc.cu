@@ -168,11 +168,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 }
 
 struct Epi {
-    int mode;  // 0: split store of Z (GEMM1), 1: FP64 accumulate (GEMM2)
+    int mode;  // 0: split store of Z (GEMM1, through shared memory and TMA), 1: FP64 accumulate (GEMM2)
     int M, N;
-    // mode 0: row r = (q, a), col j = (n, dp); Z[((n*v + a)*qn + q)*vp + dp], one array per plane
-    __nv_bfloat16* z[3];
-    int v, vp, qn;
+    // mode 0: row r = q*vpa + a (a padded to vpa, a multiple of 32), col j = n*vp + dp;
+    // Z[((n*v + a)*qn + q)*vp + dp] per plane, written through the 4-D tensor maps Maps::z
+    int vpa, vp;
     // mode 1: out[r*ldc + j] += acc
     double* out;
     long long ldc;
@@ -184,66 +184,96 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
 }
 
-// Epilogue store of 16 consecutive FP32 results of one row (col0 a multiple of 16).
-//   mode 0: split into `planes` BF16 planes of Z (GEMM1).  16 columns never
-//           straddle a matrix (vp is a multiple of 32): one full 32-byte sector
-//           per plane.  The split runs on the FMA/ALU pipes: packed
-//           round-to-nearest conversions, BF16 -> FP32 by a 16-bit shift.
-//   mode 1: FP64 accumulate into out (GEMM2).
-__device__ __forceinline__ void store16(const Epi& ep, int planes, int row, int col0, const float* v) {
-    if (ep.mode == 0) {
-        const int q = row / ep.v, a = row - q * ep.v;
-        const int n = col0 / ep.vp, dp = col0 - n * ep.vp;
-        const long long z = (((long long)n * ep.v + a) * ep.qn + q) * ep.vp + dp;
+// FP64 accumulate of 16 consecutive FP32 results of one row into out (GEMM2).
+__device__ __forceinline__ void store_out16(const Epi& ep, int row, int col0, const float* v) {
+    double* o = ep.out + (long long)row * ep.ldc + col0;
+    if (ep.vec && col0 + 16 <= ep.N) {
+        // 8 columns at a time: four 16-byte loads in flight before the stores
 #pragma unroll
         for (int h8 = 0; h8 < 16; h8 += 8) {
-            uint32_t pl[3][4];  // [plane][pair of columns]
+            double2 x[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) x[i] = ((const double2*)(o + h8))[i];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                float r0 = v[h8 + 2 * i], r1 = v[h8 + 2 * i + 1];
-#pragma unroll
-                for (int p = 0; p < 3; ++p) {
-                    if (p < planes) {
-                        const __nv_bfloat162 h = __floats2bfloat162_rn(r0, r1);
-                        const uint32_t u = *(const uint32_t*)&h;
-                        pl[p][i] = u;
-                        r0 -= __uint_as_float(u << 16);
-                        r1 -= __uint_as_float(u & 0xFFFF0000u);
-                    }
-                }
+                x[i].x += (double)v[h8 + 2 * i];
+                x[i].y += (double)v[h8 + 2 * i + 1];
+                ((double2*)(o + h8))[i] = x[i];
             }
-#pragma unroll
-            for (int p = 0; p < 3; ++p)
-                if (p < planes) *(uint4*)(ep.z[p] + z + h8) = make_uint4(pl[p][0], pl[p][1], pl[p][2], pl[p][3]);
         }
     } else {
-        double* o = ep.out + (long long)row * ep.ldc + col0;
-        if (ep.vec && col0 + 16 <= ep.N) {
-            // 8 columns at a time: four 16-byte loads in flight before the stores
 #pragma unroll
-            for (int h8 = 0; h8 < 16; h8 += 8) {
-                double2 x[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) x[i] = ((const double2*)(o + h8))[i];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    x[i].x += (double)v[h8 + 2 * i];
-                    x[i].y += (double)v[h8 + 2 * i + 1];
-                    ((double2*)(o + h8))[i] = x[i];
-                }
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < 16; ++i)
-                if (col0 + i < ep.N) o[i] += (double)v[i];
-        }
+        for (int i = 0; i < 16; ++i)
+            if (col0 + i < ep.N) o[i] += (double)v[i];
     }
 }
 
 struct Maps {
     CUtensorMap a[3];  // A operand planes (hi, mid/lo, lo)
     CUtensorMap b[3];  // B operand planes
+    CUtensorMap z[3];  // GEMM1 output planes: 4-D {dp, q, a, n}, box {16, 1, 32, 1}
 };
+
+// Z store of one warp through shared memory: the warp's 32 rows (one q, 32
+// consecutive a: row0 = q*vpa + a0 with a0 a multiple of 32) x 16 columns (one
+// matrix n), split into `planes` BF16 planes, each written by one TMA store of
+// a 32 x 16 box; rows a >= nvir (padding) and q >= qn are clipped by the
+// tensor map.  stg: this warp's staging, nbuf buffers of planes x 1 KB, reused
+// once the TMA has read them.  The split runs on the FMA/ALU pipes: packed
+// round-to-nearest conversions, BF16 -> FP32 by a 16-bit shift.
+__device__ __forceinline__ void store_z16(const Maps& maps, const Epi& ep, int planes, int row0, int col0, const float* v,
+                                          uint8_t* stg, int nbuf, int& nchunk, int lane) {
+    uint8_t* buf = stg + (nchunk % nbuf) * planes * 1024;
+    if (lane == 0) {
+        if (nbuf == 2)
+            asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        else
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    }
+    __syncwarp();
+#pragma unroll
+    for (int h8 = 0; h8 < 16; h8 += 8) {
+        uint32_t pl[3][4];  // [plane][pair of columns]
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float r0 = v[h8 + 2 * i], r1 = v[h8 + 2 * i + 1];
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                if (p < planes) {
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(r0, r1);
+                    const uint32_t u = *(const uint32_t*)&h;
+                    pl[p][i] = u;
+                    r0 -= __uint_as_float(u << 16);
+                    r1 -= __uint_as_float(u & 0xFFFF0000u);
+                }
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+            if (p < planes)
+                *(uint4*)(buf + p * 1024 + lane * 32 + h8 * 2) = make_uint4(pl[p][0], pl[p][1], pl[p][2], pl[p][3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    if (lane == 0) {
+        const int q = row0 / ep.vpa, a0 = row0 - q * ep.vpa;
+        const int n = col0 / ep.vp, dp0 = col0 - n * ep.vp;
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+            if (p < planes)
+                asm volatile(
+                    "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];" ::"l"(
+                        (uint64_t)&maps.z[p]),
+                    "r"(su32(buf + p * 1024)), "r"(dp0), "r"(q), "r"(a0), "r"(n)
+                    : "memory");
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+    ++nchunk;
+}
+__device__ __forceinline__ void store_z_drain(int lane) {
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    __syncwarp();
+}
 
 // Persistent GEMM C = A B^T with split-BF16 operands.  Roles: warp 0 lane 0
 // issues TMA loads through a ring of `stages` shared-memory stages, running
@@ -265,7 +295,7 @@ struct Maps {
 template <bool kPromote>
 __global__ void __launch_bounds__(THREADS, 1)
     k_gemm_bf16x3(const __grid_constant__ Maps maps, int planes, int a_row0, int b_x0, int K, int BN, int stages,
-                  int m_fastest, int mt, int nt, int ekb, Epi ep) {
+                  int m_fastest, int mt, int nt, int ekb, int nbuf, Epi ep) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ uint64_t full_bar[MAX_STAGES], empty_bar[MAX_STAGES], tfull[2], tempty[2], done_bar;
@@ -404,6 +434,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         // widths are multiples of 16 (BN is) and at most 128.
         const int h0 = ((BN >> 1) + 15) & ~15;
         const int cbeg = half ? h0 : 0, cw = half ? BN - h0 : h0;
+        // Z staging of this warp (mode 0) after the pipeline stages
+        uint8_t* stg = smem + (size_t)stages * STAGE + (size_t)ew * nbuf * planes * 1024;
+        int nchunk = 0;
         long long e = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
@@ -447,10 +480,14 @@ __global__ void __launch_bounds__(THREADS, 1)
                     if (lane == 0) mbar_arrive(&tempty[b]);
                 }
                 if (!ok) break;
-                if (row >= ep.M) continue;
 #pragma unroll
-                for (int c0 = 0; c0 < 128; c0 += 16)
-                    if (c0 < cw && colt + c0 < ep.N) store16(ep, planes, row, colt + c0, acc + c0);
+                for (int c0 = 0; c0 < 128; c0 += 16) {
+                    if (c0 >= cw || colt + c0 >= ep.N) continue;  // uniform across the warp
+                    if (ep.mode == 0)
+                        store_z16(maps, ep, planes, row - lane, colt + c0, acc + c0, stg, nbuf, nchunk, lane);
+                    else if (row < ep.M)
+                        store_out16(ep, row, colt + c0, acc + c0);
+                }
             } else {
                 // one epoch per tile: stream TMEM -> global 16 columns at a time, then release the buffer
                 const int b = (int)(e & 1);
@@ -464,13 +501,19 @@ __global__ void __launch_bounds__(THREADS, 1)
                 for (int c0 = 0; c0 < cw; c0 += 16) {
                     float v[16];
                     tmem_ld16(tbase + (uint32_t)c0, v);  // warp-collective: every lane loads
-                    if (row < ep.M && colt + c0 < ep.N) store16(ep, planes, row, colt + c0, v);
+                    if (colt + c0 < ep.N) {  // uniform across the warp
+                        if (ep.mode == 0)
+                            store_z16(maps, ep, planes, row - lane, colt + c0, v, stg, nbuf, nchunk, lane);
+                        else if (row < ep.M)
+                            store_out16(ep, row, colt + c0, v);
+                    }
                 }
                 fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[b]);
             }
         }
+        if (ep.mode == 0) store_z_drain(lane);  // this warp's Z stores have completed
     }
     fence_before();
     __syncthreads();
@@ -555,7 +598,7 @@ __device__ bool mbar_wait_cluster(uint64_t* b, uint32_t parity, volatile int* ab
 template <bool kPromote>
 __global__ void __launch_bounds__(THREADS, 1)
     k_gemm_pair(const __grid_constant__ Maps maps, int planes, int a_row0, int b_x0, int K, int BN, int stages,
-                int m_fastest, int mt, int nt, int ekb, Epi ep) {
+                int m_fastest, int mt, int nt, int ekb, int nbuf, Epi ep) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ uint64_t full_bar[MAX_STAGES], empty_bar[MAX_STAGES], tfull[2], tempty[2], done_bar;
@@ -699,6 +742,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int h0 = ((BN >> 1) + 15) & ~15;
         const int cbeg = half ? h0 : 0, cw = half ? BN - h0 : h0;
         const uint32_t tempty_l[2] = {mapa_rank(&tempty[0], 0), mapa_rank(&tempty[1], 0)};
+        uint8_t* stg = smem + (size_t)stages * STAGE + (size_t)ew * nbuf * planes * 1024;
+        int nchunk = 0;
         long long e = 0;
         bool ok = true;
         for (int u = cid; u < nunits && ok; u += ncl) {
@@ -740,10 +785,14 @@ __global__ void __launch_bounds__(THREADS, 1)
                     if (lane == 0) mbar_arrive_remote(tempty_l[b]);
                 }
                 if (!ok) break;
-                if (row >= ep.M) continue;
 #pragma unroll
-                for (int c0 = 0; c0 < 128; c0 += 16)
-                    if (c0 < cw && colt + c0 < ep.N) store16(ep, planes, row, colt + c0, acc + c0);
+                for (int c0 = 0; c0 < 128; c0 += 16) {
+                    if (c0 >= cw || colt + c0 >= ep.N) continue;  // uniform across the warp
+                    if (ep.mode == 0)
+                        store_z16(maps, ep, planes, row - lane, colt + c0, acc + c0, stg, nbuf, nchunk, lane);
+                    else if (row < ep.M)
+                        store_out16(ep, row, colt + c0, acc + c0);
+                }
             } else {
                 const int b = (int)(e & 1);
                 if (!mbar_wait(&tfull[b], (uint32_t)((e >> 1) & 1), &abort_flag, ep.err)) {
@@ -756,13 +805,19 @@ __global__ void __launch_bounds__(THREADS, 1)
                 for (int c0 = 0; c0 < cw; c0 += 16) {
                     float v[16];
                     tmem_ld16(tbase + (uint32_t)c0, v);
-                    if (row < ep.M && colt + c0 < ep.N) store16(ep, planes, row, colt + c0, v);
+                    if (colt + c0 < ep.N) {  // uniform across the warp
+                        if (ep.mode == 0)
+                            store_z16(maps, ep, planes, row - lane, colt + c0, v, stg, nbuf, nchunk, lane);
+                        else if (row < ep.M)
+                            store_out16(ep, row, colt + c0, v);
+                    }
                 }
                 fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive_remote(tempty_l[b]);
             }
         }
+        if (ep.mode == 0) store_z_drain(lane);  // this warp's Z stores have completed
     }
     fence_before();
     __syncthreads();
@@ -796,13 +851,16 @@ struct Planes {
     __nv_bfloat16* p[3];
 };
 
-// Bs[(Q,a)][cp] = B^Q[a][c] (c < v), zero pad
+// Bs[(Q,a')][c'] = B^Q[a][c] (a, c < v), zero pad: a' and c' both run over vp,
+// so that GEMM1's 32-row warp slices never straddle two auxiliary functions
 __global__ void k_split_Bs(const double* __restrict__ B, int naux, int v, int vp, int planes, Planes o) {
-    long long n = (long long)naux * v * vp;
+    long long n = (long long)naux * vp * vp;
     GRID_STRIDE(x, n) {
         int cp = x % vp;
-        long long qa = x / vp;
-        double val = cp < v ? B[qa * v + cp] : 0.0;
+        long long r = x / vp;
+        int a = r % vp;
+        long long Q = r / vp;
+        double val = (cp < v && a < v) ? B[(Q * v + a) * v + cp] : 0.0;
         splitp(val, planes, o.p[0] + x, o.p[1] + x, o.p[2] + x);
     }
 }
@@ -873,6 +931,23 @@ CUtensorMap make_map(const void* base, long long rows, long long cols, int box_r
 // + 32*bn bytes (B) of shared memory at 128 B/cycle; ties go to the wider tile.
 // bn is a multiple of 16 (so that each CTA's half of the B tile in pair mode
 // is whole 8-row swizzle atoms).
+// Z plane [nm][v][qn][vp] (dp fastest) as a 4-D tensor {dp, q, a, n} for the
+// GEMM1 epilogue's TMA stores: box {16, 1, 32, 1}, no swizzle; stores clip at
+// the tensor bounds (a >= v, q >= qn, n >= nm)
+CUtensorMap make_map_z(const void* base, int vp, int qn, int v, long long nm) {
+    if (((uintptr_t)base & 15) || (vp * 2) % 16) throw Error(-1, "tensor map: misaligned Z plane");
+    CUtensorMap m;
+    cuuint64_t dims[4] = {(cuuint64_t)vp, (cuuint64_t)qn, (cuuint64_t)v, (cuuint64_t)nm};
+    cuuint64_t strides[3] = {(cuuint64_t)vp * 2, (cuuint64_t)qn * vp * 2, (cuuint64_t)v * qn * vp * 2};
+    cuuint32_t box[4] = {16, 1, 32, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, es,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw Error(-3, "cuTensorMapEncodeTiled (Z) failed: " + std::to_string((int)r));
+    return m;
+}
+
 int pick_bn(int n, int maxbn) {
     int best = maxbn;
     double best_cost = 1e300;
@@ -909,7 +984,14 @@ void launch_gemm(Ctx& c, const Maps& maps, int planes, int a_row0, int b_x0, int
     if (ntiles <= 0) return;
     if (ntiles > (1LL << 31) - 1) throw Error(-1, "ladder: tile count too large");
     const int stage_bytes = planes * (A_BYTES + (pair ? BN / 2 : BN) * ROW_BYTES);
-    const int stages = std::min(MAX_STAGES, (int)((SMEM_BYTES - 1024) / stage_bytes));
+    // mode 0: per-warp Z staging of planes x 1 KB, double-buffered when two pipeline stages still fit
+    const int stg = ep.mode == 0 ? EPI_WARPS * planes * 1024 : 0;
+    int nbuf = ep.mode == 0 ? 2 : 0;
+    int stages = std::min(MAX_STAGES, (int)((SMEM_BYTES - 1024 - nbuf * stg) / stage_bytes));
+    if (stages < 2 && nbuf == 2) {
+        nbuf = 1;
+        stages = std::min(MAX_STAGES, (int)((SMEM_BYTES - 1024 - stg) / stage_bytes));
+    }
     if (stages < 2) throw Error(-1, "ladder: tile too large for shared memory");
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute cl[1];
@@ -947,10 +1029,11 @@ void launch_gemm(Ctx& c, const Maps& maps, int planes, int a_row0, int b_x0, int
     const bool promote = ekb < (K + BK - 1) / BK;
     if (pair) {
         auto kp = promote ? k_gemm_pair<true> : k_gemm_pair<false>;
-        ADC_CUDA(cudaLaunchKernelEx(&cfg, kp, maps, planes, a_row0, b_x0, K, BN, stages, m_fastest, mt, nt, ekb, ep));
+        ADC_CUDA(cudaLaunchKernelEx(&cfg, kp, maps, planes, a_row0, b_x0, K, BN, stages, m_fastest, mt, nt, ekb, nbuf, ep));
     } else {
         auto kern = promote ? k_gemm_bf16x3<true> : k_gemm_bf16x3<false>;
-        kern<<<grid, THREADS, SMEM_BYTES, c.stream>>>(maps, planes, a_row0, b_x0, K, BN, stages, m_fastest, mt, nt, ekb, ep);
+        kern<<<grid, THREADS, SMEM_BYTES, c.stream>>>(maps, planes, a_row0, b_x0, K, BN, stages, m_fastest, mt, nt, ekb, nbuf,
+                                                      ep);
     }
     ++c.kernels;
     ADC_CUDA(cudaGetLastError());
@@ -994,23 +1077,24 @@ LadderTC* ladder_tc_create(Ctx& c, const double* Bvv, int naux, int v, int aux_c
         L->chunk = aux_chunk;
         L->bn2[2] = pick_bn(v, 256);
         L->bn2[3] = pick_bn(v, 128);
-        const long long nB = (long long)naux * v * L->vp;
+        const long long nB = (long long)naux * v * L->vp;    // Bp planes
+        const long long nBs = (long long)naux * L->vp * L->vp;  // Bs planes (rows padded)
         Planes ps{}, pp{};
         for (int p = 0; p < 3; ++p) {
-            ADC_CUDA(cudaMalloc(&L->Bs[p], nB * 2));
+            ADC_CUDA(cudaMalloc(&L->Bs[p], nBs * 2));
             ADC_CUDA(cudaMalloc(&L->Bp[p], nB * 2));
             ps.p[p] = L->Bs[p];
             pp.p[p] = L->Bp[p];
         }
         ADC_CUDA(cudaMalloc(&L->d_err, sizeof(int)));
         ADC_CUDA(cudaMemsetAsync(L->d_err, 0, sizeof(int), c.stream));
-        k_split_Bs<<<grid_for(nB), 256, 0, c.stream>>>(Bvv, naux, v, L->vp, 3, ps);
+        k_split_Bs<<<grid_for(nBs), 256, 0, c.stream>>>(Bvv, naux, v, L->vp, 3, ps);
         ++c.kernels;
         k_split_Bp<<<grid_for(nB), 256, 0, c.stream>>>(Bvv, naux, v, L->vp, 3, pp);
         ++c.kernels;
         ADC_CUDA(cudaGetLastError());
         for (int p = 0; p < 3; ++p) {
-            L->mBs[p] = make_map(L->Bs[p], (long long)naux * v, L->vp, BM);
+            L->mBs[p] = make_map(L->Bs[p], (long long)naux * L->vp, L->vp, BM);
             // GEMM2-B boxes: one CTA's half of the tile in pair mode
             L->mBp2[p] = make_map(L->Bp[p], v, (long long)naux * L->vp, L->pair2 ? L->bn2[2] / 2 : L->bn2[2]);
             L->mBp3[p] = make_map(L->Bp[p], v, (long long)naux * L->vp, L->pair2 ? L->bn2[3] / 2 : L->bn2[3]);
@@ -1045,17 +1129,16 @@ void run_ladder(LadderTC& L, Ctx& c, const double* X, long long nmat, double* ou
         for (int q0 = 0; q0 < naux; q0 += qc) {
             const int qn = std::min(qc, naux - q0);
             const double algo = 2.0 * (double)qn * v * (double)nm * v * v;  // unpadded B^q X_n products
-            // GEMM1: Z[(q,a),(n,d)] = sum_c B^q[a,c] X_n[c,d]
+            // GEMM1: Z[(q,a),(n,d)] = sum_c B^q[a,c] X_n[c,d]  (rows q*vp + a, a padded to vp)
             Epi e1{};
             e1.mode = 0;
-            e1.M = qn * v;
+            e1.M = qn * vp;
             e1.N = (int)(nm * vp);
-            for (int p = 0; p < 3; ++p) e1.z[p] = zt.p[p];
-            e1.v = v;
+            e1.vpa = vp;
             e1.vp = vp;
-            e1.qn = qn;
             e1.err = L.d_err;
-            launch_gemm(c, m1, planes, q0 * v, 0, e1.M, e1.N, vp, bn1, 1, md.epoch1, L.pair1, e1, algo);
+            for (int p = 0; p < planes; ++p) m1.z[p] = make_map_z(zt.p[p], vp, qn, v, nm);
+            launch_gemm(c, m1, planes, q0 * vp, 0, e1.M, e1.N, vp, bn1, 1, md.epoch1, L.pair1, e1, algo);
             // GEMM2: out[(n,a),b] += sum_(q,d) Z_n[a,(q,d)] B^q[d,b]
             Maps m2;
             for (int p = 0; p < planes; ++p) {
