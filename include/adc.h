@@ -59,13 +59,13 @@ extern "C" {
 #define ADC_IP (-1)
 
 #define ADC_PREC_FP64 0   /* every contraction in FP64                              */
-#define ADC_PREC_BF16X3 1 /* DF ladder on tcgen05 tensor cores: Davidson sigma with  */
-                          /* hi/lo BF16 operands (3 products), the setup ladder of  */
-                          /* the amplitudes with hi/mid/lo planes (6 products);     */
-                          /* FP32 accumulation within an auxiliary chunk, FP64      */
-                          /* across chunks; the large other contractions FP32-      */
-                          /* accurate (BF16x9 emulated GEMM); FP64 vectors, subspace*/
-                          /* and accumulation; converged roots refined (refine)     */
+#define ADC_PREC_BF16X3 1 /* DF ladder on tcgen05 tensor cores with hi/lo BF16       */
+                          /* operands (3 products), FP32 accumulation (partial sums */
+                          /* promoted to round-to-nearest FP32 registers) within an */
+                          /* auxiliary chunk, FP64 across chunks; the large other   */
+                          /* contractions on the same kernel in sigma and FP32-     */
+                          /* accurate (BF16x9 emulated GEMM) in setup; FP64 vectors,*/
+                          /* subspace and accumulation; converged roots refined     */
 
 typedef struct adc_handle adc_handle; /* opaque */
 
@@ -78,13 +78,18 @@ typedef struct {
     int aux_chunk;           /* auxiliary functions per ladder chunk; 0 = automatic   */
     int keep_per_root;       /* Ritz vectors kept per root when the space is          */
                              /* collapsed (thick restart, default 2)                  */
-    int contractions;        /* non-ladder contractions: -1 follow precision (default)*/
-                             /* 0 FP64 DGEMM, 1 FP32-accurate emulated GEMM           */
-    int refine;              /* BF16X3 only: 1 (default) re-evaluates sigma of the    */
-                             /* converged roots once with the accurate ladder (three  */
-                             /* planes, FP32 partial sums promoted every 64-deep K    */
-                             /* block) and FP64 for every other contraction, then     */
-                             /* Rayleigh-Ritz in their span; 0 skips it               */
+    int contractions;        /* non-ladder contractions: -1 follow precision (default:*/
+                             /* FP64 -> 0; BF16X3 -> 2 in sigma, 1 in setup and      */
+                             /* refinement), 0 FP64 DGEMM, 1 FP32-accurate emulated   */
+                             /* GEMM, 2 as 1 but unbatched contractions that tile the */
+                             /* GPU run on the tensor-core split-BF16 GEMM of the     */
+                             /* ladder (setup and refinement use 1)                   */
+    int refine;              /* BF16X3 only: converged roots are re-evaluated once    */
+                             /* with the accurate ladder (FP32 partial sums promoted  */
+                             /* every 64-deep K block) and Rayleigh-Ritz in their     */
+                             /* span; 1 (default): other contractions as in sigma     */
+                             /* (FP32-accurate), 2: FP64 for every other contraction, */
+                             /* 0: no refinement                                      */
 } adc_options;
 
 /* Fill *opt with the defaults listed above.  Returns ADC_OK or ADC_ERR_ARG (NULL). */

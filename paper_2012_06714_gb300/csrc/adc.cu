@@ -41,6 +41,7 @@ struct adc_handle {
     // setup and refinement: every K block, drift ~4e-7)
     LadderMode lm_sigma{2, 0, 16}, lm_setup{2, 1, 1}, lm_refine{2, 1, 1};
     bool refining = false;  // sigma evaluates with lm_refine
+    int cmode_setup = 0, cmode_sigma = 0;  // Ctx::gemm_mode in setup / in sigma
     double* Lt = nullptr;    // setup only: sum_cd (ac|bd) t_kl^cd, shared by t2(2) and the EA 1p-1p block
     std::vector<void*> owned;
     std::string err;
@@ -390,7 +391,11 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
     ADC_BLAS(cublasCreate(&c.blas));
     ADC_BLAS(cublasSetStream(c.blas, c.stream));
     ADC_BLAS(cublasSetMathMode(c.blas, CUBLAS_DEFAULT_MATH));
-    c.gemm_mode = h->opt.contractions >= 0 ? (h->opt.contractions ? 1 : 0) : (h->opt.precision != ADC_PREC_FP64 ? 1 : 0);
+    // contraction arithmetic: setup (and refinement) FP32-accurate at most; sigma may use the tensor-core split GEMM
+    const int cm = h->opt.contractions >= 0 ? h->opt.contractions : (h->opt.precision != ADC_PREC_FP64 ? 2 : 0);
+    h->cmode_sigma = cm;
+    h->cmode_setup = cm > 1 ? 1 : cm;
+    c.gemm_mode = h->cmode_setup;
     const long long o = h->o, v = h->v, Q = h->naux, nmo = o + v;
     h->eps = h->dmalloc(nmo);
     ADC_CUDA(cudaMemcpyAsync(h->eps, eps_in, nmo * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -639,10 +644,18 @@ static void sigma_ip(adc_handle* h, const double* Xin, double* Sout, long long n
 }
 
 static void sigma_device(adc_handle* h, const double* X, double* S, long long nvec) {
+    Ctx& c = h->ctx;
+    if (!h->refining) c.gemm_mode = h->cmode_sigma;
     if (h->kind == ADC_EA)
         sigma_ea(h, X, S, nvec);
     else
         sigma_ip(h, X, S, nvec);
+    if (c.d_err) {
+        int e = 0;
+        ADC_CUDA(cudaMemcpyAsync(&e, c.d_err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+        ADC_CUDA(cudaStreamSynchronize(c.stream));
+        if (e) throw Error(ADC_ERR_TIMEOUT, "sigma: a bounded device wait of the tensor-core GEMM timed out");
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -885,8 +898,9 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
         d.k += kept;
     }
     // Final refinement (mixed precision): sigma of the Ritz vectors once more
-    // with the accurate ladder arithmetic (lm_refine) and FP64 for every other
-    // contraction, then Rayleigh-Ritz in their span.  The Davidson residual
+    // with the accurate ladder arithmetic (lm_refine) and, for refine = 2, FP64
+    // for every other contraction (refine = 1 keeps them FP32-accurate), then
+    // Rayleigh-Ritz in their span.  The Davidson residual
     // makes the vector error first order, its energy error second order, so
     // the refined energies carry the accurate operator's error only.
     double refine_shift = 0.0, refine_sec = 0.0;
@@ -894,7 +908,8 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
         auto tr = std::chrono::steady_clock::now();
         const int saved = c.gemm_mode;
         h->refining = true;
-        c.gemm_mode = 0;
+        // other contractions FP32-accurate (refine = 1) or FP64 (refine = 2)
+        c.gemm_mode = h->opt.refine >= 2 ? 0 : std::min(h->cmode_sigma, 1);
         try {
             sigma_device(h, X, AX, nroots);
         } catch (...) {
@@ -1101,6 +1116,10 @@ int adc_setup(const double* eps, const double* Bq, int nocc, int nvir, int naux,
     }
     if (opt && (opt->precision != ADC_PREC_FP64 && opt->precision != ADC_PREC_BF16X3)) {
         g_setup_error = "adc_setup: unknown precision";
+        return ADC_ERR_ARG;
+    }
+    if (opt && (opt->contractions < -1 || opt->contractions > 2 || opt->refine < 0 || opt->refine > 2)) {
+        g_setup_error = "adc_setup: contractions must be -1..2 and refine 0..2";
         return ADC_ERR_ARG;
     }
     adc_handle* h = new adc_handle();

@@ -4,7 +4,10 @@
 #include <cstring>
 #include <map>
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
+#include "ladder_tc.cuh"
 
 namespace adc {
 
@@ -55,6 +58,29 @@ __global__ void axpby_kernel(long long n, double alpha, const double* __restrict
 __global__ void fill_kernel(long long n, double v, double* __restrict__ y) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         y[i] = v;
+}
+
+// out[p][r*Kp + k] (two BF16 planes) from the permuted input, zero for k >= K
+__global__ void permute_split_kernel(const double* __restrict__ in, __nv_bfloat16* __restrict__ o0,
+                                     __nv_bfloat16* __restrict__ o1, PermArgs a, long long rows, long long K, long long Kp) {
+    const long long total = rows * Kp;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long r = idx / Kp, k = idx - r * Kp;
+        double x = 0.0;
+        if (k < K) {
+            long long lin = r * K + k, off = 0;
+            for (int j = a.nd - 1; j >= 0; --j) {
+                long long cj = lin % a.dout[j];
+                lin /= a.dout[j];
+                off += cj * a.sin[j];
+            }
+            x = in[off];
+        }
+        const __nv_bfloat16 h = __double2bfloat16(x);
+        o0[idx] = h;
+        o1[idx] = __double2bfloat16(x - (double)__bfloat162float(h));
+    }
 }
 
 inline int grid_for(long long n) {
@@ -108,6 +134,18 @@ static void permute_cvt(Ctx& c, const Tin* in, const Shape& s, const int* perm, 
     PermArgs a = perm_args(s, perm, total);
     if (total == 0) return;
     permute_cvt_kernel<Tin, Tout><<<grid_for(total), 256, 0, c.stream>>>(in, out, a, total, alpha, beta);
+    ++c.kernels;
+    ADC_CUDA(cudaGetLastError());
+}
+
+void split_planes(Ctx& c, const double* in, const Shape& s, const int* perm, long long rows, long long K, long long Kp,
+                  void* const* out) {
+    long long total;
+    PermArgs a = perm_args(s, perm, total);
+    if (total != rows * K) throw Error(-1, "split_planes: shape mismatch");
+    if (rows * Kp == 0) return;
+    permute_split_kernel<<<grid_for(rows * Kp), 256, 0, c.stream>>>(in, (__nv_bfloat16*)out[0], (__nv_bfloat16*)out[1], a,
+                                                                    rows, K, Kp);
     ++c.kernels;
     ADC_CUDA(cudaGetLastError());
 }
@@ -264,6 +302,65 @@ static void einsum_fp32(Ctx& c, const std::string& la, const std::string& lb, co
     permute_cvt<float, double>(c, T32, sh, perm, C, alpha, beta);
 }
 
+// Tensor-core contraction (gemm_mode 2): operands permuted into K-major GEMM
+// order and split into two BF16 planes (constant operands once, cached), the
+// tcgen05 split-BF16 GEMM into an FP64 temporary, then permuted and
+// accumulated into the output.
+static void einsum_tc(Ctx& c, const std::string& la, const std::string& lb, const std::string& lc,
+                      std::map<char, long long>& dim, const std::string& fa, const std::string& fb, const std::string& con,
+                      double alpha, const double* Ap, const double* Bp, double beta, double* C, bool constA, bool constB) {
+    auto prod = [&](const std::string& l) {
+        long long p = 1;
+        for (char x : l) p *= dim[x];
+        return p;
+    };
+    const long long M = prod(fa), N = prod(fb), K = prod(con), Kp = (K + 7) / 8 * 8;
+    auto planes_of = [&](const double* src, const std::string& ls, const std::string& lt, long long rows, bool constant) {
+        Shape sh;
+        sh.nd = (int)ls.size();
+        for (int j = 0; j < sh.nd; ++j) sh.d[j] = dim.at(ls[j]);
+        int perm[kMaxDim];
+        std::string key = "bf16x2:";
+        for (int j = 0; j < sh.nd; ++j) {
+            perm[j] = (int)ls.find(lt[j]);
+            key += (char)('0' + perm[j]);
+            key += ':';
+            key += std::to_string(sh.d[j]);
+            key += ',';
+        }
+        key += std::to_string(K);
+        void* base = nullptr;
+        if (constant) {
+            auto it = c.bf16cache.find({src, key});
+            if (it != c.bf16cache.end()) return it->second;
+            ADC_CUDA(cudaMalloc(&base, 2 * rows * Kp * 2));
+            c.bf16cache[{src, key}] = base;
+        } else {
+            base = c.arena.alloc(2 * rows * Kp * 2);
+        }
+        void* out[2] = {base, (char*)base + rows * Kp * 2};
+        split_planes(c, src, sh, perm, rows, K, Kp, out);
+        return base;
+    };
+    void* pa = planes_of(Ap, la, fa + con, M, constA);
+    void* pb = planes_of(Bp, lb, fb + con, N, constB);
+    if (!c.d_err) {
+        ADC_CUDA(cudaMalloc(&c.d_err, sizeof(int)));
+        ADC_CUDA(cudaMemsetAsync(c.d_err, 0, sizeof(int), c.stream));
+    }
+    double* T = c.arena.dalloc((size_t)(M * N));
+    const void* A2[2] = {pa, (const char*)pa + M * Kp * 2};
+    const void* B2[2] = {pb, (const char*)pb + N * Kp * 2};
+    tc_gemm(c, A2, B2, M, N, Kp, 2.0 * M * N * K, T);
+    std::string tord = fa + fb;
+    Shape sh;
+    sh.nd = (int)tord.size();
+    for (int j = 0; j < sh.nd; ++j) sh.d[j] = dim[tord[j]];
+    int perm[kMaxDim];
+    for (int j = 0; j < sh.nd; ++j) perm[j] = (int)tord.find(lc[j]);
+    permute(c, T, sh, perm, C, alpha, beta);
+}
+
 void einsum(Ctx& c, const char* specstr, double alpha, const T& A, const T& B, double beta, double* C,
             const std::vector<long long>& cdims) {
     Spec sp = parse(specstr);
@@ -307,7 +404,12 @@ void einsum(Ctx& c, const char* specstr, double alpha, const T& A, const T& B, d
     };
     long long nb = prod(batch), M = prod(fa), N = prod(fb), K = prod(con);
     Arena::Mark mk = c.arena.mark();
-    if (c.gemm_mode == 1 && 2.0 * nb * M * N * K >= c.fp32_min_flops) {
+    if (c.gemm_mode == 2 && nb == 1 && 2.0 * M * N * K >= c.fp32_min_flops && tc_gemm_worthwhile(M, N, K)) {
+        einsum_tc(c, sp.a, sp.b, sp.c, dim, fa, fb, con, alpha, A.p, B.p, beta, C, A.constant, B.constant);
+        c.arena.release(mk);
+        return;
+    }
+    if (c.gemm_mode >= 1 && 2.0 * nb * M * N * K >= c.fp32_min_flops) {
         einsum_fp32(c, sp.a, sp.b, sp.c, dim, batch, fa, fb, con, alpha, A.p, B.p, beta, C, A.constant, B.constant);
         c.arena.release(mk);
         return;

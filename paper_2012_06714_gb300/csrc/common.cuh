@@ -100,7 +100,10 @@ struct Ctx {
     long long kernels = 0;  // own kernel launches issued (for reporting)
     // 0: every contraction in FP64 (DGEMM).  1: contractions of >= fp32_min_flops
     // run as FP32-accurate GEMMs (BF16x9 emulation on the tensor cores), with
-    // FP64 inputs rounded to FP32 and results accumulated into FP64.
+    // FP64 inputs rounded to FP32 and results accumulated into FP64.  2: as 1,
+    // but unbatched contractions that tile the GPU well run on the tcgen05
+    // split-BF16 GEMM (two planes, FP32 partial sums promoted every 16 K
+    // blocks, FP64 result).
     int gemm_mode = 0;
     double fp32_min_flops = 2e8;
     int emulation_ok = -1;  // -1 unknown, 1 BF16x9 emulation available, 0 plain FP32
@@ -111,8 +114,13 @@ struct Ctx {
     long long kernels_at_start = 0;
     // FP32 copies (in GEMM operand order) of operands marked constant, reused across calls
     std::map<std::pair<const void*, std::string>, float*> f32cache;
+    // split BF16 planes (K-major GEMM operand order) of operands marked constant
+    std::map<std::pair<const void*, std::string>, void*> bf16cache;
+    int* d_err = nullptr;  // device flag raised by a bounded wait that gave up (tensor-core GEMMs)
     ~Ctx() {
         for (auto& kv : f32cache) cudaFree(kv.second);
+        for (auto& kv : bf16cache) cudaFree(kv.second);
+        if (d_err) cudaFree(d_err);
         for (auto e : ev_start) cudaEventDestroy(e);
         for (auto e : ev_stop) cudaEventDestroy(e);
     }
@@ -138,6 +146,12 @@ struct T {
 // C[lc] = beta * C + alpha * sum A[la] B[lb] ; spec "la,lb->lc" with single-letter indices.
 void einsum(Ctx& c, const char* spec, double alpha, const T& A, const T& B, double beta, double* C,
             const std::vector<long long>& cdims);
+
+// Permute `in` (shape s, output axis j = input axis perm[j]) into row-major
+// [rows][K] order and split each value x into BF16 planes x = p0 + p1 (two
+// planes), written K-major as out[p][r * Kp + k] with zeros for K <= k < Kp.
+void split_planes(Ctx& c, const double* in, const Shape& s, const int* perm, long long rows, long long K, long long Kp,
+                  void* const* out);
 
 // Row-major GEMM: C[MxN] = alpha op(A) op(B) + beta C, batched with strides.
 void gemm(Ctx& c, bool ta, bool tb, long long M, long long N, long long K, double alpha, const double* A, long long lda,

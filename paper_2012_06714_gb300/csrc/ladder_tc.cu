@@ -168,12 +168,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 }
 
 struct Epi {
-    int mode;  // 0: split store of Z (GEMM1, through shared memory and TMA), 1: FP64 accumulate (GEMM2)
+    int mode;  // 0: split store of Z (GEMM1, through shared memory and TMA), 1: FP64 accumulate (GEMM2),
+               // 2: FP64 store (generic contraction)
     int M, N;
     // mode 0: row r = q*vpa + a (a padded to vpa, a multiple of 32), col j = n*vp + dp;
     // Z[((n*v + a)*qn + q)*vp + dp] per plane, written through the 4-D tensor maps Maps::z
     int vpa, vp;
-    // mode 1: out[r*ldc + j] += acc
+    // modes 1, 2: out[r*ldc + j] (+)= acc
     double* out;
     long long ldc;
     int vec;  // out rows 16-byte aligned (vector loads and stores)
@@ -184,9 +185,21 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
 }
 
-// FP64 accumulate of 16 consecutive FP32 results of one row into out (GEMM2).
+// 16 consecutive FP32 results of one row into the FP64 output: accumulated
+// (mode 1, GEMM2 of the ladder) or stored (mode 2, generic contractions).
 __device__ __forceinline__ void store_out16(const Epi& ep, int row, int col0, const float* v) {
     double* o = ep.out + (long long)row * ep.ldc + col0;
+    if (ep.mode == 2) {
+        if (ep.vec && col0 + 16 <= ep.N) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) ((double2*)o)[i] = make_double2((double)v[2 * i], (double)v[2 * i + 1]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                if (col0 + i < ep.N) o[i] = (double)v[i];
+        }
+        return;
+    }
     if (ep.vec && col0 + 16 <= ep.N) {
         // 8 columns at a time: four 16-byte loads in flight before the stores
 #pragma unroll
@@ -1226,6 +1239,36 @@ bool ladder_tc_apply_scratch(LadderTC& L, Ctx& c, const double* X, long long nma
     run_ladder(L, c, X, nmat, out, md, xt, zt, mg, qc);
     check_err(L, c);
     return true;
+}
+
+// ---- generic split-BF16 contraction (gemm_mode 2) --------------------------
+bool tc_gemm_worthwhile(long long M, long long N, long long K) {
+    // enough 256 x 256 tiles to occupy the CTA pairs (no split-K in the kernel),
+    // K long enough to amortise a tile, and 32-bit tile coordinates
+    const long long tiles = ((M + 255) / 256) * ((N + 255) / 256);
+    return tiles >= 64 && K >= 256 && M < (1LL << 30) && N < (1LL << 30) && K < (1LL << 30);
+}
+
+void tc_gemm(Ctx& c, const void* const* A, const void* const* B, long long M, long long N, long long Kp, double algo_flops,
+             double* C) {
+    if (!c.d_err) throw Error(-1, "tc_gemm: no device error flag");
+    const int BN = pick_bn((int)std::min<long long>(N, 1 << 20), 256);
+    const bool pair = true;
+    Maps m{};
+    for (int p = 0; p < 2; ++p) {
+        m.a[p] = make_map(A[p], M, Kp, BM);
+        m.b[p] = make_map(B[p], N, Kp, pair ? BN / 2 : BN);
+    }
+    Epi e{};
+    e.mode = 2;
+    e.M = (int)M;
+    e.N = (int)N;
+    e.out = C;
+    e.ldc = N;
+    e.vec = ((uintptr_t)C % 16 == 0) && (N % 2 == 0);
+    e.err = c.d_err;
+    // consecutive tiles share the B tile when A is the smaller operand (A then stays in L2)
+    launch_gemm(c, m, 2, 0, 0, (int)M, (int)N, (int)Kp, BN, M <= N ? 1 : 0, 16, pair, e, algo_flops);
 }
 
 }  // namespace adc

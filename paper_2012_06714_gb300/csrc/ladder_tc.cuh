@@ -27,4 +27,13 @@ void ladder_tc_apply(LadderTC& L, Ctx& c, const double* X, long long nmat, doubl
 bool ladder_tc_apply_scratch(LadderTC& L, Ctx& c, const double* X, long long nmat, double* out, const LadderMode& md,
                              void* scratch, size_t bytes);
 
+// Generic contraction on the same kernel: C[M][N] (FP64 row-major, overwritten)
+// = sum_k A[m][k] B[n][k] for two-plane split-BF16 K-major operands A[p]
+// [M][Kp], B[p] [N][Kp] (Kp a multiple of 8, zeros beyond K), FP32 partial
+// sums promoted every 16 K blocks (64 deep).  A bounded device wait that gives
+// up raises c.d_err.
+bool tc_gemm_worthwhile(long long M, long long N, long long K);
+void tc_gemm(Ctx& c, const void* const* A, const void* const* B, long long M, long long N, long long Kp, double algo_flops,
+             double* C);
+
 }  // namespace adc

@@ -81,8 +81,9 @@ def test_roots_mixed_vs_fp64(kind, prec):
 
 
 def test_refinement_moves_roots_toward_fp64():
-    """The final refinement (accurate ladder + FP64 contractions on the
-    converged roots) changes the energies and lands within TOL_E of FP64."""
+    """The final refinement (accurate ladder on the converged roots, other
+    contractions FP32-accurate or FP64) changes the energies and lands within
+    TOL_E of FP64."""
     from paper_2012_06714_gb300 import ADC
 
     o, v, naux, seed = 8, 60, 160, 4
@@ -91,16 +92,40 @@ def test_refinement_moves_roots_toward_fp64():
     e64, p64, _, _ = g64.davidson(3, tol=1e-9)
     g64.close()
     res = {}
-    for rf in (0, 1):
+    for rf in (0, 1, 2):
         g = ADC(s.eps, s.B, o, order=3, kind="ea", precision="bf16x3", res_tol=1e-6, refine=rf)
         e, p, vec, st = g.davidson(3, tol=1e-9, want_vectors=True)
         assert st["status"] == 0
         res[rf] = (e, p, st)
         g.close()
     e0, _, st0 = res[0]
-    e1, p1, st1 = res[1]
     assert st0["refine_shift"] == 0.0 and st0["refine_seconds"] == 0.0
-    assert st1["refine_shift"] > 0.0
-    assert np.abs(e1 - e64).max() < TOL_E["bf16x3"]
     assert np.abs(e0 - e64).max() < 2e-6
-    assert np.abs(p1 - p64).max() < 1e-4
+    for rf in (1, 2):  # other contractions FP32-accurate (1) or FP64 (2)
+        e1, p1, st1 = res[rf]
+        assert st1["refine_shift"] > 0.0
+        assert np.abs(e1 - e64).max() < TOL_E["bf16x3"], (rf, np.abs(e1 - e64).max())
+        assert np.abs(p1 - p64).max() < 1e-4
+
+
+@pytest.mark.parametrize("kind", ["ea", "ip"])
+def test_tensor_core_contractions_vs_fp32(kind):
+    """sigma with the large non-ladder contractions on the tensor-core split-BF16
+    GEMM (contractions=2, the mixed default) against the same sigma with
+    FP32-accurate contractions (contractions=1, checked against the oracle
+    above); the system is large enough for those contractions to take the
+    tensor-core path.  Bound: the split-BF16 error (~1e-5 of each term's
+    magnitude), 3e-5 of max |sigma|."""
+    from paper_2012_06714_gb300 import ADC
+
+    o, v, naux = (24, 256, 300) if kind == "ea" else (48, 160, 300)
+    s = make_system(o, v, naux, seed=6)
+    g2 = ADC(s.eps, s.B, o, order=3, kind=kind, precision="bf16x3", contractions=2)
+    g1 = ADC(s.eps, s.B, o, order=3, kind=kind, precision="bf16x3", contractions=1)
+    X = np.random.default_rng(8).standard_normal((4, g2.dim))
+    S2 = g2.sigma(X)
+    S1 = g1.sigma(X)
+    err = np.abs(S2 - S1).max()
+    assert err <= 3e-5 * np.abs(S1).max(), (err, np.abs(S1).max())
+    g1.close()
+    g2.close()
