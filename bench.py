@@ -36,6 +36,24 @@ def ladder_flops(o, v, naux, nvec):
     return 4.0 * naux * o * v ** 3 * nvec
 
 
+def max_over_ranks(x, world, device=None):
+    """The maximum of a per-rank float over all ranks (replicas: the slowest rank
+    sets the step time); identity for one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_tflops(flops_per_rank, ms, world):
+    """Aggregate throughput of `world` replicas that each did flops_per_rank in ms."""
+    return world * flops_per_rank / (ms / 1e3) / 1e12
+
+
 def peaks():
     """(BF16 dense TF/s sustained, burst, HBM GB/s, source).  The ladder kernel is
     timed inside a seconds-long run of sigma steps (clocks settle under the power
@@ -299,12 +317,9 @@ def run_ours(args):
     barrier()
     ms = e0.elapsed_time(e1) / args.steps
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     flops = ladder_flops(o, v, naux, nvec)
-    value = world * flops / (ms / 1e3) / 1e12
+    value = whole_job_tflops(flops, ms, world)
 
     # roofline of the tensor-core ladder kernel, timed live with CUDA events
     gpu.kernel_timing(True)
@@ -343,7 +358,7 @@ def run_ours(args):
     for _ in range(ke):
         sig_host()
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / ke
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / ke, world, dev)
     e2e = {"value": world * flops / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": int(Xh.numel() * 8),
            "d2h_bytes_per_step": int(Sh.numel() * 8)}
 

@@ -108,6 +108,21 @@ int adc_default_options(adc_options* opt);
 int adc_setup(const double* eps, const double* Bq, int nocc, int nvir, int naux, int order, int kind,
               const adc_options* opt, int on_device, adc_handle** out);
 
+/*
+ * Set up nmol independent systems at once (the batched workload of many
+ * small molecules).  Arrays of length nmol: eps[i], Bq[i] (host, or device
+ * if on_device = 1), nocc[i], nvir[i], naux[i]; order, kind and opt are shared.
+ * Each handle gets its own CUDA stream (owned, destroyed with the handle) and
+ * the systems are set up concurrently on host threads, so that their small
+ * kernels overlap on the GPU; use adc_davidson_batch (or the single-system
+ * calls, which stay valid) on the result.  out receives nmol handles, each
+ * released with adc_destroy.  On failure no handle is returned and
+ * adc_last_error(NULL) names the failing system.
+ * Errors: as adc_setup.
+ */
+int adc_setup_batch(int nmol, const double* const* eps, const double* const* Bq, const int* nocc, const int* nvir,
+                    const int* naux, int order, int kind, const adc_options* opt, int on_device, adc_handle** out);
+
 /* Length of the spin-adapted vector (see layout above). */
 int adc_dim(const adc_handle* h, long long* dim);
 
@@ -141,11 +156,27 @@ int adc_davidson(adc_handle* h, int nroots, double tol, const double* guess, dou
                  double* vectors, double* stats);
 
 /*
- * Copy an intermediate to host memory (for verification).  name is one of
- * "M11" [n1][n1], "t2" [o][o][v][v] (first-order doubles), "t2_2" (second-
- * order doubles), "t1_2" [o][v], "diag" [dim].  n = number of doubles the
- * buffer holds.  Errors: ADC_ERR_ARG (unknown name, buffer too small, or the
- * intermediate does not exist at this order).
+ * adc_davidson for nmol handles concurrently (host threads, one handle each,
+ * work on each handle's stream), without guesses or vectors:
+ *   energies  host [nmol][nroots];  specfac host [nmol][nroots] or NULL
+ *   stats     host [nmol][8] or NULL;  status host [nmol] or NULL (each
+ *             system's adc_davidson return code)
+ * Returns ADC_OK if every system converged, else the first non-OK code other
+ * than ADC_ERR_NOT_CONVERGED if any (ADC_ERR_NOT_CONVERGED otherwise); the
+ * handles' adc_last_error hold the messages.
+ */
+int adc_davidson_batch(adc_handle* const* h, int nmol, int nroots, double tol, double* energies, double* specfac,
+                       double* stats, int* status);
+
+/*
+ * Copy an intermediate to host memory.  name is one of "M11" [n1][n1],
+ * "t2" [o][o][v][v] (first-order doubles), "t2_2" (second-order doubles),
+ * "t1_2" [o][v], "diag" [dim], or "X" [nroots][nmo]: the spectroscopic
+ * amplitudes X_{p,mu} = sum_nu T_{p,nu} (S Y~)_nu of the last adc_davidson
+ * that computed spectroscopic factors (Eq. spec_amp with the Appendix
+ * renormalisation, P_mu = 2 sum_p X_{p,mu}^2; occupied orbitals first).
+ * n = number of doubles the buffer holds.  Errors: ADC_ERR_ARG (unknown name,
+ * buffer too small, or the intermediate does not exist at this order / yet).
  */
 int adc_get_tensor(adc_handle* h, const char* name, double* out, long long n);
 
@@ -183,6 +214,19 @@ int adc_kernel_timing(adc_handle* h, int enable, double* out);
  * ADC_ERR_CUDA, ADC_ERR_TIMEOUT.
  */
 int adc_ladder_noalloc(adc_handle* h, const double* X, double* out, long long nmat);
+
+/*
+ * Spectral function (density of states) of computed roots on a frequency grid
+ * (Eqs. spec_function and PES): A(w) = -1/pi Im sum_mu P_mu / (w - w_mu + i eta)
+ * = 1/pi sum_mu P_mu eta / ((w - w_mu)^2 + eta^2), on the axis of the energies
+ * adc_davidson returns (EA: E_{N+1} - E_N; IP: ionisation energies).  With P
+ * from adc_davidson (Appendix normalisation) A integrates to sum_mu P_mu and
+ * counts both spin components.  Host arrays: energies, specfac [nroots];
+ * omega, A [nomega].  Host computation (O(nroots * nomega)); no handle needed.
+ * Errors: ADC_ERR_ARG (NULL arrays, negative counts, eta <= 0).
+ */
+int adc_spectrum(const double* energies, const double* specfac, int nroots, double eta, const double* omega, int nomega,
+                 double* A);
 
 /* Message of the last error on this handle (or of the last failed adc_setup
  * when h is NULL).  Never NULL. */

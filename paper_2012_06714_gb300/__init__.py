@@ -4,6 +4,6 @@ The compute path is the CUDA library ``_build/libadc.so`` (C ABI declared in
 ``include/adc.h``); this package only marshals arguments to it.  There is no
 CPU fallback: if the library is missing, importing the binding raises.
 """
-from ._lib import ADC, build_library, library_path, load_library  # noqa: F401
+from ._lib import ADC, ADCBatch, build_library, library_path, load_library, spectrum  # noqa: F401
 
-__all__ = ["ADC", "build_library", "library_path", "load_library"]
+__all__ = ["ADC", "ADCBatch", "build_library", "library_path", "load_library", "spectrum"]

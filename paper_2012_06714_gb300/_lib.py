@@ -15,6 +15,9 @@ ADC_EA, ADC_IP = 1, -1
 PRECISIONS = {"fp64": 0, "bf16x3": 1}
 
 EXPORTED = [
+    "adc_spectrum",
+    "adc_setup_batch",
+    "adc_davidson_batch",
     "adc_default_options",
     "adc_setup",
     "adc_dim",
@@ -77,6 +80,9 @@ def load_library():
     lib.adc_get_tensor.argtypes = [P, ctypes.c_char_p, P, LL]
     lib.adc_kernel_timing.argtypes = [P, I, P]
     lib.adc_ladder_noalloc.argtypes = [P, P, P, LL]
+    lib.adc_spectrum.argtypes = [P, P, I, D, P, I, P]
+    lib.adc_setup_batch.argtypes = [I, P, P, P, P, P, I, I, ctypes.POINTER(Options), I, P]
+    lib.adc_davidson_batch.argtypes = [P, I, I, D, P, P, P, P]
     lib.adc_last_error.argtypes = [P]
     lib.adc_last_error.restype = ctypes.c_char_p
     lib.adc_destroy.argtypes = [P]
@@ -86,6 +92,21 @@ def load_library():
             raise ImportError(f"libadc.so lacks {name}")
     _lib = lib
     return lib
+
+
+def spectrum(energies, specfac, omega, eta):
+    """A(omega) of computed roots (Eqs. spec_function, PES) through adc_spectrum."""
+    lib = load_library()
+    e = np.ascontiguousarray(energies, dtype=np.float64)
+    p = np.ascontiguousarray(specfac, dtype=np.float64)
+    w = np.ascontiguousarray(omega, dtype=np.float64)
+    if e.shape != p.shape:
+        raise ValueError("energies and specfac differ in length")
+    out = np.zeros(w.shape)
+    rc = lib.adc_spectrum(e.ctypes.data, p.ctypes.data, e.size, float(eta), w.ctypes.data, w.size, out.ctypes.data)
+    if rc != ADC_OK:
+        raise ADCError(rc, "adc_spectrum: invalid argument")
+    return out
 
 
 def _ptr(a):
@@ -193,6 +214,70 @@ class ADC:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.adc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ADCBatch:
+    """Many independent closed-shell systems, set up and solved concurrently
+    (adc_setup_batch / adc_davidson_batch): each system on its own CUDA stream
+    and host thread.  systems: list of (eps, B, nocc) float64 numpy arrays."""
+
+    def __init__(self, systems, order=3, kind="ip", precision="bf16x3", **opts):
+        lib = load_library()
+        self._lib = lib
+        opt = Options()
+        lib.adc_default_options(ctypes.byref(opt))
+        opt.precision = PRECISIONS[precision]
+        for k, val in opts.items():
+            if not hasattr(opt, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(opt, k, val)
+        self._keep = []
+        n = len(systems)
+        eps_p = (ctypes.c_void_p * n)()
+        b_p = (ctypes.c_void_p * n)()
+        no, nv, nq = (ctypes.c_int * n)(), (ctypes.c_int * n)(), (ctypes.c_int * n)()
+        for i, (eps, B, nocc) in enumerate(systems):
+            eps = np.ascontiguousarray(eps, dtype=np.float64)
+            B = np.ascontiguousarray(B, dtype=np.float64)
+            self._keep += [eps, B]
+            eps_p[i], b_p[i] = eps.ctypes.data, B.ctypes.data
+            no[i], nv[i], nq[i] = nocc, B.shape[1] - nocc, B.shape[0]
+        handles = (ctypes.c_void_p * n)()
+        rc = lib.adc_setup_batch(n, ctypes.cast(eps_p, ctypes.c_void_p), ctypes.cast(b_p, ctypes.c_void_p),
+                                 ctypes.cast(no, ctypes.c_void_p), ctypes.cast(nv, ctypes.c_void_p),
+                                 ctypes.cast(nq, ctypes.c_void_p), order, ADC_EA if kind == "ea" else ADC_IP,
+                                 ctypes.byref(opt), 0, ctypes.cast(handles, ctypes.c_void_p))
+        self._keep = []
+        if rc != ADC_OK:
+            raise ADCError(rc, lib.adc_last_error(None).decode())
+        self._h = handles
+        self.n = n
+
+    def davidson(self, nroots, tol=1e-6):
+        """(energies [n, nroots], spectroscopic factors [n, nroots], stats [n, 8], status [n])."""
+        e = np.zeros((self.n, nroots))
+        p = np.zeros((self.n, nroots))
+        st = np.zeros((self.n, 8))
+        status = (ctypes.c_int * self.n)()
+        rc = self._lib.adc_davidson_batch(ctypes.cast(self._h, ctypes.c_void_p), self.n, nroots, tol, e.ctypes.data,
+                                          p.ctypes.data, st.ctypes.data, ctypes.cast(status, ctypes.c_void_p))
+        status = np.array(list(status))
+        if rc not in (ADC_OK, ADC_ERR_NOT_CONVERGED):
+            bad = int(np.nonzero(status != ADC_OK)[0][0])
+            raise ADCError(rc, self._lib.adc_last_error(self._h[bad]).decode())
+        return e, p, st, status
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            for i in range(self.n):
+                self._lib.adc_destroy(self._h[i])
             self._h = None
 
     def __del__(self):

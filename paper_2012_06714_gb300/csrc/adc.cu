@@ -19,6 +19,8 @@
 #include <numeric>
 #include <string>
 #include <vector>
+#include <atomic>
+#include <thread>
 
 #include "../../include/adc.h"
 #include "common.cuh"
@@ -42,8 +44,10 @@ struct adc_handle {
     LadderMode lm_sigma{2, 0, 16}, lm_setup{2, 1, 1}, lm_refine{2, 1, 1};
     bool refining = false;  // sigma evaluates with lm_refine
     int cmode_setup = 0, cmode_sigma = 0;  // Ctx::gemm_mode in setup / in sigma
+    std::vector<double> X_last;             // spectroscopic amplitudes [nroots][nmo] of the last adc_davidson
     double* Lt = nullptr;    // setup only: sum_cd (ac|bd) t_kl^cd, shared by t2(2) and the EA 1p-1p block
     std::vector<void*> owned;
+    cudaStream_t own_stream = nullptr;  // created by adc_setup_batch, destroyed with the handle
     std::string err;
     long long dim() const {
         return kind == ADC_EA ? (long long)v + (long long)o * v * v : (long long)o + (long long)o * o * v;
@@ -56,13 +60,15 @@ struct adc_handle {
         return (double*)p;
     }
     ~adc_handle() {
+        if (ctx.stream) cudaStreamSynchronize(ctx.stream);
         ladder_tc_destroy(tc);
         for (void* p : owned) cudaFree(p);
         if (ctx.blas) cublasDestroy(ctx.blas);
+        if (own_stream) cudaStreamDestroy(own_stream);
     }
 };
 
-static std::string g_setup_error = "no error";
+static thread_local std::string g_setup_error = "no error";  // last adc_setup failure of this host thread
 
 // --------------------------------------------------------------------------
 // ADC-specific elementwise kernels
@@ -1041,6 +1047,7 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
         std::vector<double> xh((size_t)nroots * nmo);
         ADC_CUDA(cudaMemcpyAsync(xh.data(), Xp, xh.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
         ADC_CUDA(cudaStreamSynchronize(c.stream));
+        h->X_last = xh;
         for (int r = 0; r < nroots; ++r) {
             double s = 0.0;
             for (long long p = 0; p < nmo; ++p) s += xh[(size_t)r * nmo + p] * xh[(size_t)r * nmo + p];
@@ -1092,6 +1099,22 @@ bool handle_ladder_view(adc_handle* h, LadderTC** tc, Ctx** c, int* nvir, std::s
 
 extern "C" {
 
+int adc_spectrum(const double* energies, const double* specfac, int nroots, double eta, const double* omega, int nomega,
+                 double* A) {
+    if (nroots < 0 || nomega < 0 || !(eta > 0.0) || (nroots > 0 && (!energies || !specfac)) || (nomega > 0 && (!omega || !A)))
+        return ADC_ERR_ARG;
+    // A(w) = -1/pi Im sum_mu P_mu / (w - w_mu + i eta) = 1/pi sum_mu P_mu eta / ((w - w_mu)^2 + eta^2)
+    for (int k = 0; k < nomega; ++k) {
+        double a = 0.0;
+        for (int r = 0; r < nroots; ++r) {
+            const double d = omega[k] - energies[r];
+            a += specfac[r] * eta / (d * d + eta * eta);
+        }
+        A[k] = a / M_PI;
+    }
+    return ADC_OK;
+}
+
 int adc_default_options(adc_options* opt) {
     if (!opt) return ADC_ERR_ARG;
     opt->precision = ADC_PREC_FP64;
@@ -1106,20 +1129,24 @@ int adc_default_options(adc_options* opt) {
     return ADC_OK;
 }
 
-int adc_setup(const double* eps, const double* Bq, int nocc, int nvir, int naux, int order, int kind,
-              const adc_options* opt, int on_device, adc_handle** out) {
+}  // extern "C"
+
+// One system on `stream` (owned by the handle if own_stream); returns ADC_OK or
+// a negative code with the message in `msg`.
+static int setup_one(const double* eps, const double* Bq, int nocc, int nvir, int naux, int order, int kind,
+                     const adc_options* opt, int on_device, bool own_stream, adc_handle** out, std::string& msg) {
     if (!out) return ADC_ERR_ARG;
     *out = nullptr;
     if (!eps || !Bq || nocc < 1 || nvir < 1 || naux < 1 || (order != 2 && order != 3) || (kind != ADC_EA && kind != ADC_IP)) {
-        g_setup_error = "adc_setup: invalid argument";
+        msg = "adc_setup: invalid argument";
         return ADC_ERR_ARG;
     }
     if (opt && (opt->precision != ADC_PREC_FP64 && opt->precision != ADC_PREC_BF16X3)) {
-        g_setup_error = "adc_setup: unknown precision";
+        msg = "adc_setup: unknown precision";
         return ADC_ERR_ARG;
     }
     if (opt && (opt->contractions < -1 || opt->contractions > 2 || opt->refine < 0 || opt->refine > 2)) {
-        g_setup_error = "adc_setup: contractions must be -1..2 and refine 0..2";
+        msg = "adc_setup: contractions must be -1..2 and refine 0..2";
         return ADC_ERR_ARG;
     }
     adc_handle* h = new adc_handle();
@@ -1131,18 +1158,78 @@ int adc_setup(const double* eps, const double* Bq, int nocc, int nvir, int naux,
     adc_default_options(&h->opt);
     if (opt) h->opt = *opt;
     try {
+        if (own_stream) {
+            ADC_CUDA(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+            h->ctx.stream = h->own_stream;
+        }
         setup(h, eps, Bq, on_device);
+        ADC_CUDA(cudaStreamSynchronize(h->ctx.stream));
     } catch (const adc::Error& e) {
-        g_setup_error = e.what();
+        msg = e.what();
         int code = e.code;
         delete h;
         return code;
     } catch (const std::exception& e) {
-        g_setup_error = e.what();
+        msg = e.what();
         delete h;
         return ADC_ERR_CUDA;
     }
     *out = h;
+    return ADC_OK;
+}
+
+// Run f(i) for i in [0, n) on up to `threads` host threads, each with the
+// caller's current CUDA device.
+template <class F>
+static void parallel_for(int n, int threads, F f) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::atomic<int> next{0};
+    auto worker = [&] {
+        cudaSetDevice(dev);
+        for (int i = next++; i < n; i = next++) f(i);
+    };
+    std::vector<std::thread> pool;
+    const int nt = std::max(1, std::min(n, threads));
+    for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+    worker();
+    for (auto& t : pool) t.join();
+}
+
+static int batch_threads(int n) {
+    const unsigned hc = std::thread::hardware_concurrency();
+    return std::max(1, std::min(n, std::min(16, hc ? (int)hc : 4)));
+}
+
+extern "C" {
+
+int adc_setup(const double* eps, const double* Bq, int nocc, int nvir, int naux, int order, int kind,
+              const adc_options* opt, int on_device, adc_handle** out) {
+    return setup_one(eps, Bq, nocc, nvir, naux, order, kind, opt, on_device, false, out, g_setup_error);
+}
+
+int adc_setup_batch(int nmol, const double* const* eps, const double* const* Bq, const int* nocc, const int* nvir,
+                    const int* naux, int order, int kind, const adc_options* opt, int on_device, adc_handle** out) {
+    if (nmol < 1 || !eps || !Bq || !nocc || !nvir || !naux || !out) {
+        g_setup_error = "adc_setup_batch: invalid argument";
+        return ADC_ERR_ARG;
+    }
+    for (int i = 0; i < nmol; ++i) out[i] = nullptr;
+    std::vector<int> rc(nmol, ADC_OK);
+    std::vector<std::string> msg(nmol);
+    parallel_for(nmol, batch_threads(nmol), [&](int i) {
+        rc[i] = setup_one(eps[i], Bq[i], nocc[i], nvir[i], naux[i], order, kind, opt, on_device, true, &out[i], msg[i]);
+    });
+    for (int i = 0; i < nmol; ++i) {
+        if (rc[i] != ADC_OK) {
+            g_setup_error = "adc_setup_batch: system " + std::to_string(i) + ": " + msg[i];
+            for (int j = 0; j < nmol; ++j) {
+                delete out[j];
+                out[j] = nullptr;
+            }
+            return rc[i];
+        }
+    }
     return ADC_OK;
 }
 
@@ -1199,6 +1286,22 @@ int adc_davidson(adc_handle* h, int nroots, double tol, const double* guess, dou
     })
 }
 
+int adc_davidson_batch(adc_handle* const* h, int nmol, int nroots, double tol, double* energies, double* specfac,
+                       double* stats, int* status) {
+    if (!h || nmol < 1 || !energies) return ADC_ERR_ARG;
+    std::vector<int> rc(nmol, ADC_OK);
+    parallel_for(nmol, batch_threads(nmol), [&](int i) {
+        rc[i] = adc_davidson(h[i], nroots, tol, nullptr, energies + (size_t)i * nroots,
+                             specfac ? specfac + (size_t)i * nroots : nullptr, nullptr, stats ? stats + 8 * (size_t)i : nullptr);
+    });
+    int worst = ADC_OK;
+    for (int i = 0; i < nmol; ++i) {
+        if (status) status[i] = rc[i];
+        if (rc[i] != ADC_OK && (worst == ADC_OK || worst == ADC_ERR_NOT_CONVERGED)) worst = rc[i];
+    }
+    return worst;
+}
+
 int adc_get_tensor(adc_handle* h, const char* name, double* out, long long n) {
     if (!h || !name || !out) return ADC_ERR_ARG;
     GUARD(h, {
@@ -1221,6 +1324,19 @@ int adc_get_tensor(adc_handle* h, const char* name, double* out, long long n) {
         } else if (s == "diag") {
             src = h->diag;
             cnt = h->dim();
+        } else if (s == "X") {
+            // host copy kept by the last adc_davidson that computed spectroscopic factors
+            cnt = (long long)h->X_last.size();
+            if (cnt == 0) {
+                h->err = "adc_get_tensor: no spectroscopic amplitudes yet (run adc_davidson with specfac)";
+                return ADC_ERR_ARG;
+            }
+            if (n < cnt) {
+                h->err = "adc_get_tensor: buffer too small";
+                return ADC_ERR_ARG;
+            }
+            std::memcpy(out, h->X_last.data(), cnt * sizeof(double));
+            return ADC_OK;
         }
         if (!src) {
             h->err = "adc_get_tensor: unknown or unavailable tensor " + s;

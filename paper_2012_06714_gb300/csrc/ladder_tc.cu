@@ -975,23 +975,53 @@ int pick_bn(int n, int maxbn) {
     return best;
 }
 
+// Per-device launch facts, set up once per device (thread-safe): kernel
+// attributes, SM count, and how many CTA pairs of k_gemm_pair fit at once.
+struct DevInfo {
+    std::once_flag once;
+    cudaError_t st = cudaSuccess;
+    int num_sms = 0, max_pairs = 0;
+};
+const DevInfo& dev_info() {
+    static DevInfo info[64];
+    int dev = 0;
+    ADC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) throw Error(-3, "ladder: device index out of range");
+    DevInfo& d = info[dev];
+    std::call_once(d.once, [&d, dev] {
+        auto chk = [&d](cudaError_t e) {
+            if (e != cudaSuccess && d.st == cudaSuccess) d.st = e;
+        };
+        chk(cudaFuncSetAttribute(k_gemm_bf16x3<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+        chk(cudaFuncSetAttribute(k_gemm_bf16x3<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+        chk(cudaFuncSetAttribute(k_gemm_pair<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+        chk(cudaFuncSetAttribute(k_gemm_pair<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+        chk(cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev));
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute cl[1];
+        cl[0].id = cudaLaunchAttributeClusterDimension;
+        cl[0].val.clusterDim.x = 2;
+        cl[0].val.clusterDim.y = 1;
+        cl[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)(d.num_sms / 2 * 2));
+        cfg.blockDim = dim3(THREADS);
+        cfg.dynamicSmemBytes = SMEM_BYTES;
+        cfg.attrs = cl;
+        cfg.numAttrs = 1;
+        chk(cudaOccupancyMaxActiveClusters(&d.max_pairs, (void*)k_gemm_pair<true>, &cfg));
+    });
+    ADC_CUDA(d.st);
+    if (d.max_pairs < 1) throw Error(-3, "ladder: no CTA pair fits on the device");
+    return d;
+}
+
 // ekb: accumulation epoch in 64-deep K blocks (0 = one epoch per tile);
 // pair: 256-row tiles on CTA pairs (k_gemm_pair), else 128-row tiles per CTA
 void launch_gemm(Ctx& c, const Maps& maps, int planes, int a_row0, int b_x0, int M, int N, int K, int BN, int m_fastest,
                  int ekb, bool pair, const Epi& ep, double algo_flops) {
-    static bool attr = false;
-    static int num_sms = 0, max_pairs = 0;
     if (BN % 16 || BN < 16 || BN > 256) throw Error(-1, "ladder: tile width must be a multiple of 16 in [16, 256]");
-    if (!attr) {
-        ADC_CUDA(cudaFuncSetAttribute(k_gemm_bf16x3<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
-        ADC_CUDA(cudaFuncSetAttribute(k_gemm_bf16x3<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
-        ADC_CUDA(cudaFuncSetAttribute(k_gemm_pair<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
-        ADC_CUDA(cudaFuncSetAttribute(k_gemm_pair<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
-        int dev = 0;
-        ADC_CUDA(cudaGetDevice(&dev));
-        ADC_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
-        attr = true;
-    }
+    const DevInfo& di = dev_info();
+    const int num_sms = di.num_sms, max_pairs = di.max_pairs;
     const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
     const long long ntiles = (long long)mt * nt;
     if (ntiles <= 0) return;
@@ -1021,11 +1051,6 @@ void launch_gemm(Ctx& c, const Maps& maps, int planes, int a_row0, int b_x0, int
     if (!pair) {
         grid = (int)std::min<long long>(ntiles, num_sms);
     } else {
-        if (!max_pairs) {
-            cfg.gridDim = dim3((unsigned)(num_sms / 2 * 2));
-            ADC_CUDA(cudaOccupancyMaxActiveClusters(&max_pairs, (void*)k_gemm_pair<true>, &cfg));
-            if (max_pairs < 1) throw Error(-3, "ladder: no CTA pair fits on the device");
-        }
         const long long units = (long long)((mt + 1) / 2) * nt;  // 256-row tiles
         grid = (int)std::min<long long>(units, max_pairs) * 2;
     }
@@ -1065,7 +1090,9 @@ struct LadderTC {
     int naux = 0, v = 0, vp = 0, chunk = 0;
     bool pair1 = true, pair2 = true;    // 2-SM tiles (cta_group::2 on CTA pairs) for GEMM1 / GEMM2
     int bn2[4] = {256, 256, 256, 256};  // GEMM2 tile width by plane count (2 or 3)
-    __nv_bfloat16 *Bs[3] = {}, *Bp[3] = {};  // three BF16 planes of B^Q in the GEMM1-A and GEMM2-B layouts
+    const double* Bvv = nullptr;        // FP64 source (owned by the caller, outlives this object)
+    int nplanes = 0;                    // BF16 planes held (2; 3 once a three-plane ladder was asked for)
+    __nv_bfloat16 *Bs[3] = {}, *Bp[3] = {};  // BF16 planes of B^Q in the GEMM1-A and GEMM2-B layouts
     CUtensorMap mBs[3], mBp2[3], mBp3[3];     // GEMM2-B maps exist for both tile widths
     int* d_err = nullptr;
     ~LadderTC() {
@@ -1079,7 +1106,32 @@ struct LadderTC {
 
 namespace {
 constexpr int BN1[4] = {0, 0, 256, 128};  // GEMM1 tile width by plane count (two stages must fit)
+
+// (Re)split B^Q_vv into `planes` BF16 planes of both layouts and make their tensor maps.
+void split_B(LadderTC& L, Ctx& c, int planes) {
+    const long long nB = (long long)L.naux * L.v * L.vp;      // Bp planes
+    const long long nBs = (long long)L.naux * L.vp * L.vp;    // Bs planes (rows padded)
+    Planes ps{}, pp{};
+    for (int p = 0; p < planes; ++p) {
+        if (!L.Bs[p]) ADC_CUDA(cudaMalloc(&L.Bs[p], nBs * 2));
+        if (!L.Bp[p]) ADC_CUDA(cudaMalloc(&L.Bp[p], nB * 2));
+        ps.p[p] = L.Bs[p];
+        pp.p[p] = L.Bp[p];
+    }
+    k_split_Bs<<<grid_for(nBs), 256, 0, c.stream>>>(L.Bvv, L.naux, L.v, L.vp, planes, ps);
+    ++c.kernels;
+    k_split_Bp<<<grid_for(nB), 256, 0, c.stream>>>(L.Bvv, L.naux, L.v, L.vp, planes, pp);
+    ++c.kernels;
+    ADC_CUDA(cudaGetLastError());
+    for (int p = 0; p < planes; ++p) {
+        L.mBs[p] = make_map(L.Bs[p], (long long)L.naux * L.vp, L.vp, BM);
+        // GEMM2-B boxes: one CTA's half of the tile in pair mode
+        L.mBp2[p] = make_map(L.Bp[p], L.v, (long long)L.naux * L.vp, L.pair2 ? L.bn2[2] / 2 : L.bn2[2]);
+        L.mBp3[p] = make_map(L.Bp[p], L.v, (long long)L.naux * L.vp, L.pair2 ? L.bn2[3] / 2 : L.bn2[3]);
+    }
+    L.nplanes = planes;
 }
+}  // namespace
 
 LadderTC* ladder_tc_create(Ctx& c, const double* Bvv, int naux, int v, int aux_chunk) {
     auto* L = new LadderTC();
@@ -1088,30 +1140,12 @@ LadderTC* ladder_tc_create(Ctx& c, const double* Bvv, int naux, int v, int aux_c
         L->v = v;
         L->vp = (v + 31) / 32 * 32;
         L->chunk = aux_chunk;
+        L->Bvv = Bvv;
         L->bn2[2] = pick_bn(v, 256);
         L->bn2[3] = pick_bn(v, 128);
-        const long long nB = (long long)naux * v * L->vp;    // Bp planes
-        const long long nBs = (long long)naux * L->vp * L->vp;  // Bs planes (rows padded)
-        Planes ps{}, pp{};
-        for (int p = 0; p < 3; ++p) {
-            ADC_CUDA(cudaMalloc(&L->Bs[p], nBs * 2));
-            ADC_CUDA(cudaMalloc(&L->Bp[p], nB * 2));
-            ps.p[p] = L->Bs[p];
-            pp.p[p] = L->Bp[p];
-        }
         ADC_CUDA(cudaMalloc(&L->d_err, sizeof(int)));
         ADC_CUDA(cudaMemsetAsync(L->d_err, 0, sizeof(int), c.stream));
-        k_split_Bs<<<grid_for(nBs), 256, 0, c.stream>>>(Bvv, naux, v, L->vp, 3, ps);
-        ++c.kernels;
-        k_split_Bp<<<grid_for(nB), 256, 0, c.stream>>>(Bvv, naux, v, L->vp, 3, pp);
-        ++c.kernels;
-        ADC_CUDA(cudaGetLastError());
-        for (int p = 0; p < 3; ++p) {
-            L->mBs[p] = make_map(L->Bs[p], (long long)naux * L->vp, L->vp, BM);
-            // GEMM2-B boxes: one CTA's half of the tile in pair mode
-            L->mBp2[p] = make_map(L->Bp[p], v, (long long)naux * L->vp, L->pair2 ? L->bn2[2] / 2 : L->bn2[2]);
-            L->mBp3[p] = make_map(L->Bp[p], v, (long long)naux * L->vp, L->pair2 ? L->bn2[3] / 2 : L->bn2[3]);
-        }
+        split_B(*L, c, 2);
     } catch (...) {
         delete L;
         throw;
@@ -1185,6 +1219,7 @@ void ladder_tc_apply(LadderTC& L, Ctx& c, const double* X, long long nmat, doubl
     if (nmat <= 0) return;
     if (planes != 2 && planes != 3) throw Error(-1, "ladder: planes must be 2 or 3");
     if (md.epoch1 < 0 || md.epoch2 < 0) throw Error(-1, "ladder: negative epoch length");
+    if (planes > L.nplanes) split_B(L, c, planes);  // the third plane only when first asked for
     // Scratch budget for Z (all planes): ~1 GiB.  Matrices are processed in
     // groups small enough that a chunk holds >= 8 auxiliary functions (long K
     // in GEMM2, fewer FP64 read-modify-write passes over the output); K2 <= 8192.

@@ -96,3 +96,22 @@ def test_invalid_arguments(lib):
     with pytest.raises(ADCError):
         gpu.davidson(gpu.dim + 1)
     gpu.close()
+
+
+@pytest.mark.parametrize("kind", ["ea", "ip"])
+def test_spectroscopic_amplitudes_and_spectrum(kind):
+    """X from adc_get_tensor("X") reproduces the returned factors (P = 2 sum_p X^2,
+    Appendix) and the propagator route of the spectral function (Eqs. g_adc,
+    spec_function) equals adc_spectrum's P route."""
+    from oracle.spectrum import spectral_function
+    from paper_2012_06714_gb300 import ADC, spectrum
+
+    o, v, naux = 4, 14, 40
+    s = make_system(o, v, naux, seed=3)
+    g = ADC(s.eps, s.B, o, order=3, kind=kind, precision="fp64")
+    e, p, _, st = g.davidson(3, tol=1e-10)
+    X = g.get("X", (3, o + v))
+    g.close()
+    assert np.abs(2.0 * (X * X).sum(axis=1) - p).max() < 1e-12
+    w = np.linspace(e.min() - 0.2, e.max() + 0.2, 101)
+    assert np.abs(spectrum(e, p, w, 0.01) - 2.0 * spectral_function(X.T, e, w, 0.01)).max() < 1e-10
