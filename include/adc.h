@@ -112,10 +112,10 @@ int adc_setup(const double* eps, const double* Bq, int nocc, int nvir, int naux,
  * Set up nmol independent systems at once (the batched workload of many
  * small molecules).  Arrays of length nmol: eps[i], Bq[i] (host, or device
  * if on_device = 1), nocc[i], nvir[i], naux[i]; order, kind and opt are shared.
- * Each handle gets its own CUDA stream (owned, destroyed with the handle) and
- * the systems are set up concurrently on host threads, so that their small
- * kernels overlap on the GPU; use adc_davidson_batch (or the single-system
- * calls, which stay valid) on the result.  out receives nmol handles, each
+ * Each handle gets its own CUDA stream (owned, destroyed with the handle).
+ * The systems are set up one after another (setup fills the GPU); solve
+ * them with adc_davidson_batch, which overlaps their small kernels on the
+ * GPU (or with the single-system calls, which stay valid).  out receives nmol handles, each
  * released with adc_destroy.  On failure no handle is returned and
  * adc_last_error(NULL) names the failing system.
  * Errors: as adc_setup.

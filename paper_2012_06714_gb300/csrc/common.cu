@@ -260,9 +260,7 @@ static void einsum_fp32(Ctx& c, const std::string& la, const std::string& lb, co
         if (constant) {
             auto it = c.f32cache.find({src, key});
             if (it != c.f32cache.end()) return (const float*)it->second;
-            void* p = nullptr;
-            ADC_CUDA(cudaMalloc(&p, n * sizeof(float)));
-            dst = (float*)p;
+            dst = (float*)dev_alloc(n * sizeof(float), c.stream);
             c.f32cache[{src, key}] = dst;
         } else {
             dst = (float*)c.arena.alloc(n * sizeof(float));
@@ -333,7 +331,7 @@ static void einsum_tc(Ctx& c, const std::string& la, const std::string& lb, cons
         if (constant) {
             auto it = c.bf16cache.find({src, key});
             if (it != c.bf16cache.end()) return it->second;
-            ADC_CUDA(cudaMalloc(&base, 2 * rows * Kp * 2));
+            base = dev_alloc(2 * rows * Kp * 2, c.stream);
             c.bf16cache[{src, key}] = base;
         } else {
             base = c.arena.alloc(2 * rows * Kp * 2);
@@ -345,7 +343,7 @@ static void einsum_tc(Ctx& c, const std::string& la, const std::string& lb, cons
     void* pa = planes_of(Ap, la, fa + con, M, constA);
     void* pb = planes_of(Bp, lb, fb + con, N, constB);
     if (!c.d_err) {
-        ADC_CUDA(cudaMalloc(&c.d_err, sizeof(int)));
+        c.d_err = (int*)dev_alloc(sizeof(int), c.stream);
         ADC_CUDA(cudaMemsetAsync(c.d_err, 0, sizeof(int), c.stream));
     }
     double* T = c.arena.dalloc((size_t)(M * N));

@@ -36,9 +36,12 @@ struct Error : std::runtime_error {
     } while (0)
 
 // Device scratch: blocks are allocated on demand and kept; mark()/release()
-// give stack semantics so that repeated calls reuse the same memory.
+// give stack semantics so that repeated calls reuse the same memory.  Blocks
+// come from the stream-ordered allocator on `stream` (no device-wide
+// synchronisation, so handles on other streams keep running).
 class Arena {
    public:
+    cudaStream_t stream = nullptr;
     ~Arena() { free_all(); }
     struct Mark {
         size_t block, top;
@@ -66,7 +69,7 @@ class Arena {
         }
         size_t cap = bytes > (size_t(256) << 20) ? bytes : (size_t(256) << 20);
         void* p = nullptr;
-        ADC_CUDA(cudaMalloc(&p, cap));
+        ADC_CUDA(cudaMallocAsync(&p, cap, stream));
         blocks_.push_back(p);
         caps_.push_back(cap);
         tops_.push_back(bytes);
@@ -93,8 +96,19 @@ class Arena {
     size_t cur_ = 0;
 };
 
+// Stream-ordered device allocation (memory from it is freed with cudaFree).
+inline void* dev_alloc(size_t bytes, cudaStream_t s) {
+    void* p = nullptr;
+    ADC_CUDA(cudaMallocAsync(&p, bytes ? bytes : 1, s));
+    return p;
+}
+
 struct Ctx {
-    cudaStream_t stream = 0;
+    cudaStream_t stream = 0;  // set with set_stream (the arena allocates on it)
+    void set_stream(cudaStream_t s) {
+        stream = s;
+        arena.stream = s;
+    }
     cublasHandle_t blas = nullptr;
     Arena arena;
     long long kernels = 0;  // own kernel launches issued (for reporting)

@@ -1113,8 +1113,8 @@ void split_B(LadderTC& L, Ctx& c, int planes) {
     const long long nBs = (long long)L.naux * L.vp * L.vp;    // Bs planes (rows padded)
     Planes ps{}, pp{};
     for (int p = 0; p < planes; ++p) {
-        if (!L.Bs[p]) ADC_CUDA(cudaMalloc(&L.Bs[p], nBs * 2));
-        if (!L.Bp[p]) ADC_CUDA(cudaMalloc(&L.Bp[p], nB * 2));
+        if (!L.Bs[p]) L.Bs[p] = (__nv_bfloat16*)dev_alloc(nBs * 2, c.stream);
+        if (!L.Bp[p]) L.Bp[p] = (__nv_bfloat16*)dev_alloc(nB * 2, c.stream);
         ps.p[p] = L.Bs[p];
         pp.p[p] = L.Bp[p];
     }
@@ -1143,7 +1143,7 @@ LadderTC* ladder_tc_create(Ctx& c, const double* Bvv, int naux, int v, int aux_c
         L->Bvv = Bvv;
         L->bn2[2] = pick_bn(v, 256);
         L->bn2[3] = pick_bn(v, 128);
-        ADC_CUDA(cudaMalloc(&L->d_err, sizeof(int)));
+        L->d_err = (int*)dev_alloc(sizeof(int), c.stream);
         ADC_CUDA(cudaMemsetAsync(L->d_err, 0, sizeof(int), c.stream));
         split_B(*L, c, 2);
     } catch (...) {
