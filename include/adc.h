@@ -123,6 +123,11 @@ int adc_setup(const double* eps, const double* Bq, int nocc, int nvir, int naux,
 int adc_setup_batch(int nmol, const double* const* eps, const double* const* Bq, const int* nocc, const int* nvir,
                     const int* naux, int order, int kind, const adc_options* opt, int on_device, adc_handle** out);
 
+/* Replace the solver options of a handle (max_space_per_root, max_iter,
+ * nguess_extra, res_tol, keep_per_root, refine); precision, contractions and
+ * aux_chunk stay as set up.  Errors: ADC_ERR_ARG. */
+int adc_set_options(adc_handle* h, const adc_options* opt);
+
 /* Length of the spin-adapted vector (see layout above). */
 int adc_dim(const adc_handle* h, long long* dim);
 
@@ -148,7 +153,8 @@ int adc_sigma(adc_handle* h, const double* X, double* S, int nvec, int on_device
  *   vectors   host [nroots][dim] (S-normalised eigenvectors) or NULL
  *   stats     host double[8] or NULL: {iterations, sigma vectors, seconds,
  *             max S-norm residual, sigma seconds, max |energy change| of the
- *             final refinement, refinement seconds, 0}; with refinement the
+ *             final refinement, refinement seconds, roots that fell back from
+ *             the learned to the diagonal preconditioner}; with refinement the
  *             residual is that of the refined pairs under the accurate sigma
  * Errors: ADC_ERR_ARG, ADC_ERR_OOM, ADC_ERR_CUDA, ADC_ERR_NOT_CONVERGED.
  */
@@ -227,6 +233,33 @@ int adc_ladder_noalloc(adc_handle* h, const double* X, double* out, long long nm
  */
 int adc_spectrum(const double* energies, const double* specfac, int nroots, double eta, const double* omega, int nomega,
                  double* A);
+
+/*
+ * Learned Davidson preconditioner.  The paper uses the diagonal correction
+ * t = r / (w - D) (Sec. III A, Davidson); this adds to its multiplier a small
+ * network m(f) (3 -> 64 -> 64 -> 1, tanh, FP32) of per-element features
+ * f = (d, sign(d)/max(|d|, 0.01), [element in the 1p/1h block]), d = D - w:
+ *   t_x = r_x (1 / (w - D_x) + m(f_x)),
+ * weights laid out W1[64][3], b1[64], W2[64][64], b2[64], W3[64], b3
+ * (adc_mlp_nweights() floats; all zero = the diagonal preconditioner).
+ * Training samples (host arrays of n): d = D_x - w, blk (1: 1p/1h block),
+ * r = residual element, t = exact correction element (y_exact / <y, y_exact>_S
+ * - y of a Davidson iterate y); loss = sum (r (p + m) - t)^2 / sum t^2.
+ *   adc_mlp_loss_grad: loss and gradient (host grad [nweights]) at `weights`
+ *   adc_mlp_train:     `steps` full-batch Adam steps of rate lr on the GPU;
+ *                      weights host in/out; loss_hist host [steps] or NULL
+ *   adc_set_mlp:       use these weights (host) in adc_davidson of this handle,
+ *                      NULL for the diagonal preconditioner (default).  A root
+ *                      whose residual does not fall below 0.9 x its best for 4
+ *                      iterations falls back to the diagonal preconditioner.
+ * Errors: ADC_ERR_ARG, ADC_ERR_CUDA (adc_last_error(NULL) for the first two).
+ */
+int adc_mlp_nweights(void);
+int adc_mlp_loss_grad(const float* weights, const double* d, const unsigned char* blk, const double* r, const double* t,
+                      long long n, float* grad, double* loss);
+int adc_mlp_train(float* weights, const double* d, const unsigned char* blk, const double* r, const double* t, long long n,
+                  int steps, float lr, double* loss_hist);
+int adc_set_mlp(adc_handle* h, const float* weights);
 
 /* Message of the last error on this handle (or of the last failed adc_setup
  * when h is NULL).  Never NULL. */

@@ -15,6 +15,11 @@ ADC_EA, ADC_IP = 1, -1
 PRECISIONS = {"fp64": 0, "bf16x3": 1}
 
 EXPORTED = [
+    "adc_set_options",
+    "adc_mlp_nweights",
+    "adc_mlp_loss_grad",
+    "adc_mlp_train",
+    "adc_set_mlp",
     "adc_spectrum",
     "adc_setup_batch",
     "adc_davidson_batch",
@@ -81,6 +86,11 @@ def load_library():
     lib.adc_kernel_timing.argtypes = [P, I, P]
     lib.adc_ladder_noalloc.argtypes = [P, P, P, LL]
     lib.adc_spectrum.argtypes = [P, P, I, D, P, I, P]
+    lib.adc_mlp_nweights.argtypes = []
+    lib.adc_mlp_loss_grad.argtypes = [P, P, P, P, P, LL, P, P]
+    lib.adc_mlp_train.argtypes = [P, P, P, P, P, LL, I, ctypes.c_float, P]
+    lib.adc_set_mlp.argtypes = [P, P]
+    lib.adc_set_options.argtypes = [P, ctypes.POINTER(Options)]
     lib.adc_setup_batch.argtypes = [I, P, P, P, P, P, I, I, ctypes.POINTER(Options), I, P]
     lib.adc_davidson_batch.argtypes = [P, I, I, D, P, P, P, P]
     lib.adc_last_error.argtypes = [P]
@@ -138,6 +148,8 @@ class ADC:
         opt.keep_per_root = keep_per_root
         opt.contractions = contractions
         opt.refine = refine
+        self._solver = dict(max_space_per_root=max_space_per_root, max_iter=max_iter, nguess_extra=nguess_extra,
+                            res_tol=res_tol, keep_per_root=keep_per_root, refine=refine)
         if isinstance(eps, np.ndarray):
             eps = np.ascontiguousarray(eps, dtype=np.float64)
             B = np.ascontiguousarray(B, dtype=np.float64)
@@ -191,10 +203,29 @@ class ADC:
         rc = self._lib.adc_davidson(self._h, nroots, tol, None if g is None else g.ctypes.data, e.ctypes.data,
                                     p.ctypes.data, None if vec is None else vec.ctypes.data, st.ctypes.data)
         stats = dict(iterations=int(st[0]), sigma_vectors=int(st[1]), seconds=st[2], max_residual=st[3],
-                     sigma_seconds=st[4], refine_shift=st[5], refine_seconds=st[6], status=rc)
+                     sigma_seconds=st[4], refine_shift=st[5], refine_seconds=st[6], mlp_fallbacks=int(st[7]), status=rc)
         if rc not in (ADC_OK, ADC_ERR_NOT_CONVERGED):
             self._check(rc)
         return e, p, vec, stats
+
+    def set_options(self, **kw):
+        """Change solver options (max_space_per_root, max_iter, nguess_extra, res_tol, keep_per_root, refine)."""
+        opt = Options()
+        self._lib.adc_default_options(ctypes.byref(opt))
+        for k in ("max_space_per_root", "max_iter", "nguess_extra", "res_tol", "keep_per_root", "refine"):
+            setattr(opt, k, kw.pop(k, self._solver[k]))
+        if kw:
+            raise TypeError(f"not a solver option: {sorted(kw)}")
+        self._check(self._lib.adc_set_options(self._h, ctypes.byref(opt)))
+        self._solver = {k: getattr(opt, k) for k in self._solver}
+
+    def set_mlp(self, weights):
+        """Use the learned preconditioner with these weights (None: the diagonal one)."""
+        if weights is None:
+            self._check(self._lib.adc_set_mlp(self._h, None))
+        else:
+            w = np.ascontiguousarray(weights, dtype=np.float32)
+            self._check(self._lib.adc_set_mlp(self._h, w.ctypes.data))
 
     def get(self, name, shape):
         out = np.zeros(int(np.prod(shape)))
@@ -285,3 +316,44 @@ class ADCBatch:
             self.close()
         except Exception:
             pass
+
+
+def mlp_nweights():
+    return load_library().adc_mlp_nweights()
+
+
+def _mlp_samples(d, blk, r, t):
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    blk = np.ascontiguousarray(blk, dtype=np.uint8)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    if not (d.shape == blk.shape == r.shape == t.shape) or d.ndim != 1:
+        raise ValueError("samples must be 1-D arrays of one length")
+    return d, blk, r, t
+
+
+def mlp_loss_grad(weights, d, blk, r, t):
+    """(loss, gradient) of the learned preconditioner on samples (adc_mlp_loss_grad)."""
+    lib = load_library()
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    d, blk, r, t = _mlp_samples(d, blk, r, t)
+    grad = np.zeros(lib.adc_mlp_nweights(), dtype=np.float32)
+    loss = ctypes.c_double()
+    rc = lib.adc_mlp_loss_grad(w.ctypes.data, d.ctypes.data, blk.ctypes.data, r.ctypes.data, t.ctypes.data, d.size,
+                               grad.ctypes.data, ctypes.byref(loss))
+    if rc != ADC_OK:
+        raise ADCError(rc, lib.adc_last_error(None).decode())
+    return loss.value, grad
+
+
+def mlp_train(weights, d, blk, r, t, steps=500, lr=1e-3):
+    """Full-batch Adam on the GPU (adc_mlp_train); returns (weights, loss history)."""
+    lib = load_library()
+    w = np.array(weights, dtype=np.float32)
+    d, blk, r, t = _mlp_samples(d, blk, r, t)
+    hist = np.zeros(max(steps, 1))
+    rc = lib.adc_mlp_train(w.ctypes.data, d.ctypes.data, blk.ctypes.data, r.ctypes.data, t.ctypes.data, d.size, steps,
+                           float(lr), hist.ctypes.data)
+    if rc != ADC_OK:
+        raise ADCError(rc, lib.adc_last_error(None).decode())
+    return w, hist[:steps]

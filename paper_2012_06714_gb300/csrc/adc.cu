@@ -25,6 +25,7 @@
 #include "../../include/adc.h"
 #include "common.cuh"
 #include "ladder_tc.cuh"
+#include "mlp.cuh"
 
 using namespace adc;
 
@@ -45,6 +46,7 @@ struct adc_handle {
     bool refining = false;  // sigma evaluates with lm_refine
     int cmode_setup = 0, cmode_sigma = 0;  // Ctx::gemm_mode in setup / in sigma
     std::vector<double> X_last;             // spectroscopic amplitudes [nroots][nmo] of the last adc_davidson
+    float* mlp_w = nullptr;                 // learned preconditioner weights (device), NULL: diagonal
     double* Lt = nullptr;    // setup only: sum_cd (ac|bd) t_kl^cd, shared by t2(2) and the EA 1p-1p block
     std::vector<void*> owned;
     cudaStream_t own_stream = nullptr;  // created by adc_setup_batch, destroyed with the handle
@@ -822,6 +824,10 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
     if (d.k < nroots) throw Error(ADC_ERR_ARG, "davidson: guess space too small");
     d.sigma(0, d.k);
     std::vector<double> wold(nroots, INFINITY), w, C, G, rn(nroots);
+    // learned preconditioner: a root whose residual has not dropped below 0.9 x its best for
+    // 4 iterations falls back to the diagonal one for the rest of the run
+    std::vector<double> best_rn(nroots, INFINITY);
+    std::vector<int> stall(nroots, 0), diag_only(nroots, h->mlp_w ? 0 : 1);
     int it = 0, status = ADC_ERR_NOT_CONVERGED;
     int maxit = std::max(1, h->opt.max_iter);
     for (it = 1; it <= maxit; ++it) {
@@ -861,6 +867,12 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
                 todo.push_back(r);
             }
             wold[r] = w[r];
+            if (rn[r] < 0.9 * best_rn[r]) {
+                best_rn[r] = rn[r];
+                stall[r] = 0;
+            } else if (++stall[r] >= 4) {
+                diag_only[r] = 1;
+            }
         }
         if (all) {
             status = ADC_OK;
@@ -892,8 +904,15 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
                                      cudaMemcpyDeviceToDevice, c.stream));
         }
         ADC_CUDA(cudaMemcpyAsync(wd, wt.data(), nnew * sizeof(double), cudaMemcpyHostToDevice, c.stream));
-        k_precond<<<grid_for((long long)nnew * dim), 256, 0, c.stream>>>(nnew, dim, SR, wd, h->diag, d.V + (long long)d.k * dim);
-        launch_check(c);
+        for (int j = 0; j < nnew; ++j) {
+            double* dst = d.V + (long long)(d.k + j) * dim;
+            if (diag_only[todo[j]]) {
+                k_precond<<<grid_for(dim), 256, 0, c.stream>>>(1, dim, SR + (long long)j * dim, wd + j, h->diag, dst);
+                launch_check(c);
+            } else {
+                mlp_precondition(c, 1, dim, h->n1(), SR + (long long)j * dim, wd + j, h->diag, h->mlp_w, dst);
+            }
+        }
         int kept = d.orthonormalise(d.k, nnew);
         if (kept == 0) {
             status = ADC_OK;
@@ -1064,7 +1083,10 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
         stats[4] = d.sigma_seconds;
         stats[5] = refine_shift;
         stats[6] = refine_sec;
-        stats[7] = 0.0;
+        int fell = 0;
+        if (h->mlp_w)
+            for (int r = 0; r < nroots; ++r) fell += diag_only[r];
+        stats[7] = fell;
     }
     return status;
 }
@@ -1112,6 +1134,72 @@ int adc_spectrum(const double* energies, const double* specfac, int nroots, doub
         A[k] = a / M_PI;
     }
     return ADC_OK;
+}
+
+int adc_mlp_nweights(void) { return mlp_nweights(); }
+
+int adc_mlp_loss_grad(const float* weights, const double* d, const unsigned char* blk, const double* r, const double* t,
+                      long long n, float* grad, double* loss) {
+    if (!weights || !grad || !loss || n < 1 || !d || !blk || !r || !t) return ADC_ERR_ARG;
+    try {
+        *loss = mlp_loss_grad_host(weights, d, blk, r, t, n, grad);
+        return ADC_OK;
+    } catch (const adc::Error& e) {
+        g_setup_error = e.what();
+        return e.code;
+    } catch (const std::exception& e) {
+        g_setup_error = e.what();
+        return ADC_ERR_CUDA;
+    }
+}
+
+int adc_mlp_train(float* weights, const double* d, const unsigned char* blk, const double* r, const double* t, long long n,
+                  int steps, float lr, double* loss_hist) {
+    if (!weights || n < 1 || steps < 0 || !(lr > 0) || !d || !blk || !r || !t) return ADC_ERR_ARG;
+    try {
+        mlp_train_host(weights, d, blk, r, t, n, steps, lr, loss_hist);
+        return ADC_OK;
+    } catch (const adc::Error& e) {
+        g_setup_error = e.what();
+        return e.code;
+    } catch (const std::exception& e) {
+        g_setup_error = e.what();
+        return ADC_ERR_CUDA;
+    }
+}
+
+int adc_set_options(adc_handle* h, const adc_options* opt) {
+    if (!h || !opt) return ADC_ERR_ARG;
+    if (opt->max_space_per_root < 1 || opt->max_iter < 1 || opt->nguess_extra < 0 || opt->keep_per_root < 1 ||
+        opt->refine < 0 || opt->refine > 2) {
+        h->err = "adc_set_options: invalid option";
+        return ADC_ERR_ARG;
+    }
+    // solver options only; precision, contractions and aux_chunk are fixed at setup
+    h->opt.max_space_per_root = opt->max_space_per_root;
+    h->opt.max_iter = opt->max_iter;
+    h->opt.nguess_extra = opt->nguess_extra;
+    h->opt.res_tol = opt->res_tol;
+    h->opt.keep_per_root = opt->keep_per_root;
+    h->opt.refine = opt->refine;
+    return ADC_OK;
+}
+
+int adc_set_mlp(adc_handle* h, const float* weights) {
+    if (!h) return ADC_ERR_ARG;
+    GUARD(h, {
+        if (!weights) {
+            h->mlp_w = nullptr;  // the buffer stays owned by the handle
+            return ADC_OK;
+        }
+        const int nw = mlp_nweights();
+        float* w = (float*)dev_alloc(nw * sizeof(float), h->ctx.stream);
+        h->owned.push_back(w);
+        ADC_CUDA(cudaMemcpyAsync(w, weights, nw * sizeof(float), cudaMemcpyHostToDevice, h->ctx.stream));
+        ADC_CUDA(cudaStreamSynchronize(h->ctx.stream));
+        h->mlp_w = w;
+        return ADC_OK;
+    })
 }
 
 int adc_default_options(adc_options* opt) {
