@@ -187,13 +187,14 @@ int adc_davidson_batch(adc_handle* const* h, int nmol, int nroots, double tol, d
 int adc_get_tensor(adc_handle* h, const char* name, double* out, long long n);
 
 /*
- * Live timing of the tensor-core ladder kernel launches (for roofline
- * reporting).  enable = 1 clears the record and starts bracketing every
- * tensor-core GEMM launch on the handle's stream with CUDA events; enable = 0
- * stops, synchronises and, if out is non-NULL, writes out[5] =
- * {launches, total milliseconds of those launches, algorithmic flops
- * (4 naux nocc nvir^3-type count, unpadded), tensor-core flops issued
- * (3 split products over padded tiles), all own kernels launched meanwhile}.
+ * Live timing of the tensor-core GEMM launches (for roofline reporting).
+ * enable = 1 clears the record and starts bracketing every tensor-core GEMM
+ * launch on the handle's stream with CUDA events; enable = 0 stops,
+ * synchronises and, if out is non-NULL, writes out[9] = {launches, total
+ * milliseconds of those launches, algorithmic flops (unpadded), tensor-core
+ * flops issued (split products over padded tiles), all own kernels launched
+ * meanwhile, and for the DF-ladder GEMMs alone: launches, milliseconds,
+ * algorithmic flops (4 naux nocc nvir^3-type count), tensor-core flops}.
  * Errors: ADC_ERR_ARG, ADC_ERR_CUDA.
  */
 int adc_kernel_timing(adc_handle* h, int enable, double* out);

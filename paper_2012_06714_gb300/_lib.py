@@ -235,12 +235,14 @@ class ADC:
     def kernel_timing(self, enable: bool):
         """Start (True) or stop (False) live timing of the tensor-core launches.
 
-        On stop returns dict(launches, ms, algo_flops, mma_flops, kernels)."""
-        out = np.zeros(5)
+        On stop returns dict(launches, ms, algo_flops, mma_flops, kernels) over all tensor-core GEMM
+        launches, and the same for the DF-ladder GEMMs alone (ladder_launches, ladder_ms, ...)."""
+        out = np.zeros(9)
         self._check(self._lib.adc_kernel_timing(self._h, 1 if enable else 0, out.ctypes.data))
         if enable:
             return None
-        return dict(launches=int(out[0]), ms=out[1], algo_flops=out[2], mma_flops=out[3], kernels=int(out[4]))
+        return dict(launches=int(out[0]), ms=out[1], algo_flops=out[2], mma_flops=out[3], kernels=int(out[4]),
+                    ladder_launches=int(out[5]), ladder_ms=out[6], ladder_algo_flops=out[7], ladder_mma_flops=out[8])
 
     def close(self):
         if getattr(self, "_h", None):

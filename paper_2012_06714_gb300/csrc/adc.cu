@@ -1451,20 +1451,30 @@ int adc_kernel_timing(adc_handle* h, int enable, double* out) {
             for (auto e : c.ev_stop) cudaEventDestroy(e);
             c.ev_start.clear();
             c.ev_stop.clear();
+            c.ev_ladder.clear();
+            c.ev_algo.clear();
+            c.ev_mma.clear();
             c.algo_flops = c.mma_flops = 0.0;
             c.kernels_at_start = c.kernels;
             c.timing = true;
             if (out)
-                for (int i = 0; i < 5; ++i) out[i] = 0.0;
+                for (int i = 0; i < 9; ++i) out[i] = 0.0;
             return ADC_OK;
         }
         c.timing = false;
         ADC_CUDA(cudaStreamSynchronize(c.stream));
-        double ms = 0.0;
+        double ms = 0.0, lms = 0.0, lalgo = 0.0, lmma = 0.0;
+        long long nl = 0;
         for (size_t i = 0; i < c.ev_start.size(); ++i) {
             float t = 0.f;
             ADC_CUDA(cudaEventElapsedTime(&t, c.ev_start[i], c.ev_stop[i]));
             ms += t;
+            if (c.ev_ladder[i]) {
+                ++nl;
+                lms += t;
+                lalgo += c.ev_algo[i];
+                lmma += c.ev_mma[i];
+            }
         }
         if (out) {
             out[0] = (double)c.ev_start.size();
@@ -1472,6 +1482,10 @@ int adc_kernel_timing(adc_handle* h, int enable, double* out) {
             out[2] = c.algo_flops;
             out[3] = c.mma_flops;
             out[4] = (double)(c.kernels - c.kernels_at_start);
+            out[5] = (double)nl;
+            out[6] = lms;
+            out[7] = lalgo;
+            out[8] = lmma;
         }
         return ADC_OK;
     })

@@ -83,6 +83,14 @@ __global__ void permute_split_kernel(const double* __restrict__ in, __nv_bfloat1
     }
 }
 
+__global__ void sum_slices_kernel(int S, long long n, const double* __restrict__ T, double* __restrict__ C) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double a = 0.0;
+        for (int s = 0; s < S; ++s) a += T[s * n + i];
+        C[i] = a;
+    }
+}
+
 inline int grid_for(long long n) {
     long long g = (n + 255) / 256;
     return (int)std::min<long long>(std::max<long long>(g, 1), 152LL * 32);
@@ -155,6 +163,25 @@ void axpby(Ctx& c, long long n, double alpha, const double* x, double beta, doub
     axpby_kernel<<<grid_for(n), 256, 0, c.stream>>>(n, alpha, x, beta, y);
     ++c.kernels;
     ADC_CUDA(cudaGetLastError());
+}
+
+void sum_slices(Ctx& c, int S, long long n, const double* T, double* C) {
+    if (n <= 0) return;
+    sum_slices_kernel<<<grid_for(n), 256, 0, c.stream>>>(S, n, T, C);
+    ++c.kernels;
+    ADC_CUDA(cudaGetLastError());
+}
+
+void ensure_side_streams(Ctx& c, int count) {
+    if (!c.side_fork) ADC_CUDA(cudaEventCreateWithFlags(&c.side_fork, cudaEventDisableTiming));
+    while ((int)c.side.size() < count) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+        ADC_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        ADC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        c.side.push_back(s);
+        c.side_join.push_back(e);
+    }
 }
 
 void fill(Ctx& c, long long n, double v, double* y) {

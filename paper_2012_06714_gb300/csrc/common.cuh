@@ -124,6 +124,8 @@ struct Ctx {
     // live timing of the tensor-core GEMM launches (see adc_kernel_timing)
     bool timing = false;
     std::vector<cudaEvent_t> ev_start, ev_stop;
+    std::vector<char> ev_ladder;          // launch is one of the DF ladder GEMMs
+    std::vector<double> ev_algo, ev_mma;  // its algorithmic / issued tensor-core flops
     double algo_flops = 0.0, mma_flops = 0.0;
     long long kernels_at_start = 0;
     // FP32 copies (in GEMM operand order) of operands marked constant, reused across calls
@@ -131,10 +133,17 @@ struct Ctx {
     // split BF16 planes (K-major GEMM operand order) of operands marked constant
     std::map<std::pair<const void*, std::string>, void*> bf16cache;
     int* d_err = nullptr;  // device flag raised by a bounded wait that gave up (tensor-core GEMMs)
+    // side streams for concurrent K slices of a contraction, with their fork / join events
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> side_join;
+    cudaEvent_t side_fork = nullptr;
     ~Ctx() {
         for (auto& kv : f32cache) cudaFree(kv.second);
         for (auto& kv : bf16cache) cudaFree(kv.second);
         if (d_err) cudaFree(d_err);
+        for (auto s : side) cudaStreamDestroy(s);
+        for (auto e : side_join) cudaEventDestroy(e);
+        if (side_fork) cudaEventDestroy(side_fork);
         for (auto e : ev_start) cudaEventDestroy(e);
         for (auto e : ev_stop) cudaEventDestroy(e);
     }
@@ -150,6 +159,10 @@ struct Shape {
 void permute(Ctx& c, const double* in, const Shape& in_shape, const int* perm, double* out, double alpha, double beta);
 void axpby(Ctx& c, long long n, double alpha, const double* x, double beta, double* y);  // y = a x + b y
 void fill(Ctx& c, long long n, double v, double* y);
+// C[i] = sum_s T[s*n + i]
+void sum_slices(Ctx& c, int S, long long n, const double* T, double* C);
+// make at least `count` side streams (non-blocking) and their events
+void ensure_side_streams(Ctx& c, int count);
 
 // ---- contraction executor -------------------------------------------------
 struct T {

@@ -961,6 +961,23 @@ CUtensorMap make_map_z(const void* base, int vp, int qn, int v, long long nm) {
     return m;
 }
 
+// 2-D BF16 tensor [rows][cols] with a row stride of `ld` elements (a column
+// slice of a wider matrix); box {BK, box_rows}, ROW_BYTES swizzle
+CUtensorMap make_map_ld(const void* base, long long rows, long long cols, long long ld, int box_rows) {
+    if (((uintptr_t)base & 15) || (ld * 2) % 16) throw Error(-1, "tensor map: misaligned operand slice");
+    CUtensorMap m;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             ROW_BYTES == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw Error(-3, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    return m;
+}
+
 int pick_bn(int n, int maxbn) {
     int best = maxbn;
     double best_cost = 1e300;
@@ -1018,7 +1035,8 @@ const DevInfo& dev_info() {
 // ekb: accumulation epoch in 64-deep K blocks (0 = one epoch per tile);
 // pair: 256-row tiles on CTA pairs (k_gemm_pair), else 128-row tiles per CTA
 void launch_gemm(Ctx& c, const Maps& maps, int planes, int a_row0, int b_x0, int M, int N, int K, int BN, int m_fastest,
-                 int ekb, bool pair, const Epi& ep, double algo_flops) {
+                 int ekb, bool pair, const Epi& ep, double algo_flops, cudaStream_t stream_override = nullptr) {
+    const cudaStream_t st = stream_override ? stream_override : c.stream;
     if (BN % 16 || BN < 16 || BN > 256) throw Error(-1, "ladder: tile width must be a multiple of 16 in [16, 256]");
     const DevInfo& di = dev_info();
     const int num_sms = di.num_sms, max_pairs = di.max_pairs;
@@ -1044,7 +1062,7 @@ void launch_gemm(Ctx& c, const Maps& maps, int planes, int a_row0, int b_x0, int
     cl[0].val.clusterDim.z = 1;
     cfg.blockDim = dim3(THREADS);
     cfg.dynamicSmemBytes = SMEM_BYTES;
-    cfg.stream = c.stream;
+    cfg.stream = st;
     cfg.attrs = cl;
     cfg.numAttrs = 1;
     int grid;
@@ -1059,7 +1077,7 @@ void launch_gemm(Ctx& c, const Maps& maps, int planes, int a_row0, int b_x0, int
     if (c.timing) {
         ADC_CUDA(cudaEventCreate(&e0));
         ADC_CUDA(cudaEventCreate(&e1));
-        ADC_CUDA(cudaEventRecord(e0, c.stream));
+        ADC_CUDA(cudaEventRecord(e0, st));
     }
     // epoch length in the kernel's K blocks (MMAs per epoch = ekb * BK/16 * (3 or 6 products))
     ekb = ekb <= 0 ? (K + BK - 1) / BK : ekb * KB_PER_EPOCH_UNIT;
@@ -1070,17 +1088,21 @@ void launch_gemm(Ctx& c, const Maps& maps, int planes, int a_row0, int b_x0, int
         ADC_CUDA(cudaLaunchKernelEx(&cfg, kp, maps, planes, a_row0, b_x0, K, BN, stages, m_fastest, mt, nt, ekb, nbuf, ep));
     } else {
         auto kern = promote ? k_gemm_bf16x3<true> : k_gemm_bf16x3<false>;
-        kern<<<grid, THREADS, SMEM_BYTES, c.stream>>>(maps, planes, a_row0, b_x0, K, BN, stages, m_fastest, mt, nt, ekb, nbuf,
+        kern<<<grid, THREADS, SMEM_BYTES, st>>>(maps, planes, a_row0, b_x0, K, BN, stages, m_fastest, mt, nt, ekb, nbuf,
                                                       ep);
     }
     ++c.kernels;
     ADC_CUDA(cudaGetLastError());
     if (c.timing) {
-        ADC_CUDA(cudaEventRecord(e1, c.stream));
+        ADC_CUDA(cudaEventRecord(e1, st));
         c.ev_start.push_back(e0);
         c.ev_stop.push_back(e1);
+        const double mma = (planes == 3 ? 6.0 : 3.0) * 2.0 * (double)mt * BM * (double)nt * BN * (double)(((K + BK - 1) / BK) * BK);
+        c.ev_ladder.push_back(ep.mode != 2);  // the DF ladder's two GEMMs (mode 2: other contractions)
+        c.ev_algo.push_back(algo_flops);
+        c.ev_mma.push_back(mma);
         c.algo_flops += algo_flops;
-        c.mma_flops += (planes == 3 ? 6.0 : 3.0) * 2.0 * (double)mt * BM * (double)nt * BN * (double)(((K + BK - 1) / BK) * BK);
+        c.mma_flops += mma;
     }
 }
 
@@ -1220,11 +1242,12 @@ void ladder_tc_apply(LadderTC& L, Ctx& c, const double* X, long long nmat, doubl
     if (planes != 2 && planes != 3) throw Error(-1, "ladder: planes must be 2 or 3");
     if (md.epoch1 < 0 || md.epoch2 < 0) throw Error(-1, "ladder: negative epoch length");
     if (planes > L.nplanes) split_B(L, c, planes);  // the third plane only when first asked for
-    // Scratch budget for Z (all planes): ~1 GiB.  Matrices are processed in
+    // Scratch budget for Z (all planes): ~4 GiB.  Matrices are processed in
     // groups small enough that a chunk holds >= 8 auxiliary functions (long K
-    // in GEMM2, fewer FP64 read-modify-write passes over the output); K2 <= 8192.
-    const long long budget = 1LL << 30;
-    const int qmax = std::max(1, std::min(naux, std::max(1, 8192 / vp)));
+    // in GEMM2, fewer FP64 read-modify-write passes over the output); with
+    // promotion of the FP32 partial sums K2 = chunk * vp has no accuracy limit.
+    const long long budget = 4LL << 30;
+    const int qmax = std::max(1, naux);
     const int qwant = L.chunk > 0 ? std::min(L.chunk, qmax) : std::min(8, qmax);
     const long long per_mq = (long long)v * vp * 2 * planes;  // Z bytes per (matrix, aux function)
     long long mg = std::max<long long>(1, budget / (per_mq * qwant));
@@ -1278,10 +1301,11 @@ bool ladder_tc_apply_scratch(LadderTC& L, Ctx& c, const double* X, long long nma
 
 // ---- generic split-BF16 contraction (gemm_mode 2) --------------------------
 bool tc_gemm_worthwhile(long long M, long long N, long long K) {
-    // enough 256 x 256 tiles to occupy the CTA pairs (no split-K in the kernel),
-    // K long enough to amortise a tile, and 32-bit tile coordinates
+    // enough 256 x 256 tiles to occupy the CTA pairs -- directly, or (few tiles, long K) as
+    // up to 16 concurrent K slices -- and 32-bit tile coordinates
     const long long tiles = ((M + 255) / 256) * ((N + 255) / 256);
-    return tiles >= 64 && K >= 256 && M < (1LL << 30) && N < (1LL << 30) && K < (1LL << 30);
+    if (M >= (1LL << 30) || N >= (1LL << 30) || K >= (1LL << 30)) return false;
+    return (tiles >= 64 && K >= 256) || (tiles >= 4 && K >= 4096);
 }
 
 void tc_gemm(Ctx& c, const void* const* A, const void* const* B, long long M, long long N, long long Kp, double algo_flops,
@@ -1289,21 +1313,51 @@ void tc_gemm(Ctx& c, const void* const* A, const void* const* B, long long M, lo
     if (!c.d_err) throw Error(-1, "tc_gemm: no device error flag");
     const int BN = pick_bn((int)std::min<long long>(N, 1 << 20), 256);
     const bool pair = true;
-    Maps m{};
-    for (int p = 0; p < 2; ++p) {
-        m.a[p] = make_map(A[p], M, Kp, BM);
-        m.b[p] = make_map(B[p], N, Kp, pair ? BN / 2 : BN);
+    const long long tiles = ((M + 255) / 256) * ((N + BN - 1) / BN);
+    // K slices, each its own launch on a side stream (the launches of few tiles run side by side)
+    int S = 1;
+    long long ks = Kp;
+    if (tiles < 64) {
+        S = (int)std::min<long long>(16, std::max<long long>(2, (64 + tiles - 1) / tiles));
+        ks = ((Kp + S - 1) / S + 63) / 64 * 64;
+        S = (int)((Kp + ks - 1) / ks);
     }
     Epi e{};
     e.mode = 2;
     e.M = (int)M;
     e.N = (int)N;
-    e.out = C;
     e.ldc = N;
-    e.vec = ((uintptr_t)C % 16 == 0) && (N % 2 == 0);
     e.err = c.d_err;
-    // consecutive tiles share the B tile when A is the smaller operand (A then stays in L2)
-    launch_gemm(c, m, 2, 0, 0, (int)M, (int)N, (int)Kp, BN, M <= N ? 1 : 0, 16, pair, e, algo_flops);
+    const int m_fastest = M <= N ? 1 : 0;  // consecutive tiles share the B tile when A is the smaller operand
+    if (S == 1) {
+        Maps m{};
+        for (int p = 0; p < 2; ++p) {
+            m.a[p] = make_map(A[p], M, Kp, BM);
+            m.b[p] = make_map(B[p], N, Kp, pair ? BN / 2 : BN);
+        }
+        e.out = C;
+        e.vec = ((uintptr_t)C % 16 == 0) && (N % 2 == 0);
+        launch_gemm(c, m, 2, 0, 0, (int)M, (int)N, (int)Kp, BN, m_fastest, 16, pair, e, algo_flops);
+        return;
+    }
+    double* T = c.arena.dalloc((size_t)(S * M * N));
+    ensure_side_streams(c, S);
+    ADC_CUDA(cudaEventRecord(c.side_fork, c.stream));
+    for (int sl = 0; sl < S; ++sl) {
+        const long long k0 = sl * ks, kn = std::min(ks, Kp - k0);
+        Maps m{};
+        for (int p = 0; p < 2; ++p) {
+            m.a[p] = make_map_ld((const __nv_bfloat16*)A[p] + k0, M, kn, Kp, BM);
+            m.b[p] = make_map_ld((const __nv_bfloat16*)B[p] + k0, N, kn, Kp, pair ? BN / 2 : BN);
+        }
+        e.out = T + sl * M * N;
+        e.vec = ((uintptr_t)e.out % 16 == 0) && (N % 2 == 0);
+        ADC_CUDA(cudaStreamWaitEvent(c.side[sl], c.side_fork, 0));
+        launch_gemm(c, m, 2, 0, 0, (int)M, (int)N, (int)kn, BN, m_fastest, 16, pair, e, algo_flops * kn / Kp, c.side[sl]);
+        ADC_CUDA(cudaEventRecord(c.side_join[sl], c.side[sl]));
+    }
+    for (int sl = 0; sl < S; ++sl) ADC_CUDA(cudaStreamWaitEvent(c.stream, c.side_join[sl], 0));
+    sum_slices(c, S, M * N, T, C);
 }
 
 }  // namespace adc
