@@ -28,31 +28,57 @@ def dense_roots(adc, nroots):
 
 
 def transition_moments(adc):
-    """Spatial T through second order: (T1 [nmo, n1], T2 [nmo, ...2p1h/2h1p shape]).
+    """Spatial T through order n = adc.order (Eqs. T_ea, T_ip, k + l <= n):
+    (T1 [nmo, n1], T2 [nmo, ...2p1h/2h1p shape]).
 
-    EA: T_{c,b} = d_cb - sum t_kl^cd t_kl^bd + 1/2 sum t_kl^cd t_kl^db,
-        T_{k,b} = -t_k^b(2), T_{k,jcd} = -t_kj^dc, T_{c,jde} = 0.
-    IP: T_{k,j} = d_kj - sum t_kl^cd t_jl^cd + 1/2 sum t_kl^cd t_jl^dc,
-        T_{c,j} = t_j^c(2), T_{c,ija} = -t_ij^ac, T_{k,ija} = 0.
-    (First order vanishes; t_k^b(2) enters only at third-order M, so for
+    Second order, with the density form B(x, y) (EA) / B'(x, y) (IP)
+      B(x, y)_cb  = -sum x_kl^cd y_kl^bd + 1/2 sum x_kl^cd y_kl^db,
+      B'(x, y)_kj = -sum x_kl^cd y_jl^cd + 1/2 sum x_kl^cd y_jl^dc:
+    EA: T_{c,b} = d_cb + B(t, t)_cb, T_{k,b} = -t_k^b(2), T_{k,jcd} = -t_kj^dc, T_{c,jde} = 0.
+    IP: T_{k,j} = d_kj + B'(t, t)_kj, T_{c,j} = t_j^c(2), T_{c,ija} = -t_ij^ac, T_{k,ija} = 0.
+    (First order vanishes; t_k^b(2) enters M only at third order, so for
     ADC(2) it is still included here as the second-order T term.)
+    Third order (ADC(3)) adds, with tau = 2t - t(ab swapped):
+    EA: T_{c,b} += B(t, t2)_cb + B(t2, t)_cb, T_{k,b} -= t_k^b(3) + 1/2 sum tau_kl^bc t_l^c(2),
+        T_{k,jcd} -= t2_kj^dc;
+    IP: T_{k,j} += B'(t, t2)_kj + B'(t2, t)_kj, T_{c,j} += t_j^c(3) + 1/2 sum tau_jl^cd t_l^d(2),
+        T_{c,ija} -= t2_ij^ac
+    (t2 = t2(2); the spin integration of the spin-orbital third-order terms).
     """
     o, v = adc.o, adc.v
     t = adc.t
     t1 = adc.t1_2 if hasattr(adc, "t1_2") else _t1_second_order(adc)
     nmo = o + v
+    third = adc.order >= 3
+    if third:
+        t2 = adc.t_2
+        tau = 2.0 * t - t.transpose(0, 1, 3, 2)
     if adc.kind == "ea":
+        def dens(x, y):
+            return -np.einsum("klcd,klbd->cb", x, y) + 0.5 * np.einsum("klcd,kldb->cb", x, y)
+
         T1 = np.zeros((nmo, v))
-        T1[o:] = np.eye(v) - np.einsum("klcd,klbd->cb", t, t) + 0.5 * np.einsum("klcd,kldb->cb", t, t)
+        T1[o:] = np.eye(v) + dens(t, t)
         T1[:o] = -t1
         T2 = np.zeros((nmo, o, v, v))
         T2[:o] = -t.transpose(0, 1, 3, 2)
+        if third:
+            T1[o:] += dens(t, t2) + dens(t2, t)
+            T1[:o] -= adc.t1_3 + 0.5 * np.einsum("klbc,lc->kb", tau, t1)
+            T2[:o] -= t2.transpose(0, 1, 3, 2)
     else:
+        def dens(x, y):
+            return -np.einsum("klcd,jlcd->kj", x, y) + 0.5 * np.einsum("klcd,jldc->kj", x, y)
+
         T1 = np.zeros((nmo, o))
-        T1[:o] = np.eye(o) - np.einsum("klcd,jlcd->kj", t, t) + 0.5 * np.einsum("klcd,jldc->kj", t, t)
+        T1[:o] = np.eye(o) + dens(t, t)
         T1[o:] = t1.T
         T2 = np.zeros((nmo, o, o, v))
         T2[o:] = -t.transpose(3, 0, 1, 2)
+        if third:
+            T1[:o] += dens(t, t2) + dens(t2, t)
+            T1[o:] += adc.t1_3.T + 0.5 * np.einsum("jlcd,ld->cj", tau, t1)
+            T2[o:] -= t2.transpose(3, 0, 1, 2)
     return T1, T2
 
 

@@ -108,6 +108,61 @@ class SpinAdaptedADC:
         s1 = self.ovvv_contract(tau, "Qkc,Qad,ikdc->ia")
         s2 = np.einsum("kilc,klac->ia", self.ooov, tau, optimize=True)
         self.t1_2 = (s1 - s2) / D1
+        self.t1_3 = self._t1_third_order()
+
+    def _t1_third_order(self):
+        """Third-order singles t_i^a(3) (Eq. t_singles at k = 3), spin-integrated.
+
+        Spin-orbital form: D t(3) = A + 1/4 t_jk^bc W_ijk^abc, plus
+        1/2 t_ij^ab t_j^b(2) after the division (A: the t1(2) and t2(2) singles
+        terms; W: connected first-order triples).  Integrating over spin with
+        tau = 2t - t(ab swapped), u = t - t(ab swapped) gives, term for term,
+          A1 = sum [2 (ia|jb) - (ij|ab)] t_j^b(2)
+          A2 = the t1(2) expression with tau(2) built from t2(2)
+          E1 = sum tau_ij^ad Y_jd,  Y_jd = 2 sum tau_jk^bc (bd|kc)
+          E2 = -4 sum t_jk^ad tau_jk^cb (bd|ic)
+          E3 = sum (ad|kc) R1_ik^dc + sum (ka|cd) R2_ik^cd
+          E4 = sum rho_cd [2 (ia|cd) - (ad|ic)],  rho_cd = 2 sum t_jk^cb tau_jk^db
+          F1 = sum tau_il^ab Z_lb,  Z_lb = 2 sum tau_jk^bc (lj|kc)
+          F2 = sum (li|kc) R1_lk^ac + sum (lk|ic) R2_lk^ca
+          F3 = 4 sum (lj|ka) X_jkil,  X_jkil = sum t_jk^bc u_il^bc - t_kj^bc t_il^bc
+          F4 = sum rho'_kl [2 (lk|ia) - (li|ka)],  rho'_kl = 2 sum t_jk^bc tau_jl^bc
+        with the ring products R1_ik^dc = sum tau_ij^db tau_jk^bc and
+        R2_ik^cd = -sum (tau_ij^db t_jk^bc + tau_ij^bd t_jk^cb), and
+        D t(3) = A1 + A2 + (2 E1 + E2 + 4 E3 + 2 E4)/4 - (2 F1 + 4 F2 + F3 + 2 F4)/4.
+        """
+        t, t1, t2 = self.t, self.t1_2, self.t_2
+        Boo, Bov, Bvv = self.Boo, self.Bov, self.Bvv
+
+        def e(spec, *ops):
+            return np.einsum(spec, *ops, optimize=True)
+
+        sw = (0, 1, 3, 2)
+        tau = 2.0 * t - t.transpose(sw)
+        u = t - t.transpose(sw)
+        tau2 = 2.0 * t2 - t2.transpose(sw)
+        A1 = 2.0 * e("iajb,jb->ia", self.ovov, t1) - e("jiab,jb->ia", self.oovv, t1)
+        A2 = self.ovvv_contract(tau2, "Qkc,Qad,ikdc->ia") - e("kilc,klac->ia", self.ooov, tau2)
+        E1 = e("ijad,jd->ia", tau, 2.0 * self.ovvv_contract(tau, "Qkc,Qbd,jkbc->jd"))
+        # E2 one auxiliary index at a time: V_jkdi = sum_Q sum_b B^Q_db sum_c tau_jk^cb B^Q_ic
+        V = np.zeros((self.o, self.o, self.v, self.o))
+        for q in range(Boo.shape[0]):
+            Wq = np.tensordot(tau, Bov[q], axes=([2], [1]))  # [j,k,b,i]
+            V += np.tensordot(Wq, Bvv[q], axes=([2], [1])).transpose(0, 1, 3, 2)  # [j,k,d,i]
+        E2 = -4.0 * e("jkad,jkdi->ia", t, V)
+        R1 = e("ijdb,jkbc->ikdc", tau, tau)
+        R2 = -e("ijdb,jkbc->ikcd", tau, t) - e("ijbd,jkcb->ikcd", tau, t)
+        E3 = e("Qad,Qkc,ikdc->ia", Bvv, Bov, R1) + e("Qka,Qcd,ikcd->ia", Bov, Bvv, R2)
+        rho = 2.0 * e("jkcb,jkdb->cd", t, tau)
+        E4 = 2.0 * e("Qia,Qcd,cd->ia", Bov, Bvv, rho) - e("Qad,Qic,cd->ia", Bvv, Bov, rho)
+        F1 = e("ilab,lb->ia", tau, 2.0 * e("Qlj,Qkc,jkbc->lb", Boo, Bov, tau))
+        F2 = e("Qli,Qkc,lkac->ia", Boo, Bov, R1) + e("Qlk,Qic,lkca->ia", Boo, Bov, R2)
+        X = e("jkbc,ilbc->jkil", t, u) - e("kjbc,ilbc->jkil", t, t)
+        F3 = 4.0 * e("ljka,jkil->ia", self.ooov, X)
+        rhoh = 2.0 * e("jkbc,jlbc->kl", t, tau)
+        F4 = 2.0 * e("lkia,kl->ia", self.ooov, rhoh) - e("lika,kl->ia", self.ooov, rhoh)
+        num = A1 + A2 + 0.25 * (2.0 * E1 + E2 + 4.0 * E3 + 2.0 * E4) - 0.25 * (2.0 * F1 + 4.0 * F2 + F3 + 2.0 * F4)
+        return num / self.D1 + 0.5 * e("ijab,jb->ia", tau, t1)
 
     # ---- 1p-1p / 1h-1h block (Table 1 second row; precomputed, Sec. III A) --
     def _m11(self):

@@ -19,6 +19,15 @@ Notation (spin orbitals, occupied i,j,k,l,m and virtual a,b,c,d,e):
                  + P(ij)P(ab) <kb||cj> t_ik^ac ] / D_ij^ab
   t_i^a(2)   = [ -1/2 <ka||cd> t_ik^cd - 1/2 <kl||ic> t_kl^ac ] / D_i^a
   (t1(1) = 0 because the Fock operator is diagonal.)
+  t_i^a(3)   = [ <aj||ib> t_j^b(2) - 1/2 <ka||cd> t_ik^cd(2) - 1/2 <kl||ic> t_kl^ac(2)
+                 + 1/4 t_jk^bc W_ijk^abc ] / D_i^a + 1/2 t_ij^ab t_j^b(2)
+  with the connected first-order triples
+  W_ijk^abc = P(k/ij) P(a/bc) <bc||dk> t_ij^ad - P(i/jk) P(c/ab) <lc||jk> t_il^ab.
+  This is the singles projection (Eq. t_singles) of the third-order effective
+  Hamiltonian: [V, sigma2] gives the CC-like singles terms of t1(2) and t2(2)
+  plus t1(2)+ V; the double commutators with H0 turn into -1/2 t1(2)+ V and
+  -1/2 (D t1(2))+ t2(1), which with it leave 1/2 t_ij^ab t_j^b(2); and
+  1/2 [[V, sigma1], sigma1] leaves the triples term T2+ V T2.
 
 Basis conventions (identical to fock.py): EA 2p1h state (i,a,b) is
 a_b+ a_a+ a_i |Phi>; IP 2h1p state (i,j,a) is (a_a+ a_j a_i)+ acting on the
@@ -87,6 +96,31 @@ class SpinOrbitalADC:
         self.t2_2 = num / self.D2
         num1 = -0.5 * np.einsum("kacd,ikcd->ia", g("ovvv"), t) - 0.5 * np.einsum("klic,klac->ia", g("ooov"), t)
         self.t1_2 = num1 / self.D1
+        if self.order >= 3:
+            self.t1_3 = self._t1_third_order()
+
+    def _t1_third_order(self):
+        """t_i^a(3) of the module docstring, with the triples term expanded.
+
+        1/4 t_jk^bc W_ijk^abc is summed permutation by permutation; equal
+        terms are collected, which leaves four particle contractions (E1..E4)
+        and four hole contractions (F1..F4), none of them forming W.
+        """
+        g = self.blk
+        t, t1, t2 = self.t2_1, self.t1_2, self.t2_2
+        A = np.einsum("ajib,jb->ia", g("voov"), t1)
+        A -= 0.5 * np.einsum("kacd,ikcd->ia", g("ovvv"), t2) + 0.5 * np.einsum("klic,klac->ia", g("ooov"), t2)
+        vvvo, ovoo = g("vvvo"), g("ovoo")
+        E1 = np.einsum("ijad,jkbc,bcdk->ia", t, t, vvvo, optimize=True)  # P(k/ij): 1, (jk)
+        E2 = np.einsum("jkad,jkbc,bcdi->ia", t, t, vvvo, optimize=True)  # (ik)
+        E3 = -np.einsum("acdk,ijbd,jkbc->ia", vvvo, t, t, optimize=True)  # P(a/bc): (ab), (ac)
+        E4 = -np.einsum("acdi,jkbc,jkbd->ia", vvvo, t, t, optimize=True)  # (ik)(ab), (ik)(ac)
+        F1 = np.einsum("ilab,jkbc,lcjk->ia", t, t, ovoo, optimize=True)  # P(c/ab): 1, (bc)
+        F2 = -np.einsum("lcik,jkbc,jlab->ia", ovoo, t, t, optimize=True)  # P(i/jk): (ij), (ik)
+        F3 = np.einsum("lajk,jkbc,ilbc->ia", ovoo, t, t, optimize=True)  # (ac)
+        F4 = -np.einsum("laik,jkbc,jlbc->ia", ovoo, t, t, optimize=True)  # (ij)(ac), (ik)(ac)
+        W = 0.25 * (2 * E1 + E2 + 4 * E3 + 2 * E4) - 0.25 * (2 * F1 + 4 * F2 + F3 + 2 * F4)
+        return (A + W) / self.D1 + 0.5 * np.einsum("ijab,jb->ia", t, t1)
 
     def mp2_energy(self):
         return 0.25 * float(np.einsum("ijab,ijab->", self.blk("oovv"), self.t2_1))
@@ -185,12 +219,18 @@ class SpinOrbitalADC:
             M = M + (R - R.transpose(0, 1, 2, 4, 3, 5))
         return M
 
-    # ---- transition moments (second order) --------------------------------
-    def ea_transition(self):
-        """T[p, nu] through second order for p over all spin orbitals.
+    # ---- transition moments (Eqs. T_ea, T_ip, orders k + l <= torder) -------
+    # First order vanishes in the one-particle columns.  Third order
+    # (torder = 3, needs order >= 3) adds the cross terms of the second-order
+    # density with t2(2), t1(3), the product t2(1) t1(2), and t2(2) in the
+    # two-particle columns; the 2p1h (2h1p) columns get no other second-order
+    # term.
+    def ea_transition(self, torder=None):
+        """T[p, nu] for p over all spin orbitals.
 
         Returns (T1 [nso, nv] for 1p columns, T2 [nso, o, v, v] for 2p1h columns).
         """
+        torder = self.order if torder is None else torder
         t = self.t2_1
         no, nv = self.no, self.nv
         T1 = np.zeros((self.nso, nv))
@@ -198,10 +238,16 @@ class SpinOrbitalADC:
         T1[:no] = -self.t1_2
         T2 = np.zeros((self.nso, no, nv, nv))
         T2[:no] = t
+        if torder >= 3:
+            t2 = self.t2_2
+            T1[no:] -= 0.25 * (np.einsum("klcd,klbd->cb", t, t2) + np.einsum("klcd,klbd->cb", t2, t))
+            T1[:no] -= self.t1_3 + 0.5 * np.einsum("klbc,lc->kb", t, self.t1_2)
+            T2[:no] += t2
         return T1, T2
 
-    def ip_transition(self):
-        """T[p, nu] through second order: (T1 [nso, o], T2 [nso, o, o, v])."""
+    def ip_transition(self, torder=None):
+        """T[p, nu]: (T1 [nso, o], T2 [nso, o, o, v])."""
+        torder = self.order if torder is None else torder
         t = self.t2_1
         no, nv = self.no, self.nv
         T1 = np.zeros((self.nso, no))
@@ -209,6 +255,11 @@ class SpinOrbitalADC:
         T1[no:] = self.t1_2.T
         T2 = np.zeros((self.nso, no, no, nv))
         T2[no:] = t.transpose(2, 0, 1, 3)
+        if torder >= 3:
+            t2 = self.t2_2
+            T1[:no] -= 0.25 * (np.einsum("klcd,jlcd->kj", t, t2) + np.einsum("klcd,jlcd->kj", t2, t))
+            T1[no:] += self.t1_3.T + 0.5 * np.einsum("jlcd,ld->cj", t, self.t1_2)
+            T2[no:] += t2.transpose(2, 0, 1, 3)
         return T1, T2
 
     # ---- dense matrix in the restricted basis ------------------------------

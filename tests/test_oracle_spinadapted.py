@@ -42,6 +42,44 @@ def test_sigma_matches_spin_orbital(o, v, seed, order, kind):
     assert np.abs(A - A.T).max() < 1e-12
 
 
+@pytest.mark.parametrize("o,v,seed", [(3, 4, 2), (2, 5, 4)])
+def test_third_order_singles_match_spin_orbital(o, v, seed):
+    """Spatial t_i^a(3) equals the alpha-alpha block of the spin-orbital one
+    (spin orbital 2p + s); the alpha-beta block vanishes."""
+    s = make_system(o, v, 16, seed=seed)
+    B = 2.0 * s.B
+    T = SpinAdaptedADC(s.eps, o, B, 3, "ea")
+    S = SpinOrbitalADC(s.eps, o, 3, B=B)
+    assert np.abs(S.t1_3[0::2, 1::2]).max() == 0.0
+    assert np.abs(T.t1_3).max() > 1e-4
+    assert np.abs(T.t1_3 - S.t1_3[0::2, 0::2]).max() < 1e-14
+    assert np.abs(T.t1_3 - S.t1_3[1::2, 1::2]).max() < 1e-14
+
+
+@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("kind", ["ea", "ip"])
+def test_transition_moments_match_spin_orbital(order, kind):
+    """X = T E Y~ for every S-normalised vector: the spatial T (through order n)
+    acting on a doublet vector equals the spin-orbital T on its embedding,
+    for the alpha (EA) / beta (IP) orbital rows the embedding addresses."""
+    o, v = 3, 4
+    s = make_system(o, v, 16, seed=6)
+    B = 2.0 * s.B
+    T = SpinAdaptedADC(s.eps, o, B, order, kind)
+    S = SpinOrbitalADC(s.eps, o, order, B=B)
+    E = embedding(o, v, kind)
+    T1, T2 = S.ea_transition() if kind == "ea" else S.ip_transition()
+    _, two = S.basis_labels(kind)
+    I = np.array(two)
+    Tso = np.concatenate([T1, T2[:, I[:, 0], I[:, 1], I[:, 2]]], axis=1)
+    Y = np.random.default_rng(0).standard_normal((5, T.dim))
+    P = spectroscopic_factors(T, Y)
+    for r in range(5):
+        u = E @ Y[r]
+        u /= np.linalg.norm(u)
+        assert abs(P[r] - 2.0 * np.sum((Tso @ u) ** 2)) < 1e-12
+
+
 @pytest.mark.parametrize("kind", ["ea", "ip"])
 def test_df_complete_auxiliary_set(kind):
     o, v = 2, 4

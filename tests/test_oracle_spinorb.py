@@ -41,6 +41,10 @@ def test_amplitudes(pair):
     assert np.abs(F.t2_tensor(2) - S.t2_2).max() < 1e-13
     assert np.abs(F.t1_tensor(2) - S.t1_2).max() < 1e-13
     assert abs(F.energy(2) - S.mp2_energy()) < 1e-13
+    # third-order singles (Eq. t_singles at k = 3): projection of the full
+    # third-order effective Hamiltonian against the closed form with triples
+    assert np.abs(F.t1_tensor(3)).max() > 1e-4
+    assert np.abs(F.t1_tensor(3) - S.t1_3).max() < 1e-13
 
 
 @pytest.mark.parametrize("kind", ["ea", "ip"])
@@ -50,7 +54,26 @@ def test_transition_second_order(pair, kind):
     Tf = T[0] + T[1] + T[2]
     S = SpinOrbitalADC(s.eps, s.nocc, 3, B=B)
     one, two = S.basis_labels(kind)
-    T1, T2 = S.ea_transition() if kind == "ea" else S.ip_transition()
+    T1, T2 = S.ea_transition(2) if kind == "ea" else S.ip_transition(2)
     I = np.array(two)
     Ts = np.concatenate([T1, T2[:, I[:, 0], I[:, 1], I[:, 2]]], axis=1)
     assert np.abs(Tf - Ts).max() < 1e-13
+
+
+@pytest.mark.parametrize("kind", ["ea", "ip"])
+def test_transition_third_order(pair, kind):
+    """T through k + l <= 3 (ADC(3)): the third-order piece alone and the sum."""
+    F, s, B = pair
+    T, bas = F.adc_transition(kind, 3)
+    S = SpinOrbitalADC(s.eps, s.nocc, 3, B=B)
+    one, two = S.basis_labels(kind)
+    I = np.array(two)
+
+    def flat(T1, T2):
+        return np.concatenate([T1, T2[:, I[:, 0], I[:, 1], I[:, 2]]], axis=1)
+
+    tr = S.ea_transition if kind == "ea" else S.ip_transition
+    T3 = flat(*tr(3)) - flat(*tr(2))
+    assert np.abs(T[3]).max() > 1e-4
+    assert np.abs(T[3] - T3).max() < 1e-13
+    assert np.abs(T[0] + T[1] + T[2] + T[3] - flat(*tr())).max() < 1e-13
