@@ -145,7 +145,9 @@ int adc_sigma(adc_handle* h, const double* X, double* S, int nvec, int on_device
 
 /*
  * Lowest nroots roots by multi-root Davidson in the S inner product (Eq. eig,
- * Sec. III A step 4), then spectroscopic factors (Eq. spec_factors, Appendix).
+ * Sec. III A step 4), then spectroscopic factors (Eq. spec_factors, Appendix)
+ * from the transition moments T through order n (Eqs. T_ea, T_ip, k + l <= n;
+ * for ADC(3) this includes the third-order singles t1(3)).
  *   tol       convergence threshold on the eigenvalue change (Eh)
  *   guess     NULL or host [nguess = nroots][dim] initial vectors
  *   energies  host [nroots], ascending
@@ -177,7 +179,9 @@ int adc_davidson_batch(adc_handle* const* h, int nmol, int nroots, double tol, d
 /*
  * Copy an intermediate to host memory.  name is one of "M11" [n1][n1],
  * "t2" [o][o][v][v] (first-order doubles), "t2_2" (second-order doubles),
- * "t1_2" [o][v], "diag" [dim], or "X" [nroots][nmo]: the spectroscopic
+ * "t1_2" [o][v], "t1_3" [o][v] (third-order singles, Eq. t_singles at k = 3;
+ * ADC(3) only, computed on the first request or the first spectroscopic
+ * factors), "diag" [dim], or "X" [nroots][nmo]: the spectroscopic
  * amplitudes X_{p,mu} = sum_nu T_{p,nu} (S Y~)_nu of the last adc_davidson
  * that computed spectroscopic factors (Eq. spec_amp with the Appendix
  * renormalisation, P_mu = 2 sum_p X_{p,mu}^2; occupied orbitals first).

@@ -37,6 +37,7 @@ struct adc_handle {
     double *eps = nullptr, *Boo = nullptr, *Bov = nullptr, *Bvv = nullptr;
     double *ovov = nullptr, *oovv = nullptr, *oooo = nullptr, *ooov = nullptr;
     double *t = nullptr, *tau = nullptr, *t_2 = nullptr, *t1_2 = nullptr, *M11 = nullptr, *diag = nullptr;
+    double* t1_3 = nullptr;  // third-order singles (ADC(3) transition moments only), made on first use
     LadderTC* tc = nullptr;  // tensor-core ladder state (BF16x3 operands of B^Q_vv)
     // tensor-core ladder arithmetic: Davidson sigma, the setup ladder of t, and
     // the final refinement of converged roots
@@ -391,6 +392,127 @@ static void setup_m11_ip(adc_handle* h) {
         einsum(c, "jcid,cd->ij", -1.0, tn(h->ovov, {o, v, o, v}), tn(Z, {v, v}), 1.0, M, {o, o});
     }
     axpby(c, o * o, 0.0, M, -1.0, M);  // apply -M_-
+}
+
+// --------------------------------------------------------------------------
+// Third-order singles t_i^a(3) (Eq. t_singles at k = 3), spin-integrated.
+// They enter only the ADC(3) transition moments, so they are made on first
+// use, in the setup's contraction arithmetic.  With tau = 2t - t(ab swap):
+//   D t(3) = A1 + A2 + (2 E1 + E2 + 4 E3 + 2 E4)/4 - (2 F1 + 4 F2 + F3 + 2 F4)/4,
+//   t(3)  += 1/2 sum tau_ij^ab t_j^b(2)
+// A1, A2: the CC-like singles terms of t1(2) and t2(2); E1..E4 and F1..F4:
+// the connected-triples term 1/4 t_jk^bc W_ijk^abc summed permutation by
+// permutation (particle and hole halves).  The costliest pieces are the ring
+// products R1, R2 (o^3 v^3) and E2 (4 naux o^3 v^2, auxiliary index chunked).
+// --------------------------------------------------------------------------
+static void make_t1_third_order(adc_handle* h) {
+    if (h->t1_3 || h->order < 3) return;
+    Ctx& c = h->ctx;
+    const int saved = c.gemm_mode;
+    c.gemm_mode = h->cmode_setup;
+    const long long o = h->o, v = h->v, Q = h->naux;
+    const long long o2v2 = o * o * v * v;
+    double* out = h->dmalloc(o * v);
+    {
+        Scope sc(c.arena);
+        const double *t = h->t, *tau = h->tau, *t1 = h->t1_2, *t2 = h->t_2;
+        const T T4 = tn(t, {o, o, v, v}), U4 = tn(tau, {o, o, v, v});
+        const T Boo = tn(h->Boo, {Q, o, o}), Bvv = tn(h->Bvv, {Q, v, v});
+        double* num = c.arena.dalloc(o * v);
+        // A1 = sum [2 (ia|jb) - (ij|ab)] t_j^b(2)
+        einsum(c, "iajb,jb->ia", 2.0, tn(h->ovov, {o, v, o, v}), tn(t1, {o, v}), 0.0, num, {o, v});
+        einsum(c, "jiab,jb->ia", -1.0, tn(h->oovv, {o, o, v, v}), tn(t1, {o, v}), 1.0, num, {o, v});
+        Shape s4{4, {o, o, v, v}};
+        int swp[4] = {0, 1, 3, 2};
+        {
+            // A2: the t1(2) expression with tau(2) = 2 t2(2) - t2(2)(ab swap)
+            Scope s2(c.arena);
+            double* tau2 = c.arena.dalloc(o2v2);
+            axpby(c, o2v2, 2.0, t2, 0.0, tau2);
+            permute(c, t2, s4, swp, tau2, -1.0, 1.0);
+            double* G = c.arena.dalloc(Q * o * v);
+            einsum(c, "Qkc,ikdc->Qid", 1.0, tn(h->Bov, {Q, o, v}), tn(tau2, {o, o, v, v}), 0.0, G, {Q, o, v});
+            einsum(c, "Qid,Qad->ia", 1.0, tn(G, {Q, o, v}), Bvv, 1.0, num, {o, v});
+            einsum(c, "kilc,klac->ia", -1.0, tn(h->ooov, {o, o, o, v}), tn(tau2, {o, o, v, v}), 1.0, num, {o, v});
+        }
+        {
+            // E1/2 and -F1/2 through G_jb^Q = sum_kc (kc|Q) tau_jk^bc
+            Scope s2(c.arena);
+            double* G = c.arena.dalloc(Q * o * v);
+            einsum(c, "Qkc,jkbc->Qjb", 1.0, tn(h->Bov, {Q, o, v}), U4, 0.0, G, {Q, o, v});
+            double* Y = c.arena.dalloc(o * v);
+            einsum(c, "Qjb,Qbd->jd", 2.0, tn(G, {Q, o, v}), Bvv, 0.0, Y, {o, v});
+            einsum(c, "ijad,jd->ia", 0.5, U4, tn(Y, {o, v}), 1.0, num, {o, v});
+            einsum(c, "Qlj,Qjb->lb", 2.0, Boo, tn(G, {Q, o, v}), 0.0, Y, {o, v});
+            einsum(c, "ilab,lb->ia", -0.5, U4, tn(Y, {o, v}), 1.0, num, {o, v});
+        }
+        {
+            // E2/4 = -sum t_jk^ad V_jkdi, V_jkdi = sum_Q sum_b B^Q_db sum_c tau_jk^cb B^Q_ic
+            Scope s2(c.arena);
+            double* tauS = c.arena.dalloc(o2v2);  // tau_jk^cb stored [j][k][b][c]
+            permute(c, tau, s4, swp, tauS, 1.0, 0.0);
+            double* V = c.arena.dalloc(v * o * o * o);  // [d][j][k][i]
+            const long long per = v * o * o * o;
+            const long long qc = std::max(1LL, std::min(Q, (1LL << 27) / std::max(per, 1LL)));
+            double* W = c.arena.dalloc(qc * per);  // [Q][b][j][k][i]
+            for (long long q0 = 0; q0 < Q; q0 += qc) {
+                const long long nq = std::min(qc, Q - q0);
+                einsum(c, "jkbc,Qic->Qbjki", 1.0, tn(tauS, {o, o, v, v}), tn(h->Bov + q0 * o * v, {nq, o, v}), 0.0, W,
+                       {nq, v, o, o, o});
+                einsum(c, "Qdb,Qbjki->djki", 1.0, tn(h->Bvv + q0 * v * v, {nq, v, v}), tn(W, {nq, v, o, o, o}),
+                       q0 == 0 ? 0.0 : 1.0, V, {v, o, o, o});
+            }
+            einsum(c, "jkad,djki->ia", -1.0, T4, tn(V, {v, o, o, o}), 1.0, num, {o, v});
+        }
+        {
+            // E3 (+1) and F2 (-1) through the ring products
+            //   R1_ik^dc = sum tau_ij^db tau_jk^bc,  R2_ik^cd = -sum (tau_ij^db t_jk^bc + tau_ij^bd t_jk^cb)
+            Scope s2(c.arena);
+            double* R = c.arena.dalloc(o2v2);
+            double* H = c.arena.dalloc(Q * std::max(std::max(o * v, v * v), o * o));
+            einsum(c, "ijdb,jkbc->ikdc", 1.0, U4, U4, 0.0, R, {o, o, v, v});
+            einsum(c, "Qkc,ikdc->Qid", 1.0, tn(h->Bov, {Q, o, v}), tn(R, {o, o, v, v}), 0.0, H, {Q, o, v});
+            einsum(c, "Qid,Qad->ia", 1.0, tn(H, {Q, o, v}), Bvv, 1.0, num, {o, v});   // E3: (ad|kc) R1
+            einsum(c, "Qla,Qli->ia", -1.0, tn(H, {Q, o, v}), Boo, 1.0, num, {o, v});  // F2: (li|kc) R1
+            einsum(c, "ijdb,jkbc->ikcd", -1.0, U4, T4, 0.0, R, {o, o, v, v});
+            einsum(c, "ijbd,jkcb->ikcd", -1.0, U4, T4, 1.0, R, {o, o, v, v});
+            einsum(c, "Qcd,ikcd->Qik", 1.0, Bvv, tn(R, {o, o, v, v}), 0.0, H, {Q, o, o});
+            einsum(c, "Qik,Qka->ia", 1.0, tn(H, {Q, o, o}), tn(h->Bov, {Q, o, v}), 1.0, num, {o, v});  // E3: (ka|cd) R2
+            einsum(c, "Qlk,lkca->Qca", 1.0, Boo, tn(R, {o, o, v, v}), 0.0, H, {Q, v, v});
+            einsum(c, "Qca,Qic->ia", -1.0, tn(H, {Q, v, v}), tn(h->Bov, {Q, o, v}), 1.0, num, {o, v});  // F2: (lk|ic) R2
+        }
+        {
+            // E4/2 with rho_cd = 2 sum t_jk^cb tau_jk^db; -F4/2 with rho'_kl = 2 sum t_jk^bc tau_jl^bc
+            Scope s2(c.arena);
+            double* rho = c.arena.dalloc(v * v);
+            double* r = c.arena.dalloc(Q);
+            double* L = c.arena.dalloc(Q * o * v);
+            einsum(c, "jkcb,jkdb->cd", 2.0, T4, U4, 0.0, rho, {v, v});
+            einsum(c, "Qcd,cd->Q", 1.0, Bvv, tn(rho, {v, v}), 0.0, r, {Q});
+            einsum(c, "Qia,Q->ia", 1.0, tn(h->Bov, {Q, o, v}), tn(r, {Q}), 1.0, num, {o, v});
+            einsum(c, "Qic,cd->Qid", 1.0, tn(h->Bov, {Q, o, v}), tn(rho, {v, v}), 0.0, L, {Q, o, v});
+            einsum(c, "Qid,Qad->ia", -0.5, tn(L, {Q, o, v}), Bvv, 1.0, num, {o, v});
+            double* rh = c.arena.dalloc(o * o);
+            einsum(c, "jkbc,jlbc->kl", 2.0, T4, U4, 0.0, rh, {o, o});
+            einsum(c, "lkia,kl->ia", -1.0, tn(h->ooov, {o, o, o, v}), tn(rh, {o, o}), 1.0, num, {o, v});
+            einsum(c, "lika,kl->ia", 0.5, tn(h->ooov, {o, o, o, v}), tn(rh, {o, o}), 1.0, num, {o, v});
+        }
+        {
+            // -F3/4 = -sum (lj|ka) X_jkil, X_jkil = sum t_jk^bc (tau - t)_il^bc - t_kj^bc t_il^bc
+            Scope s2(c.arena);
+            double* X = c.arena.dalloc(o * o * o * o);
+            einsum(c, "jkbc,ilbc->jkil", 1.0, T4, U4, 0.0, X, {o, o, o, o});
+            einsum(c, "jkbc,ilbc->jkil", -1.0, T4, T4, 1.0, X, {o, o, o, o});
+            einsum(c, "kjbc,ilbc->jkil", -1.0, T4, T4, 1.0, X, {o, o, o, o});
+            einsum(c, "ljka,jkil->ia", -1.0, tn(h->ooov, {o, o, o, v}), tn(X, {o, o, o, o}), 1.0, num, {o, v});
+        }
+        k_div_D1<<<grid_for(o * v), 256, 0, c.stream>>>((int)o, (int)v, h->eps, num);
+        launch_check(c);
+        ADC_CUDA(cudaMemcpyAsync(out, num, o * v * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+        einsum(c, "ijab,jb->ia", 0.5, U4, tn(t1, {o, v}), 1.0, out, {o, v});
+    }
+    c.gemm_mode = saved;
+    h->t1_3 = out;
 }
 
 static void setup(adc_handle* h, const double* eps_in, const double* B_in, int on_device) {
@@ -1031,34 +1153,70 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
             t1 = t1tmp;
         }
         // X rows laid out [r][p] with p over all nmo orbitals (occupied first)
+        // ADC(3): T through third order (k + l <= 3): the density cross terms with
+        // t2(2), t1(3) + 1/2 tau t1(2) in the one-particle rows of the other space,
+        // and t2(2) beside t2(1) in the two-particle columns
+        const bool third = h->order >= 3;
+        double* t1x = nullptr;  // t1(2) [+ t1(3) + 1/2 sum tau t1(2)], [o][v]
+        if (third) {
+            make_t1_third_order(h);
+            t1x = c.arena.dalloc(o * v);
+            axpby(c, o * v, 1.0, h->t1_2, 0.0, t1x);
+            axpby(c, o * v, 1.0, h->t1_3, 1.0, t1x);
+            const char* spec = h->kind == ADC_EA ? "klbc,lc->kb" : "jlcd,ld->jc";
+            einsum(c, spec, 0.5, tn(h->tau, {o, o, v, v}), tn(h->t1_2, {o, v}), 1.0, t1x, {o, v});
+            t1 = t1x;
+        }
         if (h->kind == ADC_EA) {
-            // T_{c,b} = d_cb - sum t_kl^cd t_kl^bd + 1/2 sum t_kl^cd t_kl^db
+            // T_{c,b} = d_cb + B(t, t)_cb [+ B(t, t2) + B(t2, t)],
+            // B(x, y)_cb = -sum x_kl^cd y_kl^bd + 1/2 sum x_kl^cd y_kl^db
             einsum(c, "klcd,klbd->cb", -1.0, tn(t, {o, o, v, v}), tn(t, {o, o, v, v}), 0.0, Tpp, {v, v});
             einsum(c, "klcd,kldb->cb", 0.5, tn(t, {o, o, v, v}), tn(t, {o, o, v, v}), 1.0, Tpp, {v, v});
+            if (third) {
+                const double* t2 = h->t_2;
+                einsum(c, "klcd,klbd->cb", -1.0, tn(t, {o, o, v, v}), tn(t2, {o, o, v, v}), 1.0, Tpp, {v, v});
+                einsum(c, "klcd,kldb->cb", 0.5, tn(t, {o, o, v, v}), tn(t2, {o, o, v, v}), 1.0, Tpp, {v, v});
+                einsum(c, "klcd,klbd->cb", -1.0, tn(t2, {o, o, v, v}), tn(t, {o, o, v, v}), 1.0, Tpp, {v, v});
+                einsum(c, "klcd,kldb->cb", 0.5, tn(t2, {o, o, v, v}), tn(t, {o, o, v, v}), 1.0, Tpp, {v, v});
+            }
             double* xv = c.arena.dalloc((size_t)nroots * v);
             ADC_CUDA(cudaMemcpyAsync(xv, s1, (size_t)nroots * v * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
             einsum(c, "rb,cb->rc", 1.0, tn(s1, {nroots, v}), tn(Tpp, {v, v}), 1.0, xv, {nroots, v});
             k_gather<<<grid_for(nroots * v), 256, 0, c.stream>>>(nroots, v, xv, v, 0, Xp, nmo, o, 0.0);
             launch_check(c);
-            // occupied: T_{k,b} = -t_k^b(2) ; T_{k,jcd} = -t_kj^dc
+            // occupied: T_{k,b} = -t_k^b(2) [- t_k^b(3) - 1/2 sum tau_kl^bc t_l^c(2)] ;
+            // T_{k,jcd} = -t_kj^dc [- t2_kj^dc]
             double* xo = c.arena.dalloc((size_t)nroots * o);
             einsum(c, "rb,kb->rk", -1.0, tn(s1, {nroots, v}), tn(t1, {o, v}), 0.0, xo, {nroots, o});
             einsum(c, "rjcd,kjdc->rk", -1.0, tn(s2, {nroots, o, v, v}), tn(t, {o, o, v, v}), 1.0, xo, {nroots, o});
+            if (third)
+                einsum(c, "rjcd,kjdc->rk", -1.0, tn(s2, {nroots, o, v, v}), tn(h->t_2, {o, o, v, v}), 1.0, xo, {nroots, o});
             k_gather<<<grid_for(nroots * o), 256, 0, c.stream>>>(nroots, o, xo, o, 0, Xp, nmo, 0, 0.0);
             launch_check(c);
         } else {
-            // T_{k,j} = d_kj - sum t_kl^cd t_jl^cd + 1/2 sum t_kl^cd t_jl^dc
+            // T_{k,j} = d_kj + B'(t, t)_kj [+ B'(t, t2) + B'(t2, t)],
+            // B'(x, y)_kj = -sum x_kl^cd y_jl^cd + 1/2 sum x_kl^cd y_jl^dc
             einsum(c, "klcd,jlcd->kj", -1.0, tn(t, {o, o, v, v}), tn(t, {o, o, v, v}), 0.0, Tpp, {o, o});
             einsum(c, "klcd,jldc->kj", 0.5, tn(t, {o, o, v, v}), tn(t, {o, o, v, v}), 1.0, Tpp, {o, o});
+            if (third) {
+                const double* t2 = h->t_2;
+                einsum(c, "klcd,jlcd->kj", -1.0, tn(t, {o, o, v, v}), tn(t2, {o, o, v, v}), 1.0, Tpp, {o, o});
+                einsum(c, "klcd,jldc->kj", 0.5, tn(t, {o, o, v, v}), tn(t2, {o, o, v, v}), 1.0, Tpp, {o, o});
+                einsum(c, "klcd,jlcd->kj", -1.0, tn(t2, {o, o, v, v}), tn(t, {o, o, v, v}), 1.0, Tpp, {o, o});
+                einsum(c, "klcd,jldc->kj", 0.5, tn(t2, {o, o, v, v}), tn(t, {o, o, v, v}), 1.0, Tpp, {o, o});
+            }
             double* xo = c.arena.dalloc((size_t)nroots * o);
             ADC_CUDA(cudaMemcpyAsync(xo, s1, (size_t)nroots * o * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
             einsum(c, "rj,kj->rk", 1.0, tn(s1, {nroots, o}), tn(Tpp, {o, o}), 1.0, xo, {nroots, o});
             k_gather<<<grid_for(nroots * o), 256, 0, c.stream>>>(nroots, o, xo, o, 0, Xp, nmo, 0, 0.0);
             launch_check(c);
-            // virtual: T_{c,j} = t_j^c(2) ; T_{c,ija} = -t_ij^ac
+            // virtual: T_{c,j} = t_j^c(2) [+ t_j^c(3) + 1/2 sum tau_jl^cd t_l^d(2)] ;
+            // T_{c,ija} = -t_ij^ac [- t2_ij^ac]
             double* xv = c.arena.dalloc((size_t)nroots * v);
             einsum(c, "rj,jc->rc", 1.0, tn(s1, {nroots, o}), tn(t1, {o, v}), 0.0, xv, {nroots, v});
             einsum(c, "rija,ijac->rc", -1.0, tn(s2, {nroots, o, o, v}), tn(t, {o, o, v, v}), 1.0, xv, {nroots, v});
+            if (third)
+                einsum(c, "rija,ijac->rc", -1.0, tn(s2, {nroots, o, o, v}), tn(h->t_2, {o, o, v, v}), 1.0, xv, {nroots, v});
             k_gather<<<grid_for(nroots * v), 256, 0, c.stream>>>(nroots, v, xv, v, 0, Xp, nmo, o, 0.0);
             launch_check(c);
         }
@@ -1410,6 +1568,10 @@ int adc_get_tensor(adc_handle* h, const char* name, double* out, long long n) {
             cnt = o * o * v * v;
         } else if (s == "t1_2") {
             src = h->t1_2;
+            cnt = o * v;
+        } else if (s == "t1_3") {
+            make_t1_third_order(h);
+            src = h->t1_3;
             cnt = o * v;
         } else if (s == "diag") {
             src = h->diag;

@@ -62,8 +62,33 @@ def test_setup_intermediates(lib, kind):
     assert np.abs(gpu.get("t2", (o, o, v, v)) - ref.t).max() < 1e-13
     assert np.abs(gpu.get("t2_2", (o, o, v, v)) - ref.t_2).max() < 1e-13
     assert np.abs(gpu.get("t1_2", (o, v)) - ref.t1_2).max() < 1e-13
+    assert np.abs(gpu.get("t1_3", (o, v)) - ref.t1_3).max() < 1e-13
     assert np.abs(gpu.get("diag", (ref.dim,)) - ref.diagonal()).max() < 1e-12
     gpu.close()
+
+
+@pytest.fixture(scope="module")
+def chunked_case():
+    o, v, naux = 11, 97, 1500
+    s = _mk(o, v, naux, 5)
+    return s, SpinAdaptedADC(s.eps, o, s.B, 3, "ip")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16x3"])
+def test_third_order_singles_auxiliary_chunks(lib, chunked_case, precision):
+    """t_i^a(3) with the auxiliary index split into two chunks (1500 = 1039 + 461
+    at nocc 11, nvir 97) against the oracle; the mixed path forms it in the
+    setup's FP32-accurate contractions (relative 1e-6 of the largest element)."""
+    from paper_2012_06714_gb300 import ADC
+
+    s, ref = chunked_case
+    o, v = 11, 97
+    gpu = ADC(s.eps, s.B, o, order=3, kind="ip", precision=precision)
+    got = gpu.get("t1_3", (o, v))
+    gpu.close()
+    scale = np.abs(ref.t1_3).max()
+    assert scale > 1e-4
+    assert np.abs(got - ref.t1_3).max() <= (1e-12 if precision == "fp64" else 1e-6) * scale
 
 
 @pytest.mark.parametrize("kind", ["ea", "ip"])
