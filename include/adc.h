@@ -131,6 +131,16 @@ int adc_set_options(adc_handle* h, const adc_options* opt);
 /* Length of the spin-adapted vector (see layout above). */
 int adc_dim(const adc_handle* h, long long* dim);
 
+/*
+ * Moller-Plesset correlation energy of the reference through order n
+ * (Sec. III A step 2), from the setup's amplitudes:
+ *   e[0] = E(2) = sum (ia|jb) (2 t_ij^ab - t_ij^ba)               (t = t2(1))
+ *   e[1] = E(3) = sum (ia|jb) (2 t2_ij^ab - t2_ij^ba)  (ADC(3) only; t2 = t2(2))
+ * E(1) = 0 for the normal-ordered perturbation.  n_out = number of doubles e
+ * holds; min(n_out, order - 1) values are written.  Errors: ADC_ERR_ARG.
+ */
+int adc_mp_energy(const adc_handle* h, double* e, int n_out);
+
 /* Issue subsequent work on this CUDA stream (cudaStream_t passed as void*). */
 int adc_set_stream(adc_handle* h, void* stream);
 

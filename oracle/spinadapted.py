@@ -164,6 +164,14 @@ class SpinAdaptedADC:
         num = A1 + A2 + 0.25 * (2.0 * E1 + E2 + 4.0 * E3 + 2.0 * E4) - 0.25 * (2.0 * F1 + 4.0 * F2 + F3 + 2.0 * F4)
         return num / self.D1 + 0.5 * e("ijab,jb->ia", tau, t1)
 
+    def mp_energies(self):
+        """MP correlation energy through order n (Sec. III A step 2), spin-integrated:
+        E(2) = sum (ia|jb)(2 t_ij^ab - t_ij^ba), E(3) the same with t2(2)."""
+        out = []
+        for t in (self.t, getattr(self, "t_2", None))[: self.order - 1]:
+            out.append(float(np.einsum("iajb,ijab->", self.ovov, 2.0 * t - t.transpose(0, 1, 3, 2))))
+        return out
+
     # ---- 1p-1p / 1h-1h block (Table 1 second row; precomputed, Sec. III A) --
     def _m11(self):
         return self._m11_ea() if self.kind == "ea" else -self._m11_ip()

@@ -125,6 +125,10 @@ class SpinOrbitalADC:
     def mp2_energy(self):
         return 0.25 * float(np.einsum("ijab,ijab->", self.blk("oovv"), self.t2_1))
 
+    def mp3_energy(self):
+        """Third-order energy <Phi|H~(3)|Phi> = 1/4 sum <ij||ab> t_ij^ab(2) (Sec. III A step 2)."""
+        return 0.25 * float(np.einsum("ijab,ijab->", self.blk("oovv"), self.t2_2))
+
     # ---- EA blocks ---------------------------------------------------------
     def ea_m11(self):
         """1p-1p block M_ab through order n (one-body vv part of the effective H)."""

@@ -30,6 +30,7 @@ EXPORTED = [
     "adc_sigma",
     "adc_davidson",
     "adc_get_tensor",
+    "adc_mp_energy",
     "adc_kernel_timing",
     "adc_ladder_noalloc",
     "adc_last_error",
@@ -83,6 +84,7 @@ def load_library():
     lib.adc_sigma.argtypes = [P, P, P, I, I]
     lib.adc_davidson.argtypes = [P, I, D, P, P, P, P, P]
     lib.adc_get_tensor.argtypes = [P, ctypes.c_char_p, P, LL]
+    lib.adc_mp_energy.argtypes = [P, P, ctypes.c_int]
     lib.adc_kernel_timing.argtypes = [P, I, P]
     lib.adc_ladder_noalloc.argtypes = [P, P, P, LL]
     lib.adc_spectrum.argtypes = [P, P, I, D, P, I, P]
@@ -226,6 +228,12 @@ class ADC:
         else:
             w = np.ascontiguousarray(weights, dtype=np.float32)
             self._check(self._lib.adc_set_mlp(self._h, w.ctypes.data))
+
+    def mp_energy(self):
+        """MP correlation energies (E(2),) for ADC(2) or (E(2), E(3)) for ADC(3), Eh."""
+        e = np.zeros(2)
+        self._check(self._lib.adc_mp_energy(self._h, e.ctypes.data, 2))
+        return tuple(float(x) for x in e[: self.order - 1])
 
     def get(self, name, shape):
         out = np.zeros(int(np.prod(shape)))

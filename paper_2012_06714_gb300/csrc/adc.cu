@@ -38,6 +38,7 @@ struct adc_handle {
     double *ovov = nullptr, *oovv = nullptr, *oooo = nullptr, *ooov = nullptr;
     double *t = nullptr, *tau = nullptr, *t_2 = nullptr, *t1_2 = nullptr, *M11 = nullptr, *diag = nullptr;
     double* t1_3 = nullptr;  // third-order singles (ADC(3) transition moments only), made on first use
+    double emp[2] = {0.0, 0.0};  // MP correlation energy E(2), E(3) (Sec. III A step 2)
     LadderTC* tc = nullptr;  // tensor-core ladder state (BF16x3 operands of B^Q_vv)
     // tensor-core ladder arithmetic: Davidson sigma, the setup ladder of t, and
     // the final refinement of converged roots
@@ -595,6 +596,33 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
         einsum(c, "kilc,klac->ia", -1.0, tn(h->ooov, {o, o, o, v}), tn(h->tau, {o, o, v, v}), 1.0, h->t1_2, {o, v});
         k_div_D1<<<grid_for(o * v), 256, 0, c.stream>>>((int)o, (int)v, h->eps, h->t1_2);
         launch_check(c);
+    }
+    {
+        // MPn correlation energy: E(k+1) = sum (ia|jb) (2 t_ij^ab - t_ij^ba), t = t2(k);
+        // o^2 v^2 work, always in FP64
+        Scope sc(c.arena);
+        const int saved = c.gemm_mode;
+        c.gemm_mode = 0;
+        double* part = c.arena.dalloc(o);
+        std::vector<double> hp(o);
+        for (int k = 0; k < (h->order >= 3 ? 2 : 1); ++k) {
+            const double* tk = h->tau;
+            if (k == 1) {
+                double* tau2 = c.arena.dalloc(o * o * v * v);
+                axpby(c, o * o * v * v, 2.0, h->t_2, 0.0, tau2);
+                Shape s4{4, {o, o, v, v}};
+                int swp[4] = {0, 1, 3, 2};
+                permute(c, h->t_2, s4, swp, tau2, -1.0, 1.0);
+                tk = tau2;
+            }
+            einsum(c, "iajb,ijab->i", 1.0, tn(h->ovov, {o, v, o, v}), tn(tk, {o, o, v, v}), 0.0, part, {o});
+            ADC_CUDA(cudaMemcpyAsync(hp.data(), part, o * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+            ADC_CUDA(cudaStreamSynchronize(c.stream));
+            double e = 0.0;
+            for (double x : hp) e += x;
+            h->emp[k] = e;
+        }
+        c.gemm_mode = saved;
     }
     const long long n1 = h->n1();
     h->M11 = h->dmalloc(n1 * n1);
@@ -1483,6 +1511,13 @@ int adc_setup_batch(int nmol, const double* const* eps, const double* const* Bq,
 int adc_dim(const adc_handle* h, long long* dim) {
     if (!h || !dim) return ADC_ERR_ARG;
     *dim = h->dim();
+    return ADC_OK;
+}
+
+int adc_mp_energy(const adc_handle* h, double* e, int n_out) {
+    if (!h || !e || n_out < 1) return ADC_ERR_ARG;
+    const int n = std::min(n_out, h->order - 1);
+    for (int k = 0; k < n; ++k) e[k] = h->emp[k];
     return ADC_OK;
 }
 

@@ -63,6 +63,8 @@ def test_setup_intermediates(lib, kind):
     assert np.abs(gpu.get("t2_2", (o, o, v, v)) - ref.t_2).max() < 1e-13
     assert np.abs(gpu.get("t1_2", (o, v)) - ref.t1_2).max() < 1e-13
     assert np.abs(gpu.get("t1_3", (o, v)) - ref.t1_3).max() < 1e-13
+    e_ref = ref.mp_energies()
+    assert np.abs(np.array(gpu.mp_energy()) - e_ref).max() < 1e-12 * abs(e_ref[0])
     assert np.abs(gpu.get("diag", (ref.dim,)) - ref.diagonal()).max() < 1e-12
     gpu.close()
 

@@ -56,6 +56,17 @@ def test_third_order_singles_match_spin_orbital(o, v, seed):
     assert np.abs(T.t1_3 - S.t1_3[1::2, 1::2]).max() < 1e-14
 
 
+def test_mp_energies_match_spin_orbital():
+    s = make_system(3, 5, 16, seed=2)
+    B = 2.0 * s.B
+    S = SpinOrbitalADC(s.eps, 3, 3, B=B)
+    e2 = SpinAdaptedADC(s.eps, 3, B, 2, "ea").mp_energies()
+    e3 = SpinAdaptedADC(s.eps, 3, B, 3, "ip").mp_energies()
+    assert len(e2) == 1 and len(e3) == 2
+    assert abs(e2[0] - S.mp2_energy()) < 1e-14 and abs(e3[0] - e2[0]) < 1e-15
+    assert abs(e3[1] - S.mp3_energy()) < 1e-14
+
+
 @pytest.mark.parametrize("order", [2, 3])
 @pytest.mark.parametrize("kind", ["ea", "ip"])
 def test_transition_moments_match_spin_orbital(order, kind):

@@ -41,6 +41,7 @@ def test_amplitudes(pair):
     assert np.abs(F.t2_tensor(2) - S.t2_2).max() < 1e-13
     assert np.abs(F.t1_tensor(2) - S.t1_2).max() < 1e-13
     assert abs(F.energy(2) - S.mp2_energy()) < 1e-13
+    assert abs(F.energy(3) - S.mp3_energy()) < 1e-13
     # third-order singles (Eq. t_singles at k = 3): projection of the full
     # third-order effective Hamiltonian against the closed form with triples
     assert np.abs(F.t1_tensor(3)).max() > 1e-4
