@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libadc.so")
-SOURCES = ["common.cu", "adc.cu", "ladder_tc.cu", "ladder_static.cu", "mlp.cu"]
+SOURCES = ["common.cu", "adc.cu", "ladder_tc.cu", "ladder_static.cu", "mlp.cu", "subspace.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -26,6 +26,7 @@
 #include "common.cuh"
 #include "ladder_tc.cuh"
 #include "mlp.cuh"
+#include "subspace.cuh"
 
 using namespace adc;
 
@@ -668,10 +669,10 @@ static void sigma_ea(adc_handle* h, const double* Xin, double* Sout, long long n
     launch_check(c);
     // 1p row: M_ab Y_b
     einsum(c, "nb,ab->na", 1.0, tn(y1, {n, v}), tn(h->M11, {v, v}), 0.0, s1, {n, v});
-    // coupling row, first order: sum (ad|jc) Y~_jcd
+    // coupling row, first order: sum (ad|jc) Y~_jcd.  W^Q_d collects every coupling-row
+    // term of the form sum_Qd W^Q_d (Q|da); it is contracted with B^Q_vv once, below.
     double* Wq = c.arena.dalloc(n * Q * v);
     einsum(c, "Qjc,njcd->nQd", 1.0, tc(h->Bov, {Q, o, v}), tn(Yt, {n, o, v, v}), 0.0, Wq, {n, Q, v});
-    einsum(c, "nQd,Qda->na", 1.0, tn(Wq, {n, Q, v}), tc(h->Bvv, {Q, v, v}), 1.0, s1, {n, v});
     // 2p1h column, first order: (cb|ia) Y_c
     double* hq = c.arena.dalloc(n * Q * v);
     einsum(c, "nc,Qcb->nQb", 1.0, tn(y1, {n, v}), tc(h->Bvv, {Q, v, v}), 0.0, hq, {n, Q, v});
@@ -685,20 +686,18 @@ static void sigma_ea(adc_handle* h, const double* Xin, double* Sout, long long n
         //  sum (al|jm) t_lm^dc Y~_jcd
         double* Z = c.arena.dalloc(n * o * o * o);
         einsum(c, "lmdc,njcd->nlmj", 1.0, tc(t, {o, o, v, v}), tn(Yt, {n, o, v, v}), 0.0, Z, {n, o, o, o});
+        // P^Q_l collects the terms of the form sum_Ql P^Q_l (Q|la) (contracted once, below)
         double* P = c.arena.dalloc(n * Q * o);
         einsum(c, "Qjm,nlmj->nQl", 1.0, tc(h->Boo, {Q, o, o}), tn(Z, {n, o, o, o}), 0.0, P, {n, Q, o});
-        einsum(c, "nQl,Qla->na", 1.0, tn(P, {n, Q, o}), tc(h->Bov, {Q, o, v}), 1.0, s1, {n, v});
         //  sum (ad|em)(2 t_jm^ce - t_jm^ec) Y~_jcd
         double* V = c.arena.dalloc(n * o * v * v);
         einsum(c, "jmce,njcd->nmed", 1.0, tc(tau, {o, o, v, v}), tn(Yt, {n, o, v, v}), 0.0, V, {n, o, v, v});
-        einsum(c, "nmed,Qme->nQd", 1.0, tn(V, {n, o, v, v}), tc(h->Bov, {Q, o, v}), 0.0, Wq, {n, Q, v});
-        einsum(c, "nQd,Qda->na", 1.0, tn(Wq, {n, Q, v}), tc(h->Bvv, {Q, v, v}), 1.0, s1, {n, v});
+        einsum(c, "nmed,Qme->nQd", 1.0, tn(V, {n, o, v, v}), tc(h->Bov, {Q, o, v}), 1.0, Wq, {n, Q, v});
         //  - sum (am|ed) [t_jm^ce Y~_jcd + t_jm^ed Y~_jdc]   (the two exchange-type terms)
         einsum(c, "jmce,njcd->nmed", 1.0, tc(t, {o, o, v, v}), tn(Yt, {n, o, v, v}), 0.0, V, {n, o, v, v});
         einsum(c, "jmec,njdc->nmed", 1.0, tc(t, {o, o, v, v}), tn(Yt, {n, o, v, v}), 1.0, V, {n, o, v, v});
-        double* R = c.arena.dalloc(n * Q * o);
-        einsum(c, "nmed,Qed->nQm", 1.0, tn(V, {n, o, v, v}), tc(h->Bvv, {Q, v, v}), 0.0, R, {n, Q, o});
-        einsum(c, "nQm,Qma->na", -1.0, tn(R, {n, Q, o}), tc(h->Bov, {Q, o, v}), 1.0, s1, {n, v});
+        einsum(c, "nmed,Qed->nQm", -1.0, tn(V, {n, o, v, v}), tc(h->Bvv, {Q, v, v}), 1.0, P, {n, Q, o});
+        einsum(c, "nQl,Qla->na", 1.0, tn(P, {n, Q, o}), tc(h->Bov, {Q, o, v}), 1.0, s1, {n, v});
         // 2p1h column, second order:
         //  sum_lm (cl|im) t_lm^ba Y_c
         double* p = c.arena.dalloc(n * Q * o);
@@ -722,6 +721,8 @@ static void sigma_ea(adc_handle* h, const double* Xin, double* Sout, long long n
         einsum(c, "iajc,njbc->niab", -1.0, tc(h->ovov, {o, v, o, v}), tn(Y2, {n, o, v, v}), 1.0, S2, {n, o, v, v});
         einsum(c, "jibd,njad->niab", -1.0, tc(h->oovv, {o, o, v, v}), tn(Y2, {n, o, v, v}), 1.0, S2, {n, o, v, v});
     }
+    // coupling row: every sum_Qd W^Q_d (Q|da) term at once
+    einsum(c, "nQd,Qda->na", 1.0, tn(Wq, {n, Q, v}), tc(h->Bvv, {Q, v, v}), 1.0, s1, {n, v});
     k_gather<<<grid_for(n * v), 256, 0, c.stream>>>(n, v, s1, v, 0, Sout, dim, 0, 0.0);
     launch_check(c);
     k_gather<<<grid_for(n * blk), 256, 0, c.stream>>>(n, blk, S2, blk, 0, Sout, dim, v, 0.0);
@@ -885,6 +886,8 @@ struct Davidson {
     int k = 0;
     long long nsig = 0;
     double sigma_seconds = 0.0;
+    int ldg = 0;
+    std::vector<double> G;  // host [ldg][ldg]: G_ij = (SV_i . W_j + SV_j . W_i) / 2 for i, j < k
 
     void metric(const double* in, double* out, long long nvec, int inverse) {
         k_metric<<<grid_for(nvec * dim), 256, 0, h->ctx.stream>>>(h->kind == ADC_EA, h->o, h->v, nvec, in, out, inverse);
@@ -897,27 +900,51 @@ struct Davidson {
         sigma_seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         nsig += count;
     }
-    // S-orthonormalise rows [first, first+count) of V against rows [0, first) and each other; returns kept count
+    // rows and columns [k0, k0 + kn) of the symmetrised subspace matrix, from the new vectors only
+    void update_G(int k0, int kn) {
+        Ctx& c = h->ctx;
+        Scope gs(c.arena);
+        const int kt = k0 + kn;
+        double* A = c.arena.dalloc((size_t)kt * kn * 2);
+        multidot(c, kt, SV, dim, kn, W + (long long)k0 * dim, dim, dim, A);            // SV_i . W_{k0+j}
+        multidot(c, kt, W, dim, kn, SV + (long long)k0 * dim, dim, dim, A + kt * kn);  // W_i . SV_{k0+j}
+        std::vector<double> hA((size_t)kt * kn * 2);
+        ADC_CUDA(cudaMemcpyAsync(hA.data(), A, hA.size() * sizeof(double), cudaMemcpyDeviceToHost, h->ctx.stream));
+        ADC_CUDA(cudaStreamSynchronize(h->ctx.stream));
+        for (int i = 0; i < kt; ++i)
+            for (int j = 0; j < kn; ++j) {
+                const double g = 0.5 * (hA[(size_t)i * kn + j] + hA[(size_t)kt * kn + i * kn + j]);
+                G[(size_t)i * ldg + k0 + j] = g;
+                G[(size_t)(k0 + j) * ldg + i] = g;
+            }
+    }
+    // S-orthonormalise rows [first, first+count) of V against rows [0, first) and each other; returns kept count.
+    // Block classical Gram-Schmidt against the basis (two passes), then one new vector at a time.
     int orthonormalise(int first, int count) {
         Ctx& c = h->ctx;
         Scope os(c.arena);
-        int kept = 0;
-        double* cd = c.arena.dalloc(first + count);
-        for (int r = 0; r < count; ++r) {
-            double* x = V + (long long)(first + r) * dim;
-            double* dst = V + (long long)(first + kept) * dim;
-            if (dst != x) ADC_CUDA(cudaMemcpyAsync(dst, x, dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
-            int nb = first + kept;
-            for (int pass = 0; pass < 2 && nb > 0; ++pass) {
-                // coef = SV[0:nb] . dst ; dst -= coef^T V[0:nb]
-                gemm(c, false, true, 1, nb, dim, 1.0, dst, dim, 0, SV, dim, 0, 0.0, cd, nb, 0, 1);
-                gemm(c, false, false, 1, dim, nb, -1.0, cd, nb, 0, V, dim, 0, 1.0, dst, dim, 0, 1);
+        double* D = V + (long long)first * dim;
+        double* cf = c.arena.dalloc((size_t)std::max(1, count) * std::max(1, first + count));
+        if (first > 0)
+            for (int pass = 0; pass < 2; ++pass) {
+                multidot(c, count, D, dim, first, SV, dim, dim, cf);           // cf[r][i] = D_r . (S V)_i
+                lincomb(c, count, first, cf, V, dim, dim, -1.0, 1.0, D, dim);  // D_r -= sum_i cf[r][i] V_i
             }
+        int kept = 0;
+        for (int r = 0; r < count; ++r) {
+            double* x = D + (long long)r * dim;
+            double* dst = D + (long long)kept * dim;
+            if (dst != x) ADC_CUDA(cudaMemcpyAsync(dst, x, dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+            if (kept > 0)
+                for (int pass = 0; pass < 2; ++pass) {
+                    multidot(c, 1, dst, dim, kept, SV + (long long)first * dim, dim, dim, cf);
+                    lincomb(c, 1, kept, cf, D, dim, dim, -1.0, 1.0, dst, dim);
+                }
             double* sdst = SV + (long long)(first + kept) * dim;
             metric(dst, sdst, 1, 0);
-            gemm(c, false, true, 1, 1, dim, 1.0, dst, dim, 0, sdst, dim, 0, 0.0, cd, 1, 0, 1);
+            multidot(c, 1, dst, dim, 1, sdst, dim, dim, cf);
             double nrm2 = 0.0;
-            ADC_CUDA(cudaMemcpyAsync(&nrm2, cd, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+            ADC_CUDA(cudaMemcpyAsync(&nrm2, cf, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
             ADC_CUDA(cudaStreamSynchronize(c.stream));
             if (!(nrm2 > 1e-20)) continue;
             double s = 1.0 / std::sqrt(nrm2);
@@ -942,6 +969,8 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
     const double rtol = h->opt.res_tol > 0 ? h->opt.res_tol : std::sqrt(tol);
     Scope sc(c.arena);
     Davidson d{h, dim, nroots, maxspace, nullptr, nullptr, nullptr};
+    d.ldg = cap;
+    d.G.assign((size_t)cap * cap, 0.0);
     d.V = c.arena.dalloc((size_t)cap * dim);
     d.SV = c.arena.dalloc((size_t)cap * dim);
     d.W = c.arena.dalloc((size_t)cap * dim);
@@ -973,6 +1002,7 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
     d.k = d.orthonormalise(0, nstart);
     if (d.k < nroots) throw Error(ADC_ERR_ARG, "davidson: guess space too small");
     d.sigma(0, d.k);
+    d.update_G(0, d.k);
     std::vector<double> wold(nroots, INFINITY), w, C, G, rn(nroots);
     // learned preconditioner: a root whose residual has not dropped below 0.9 x its best for
     // 4 iterations falls back to the diagonal one for the rest of the run
@@ -982,30 +1012,27 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
     int maxit = std::max(1, h->opt.max_iter);
     for (it = 1; it <= maxit; ++it) {
         int k = d.k;
-        // G = V S W^T = SV W^T (symmetric)
-        gemm(c, false, true, k, k, dim, 1.0, d.SV, dim, 0, d.W, dim, 0, 0.0, Gd, k, 0, 1);
+        // G = V S W^T (symmetrised), kept up to date on the host as vectors are added
         G.resize((size_t)k * k);
-        ADC_CUDA(cudaMemcpyAsync(G.data(), Gd, (size_t)k * k * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
-        ADC_CUDA(cudaStreamSynchronize(c.stream));
         for (int i = 0; i < k; ++i)
-            for (int j = 0; j < i; ++j) G[(size_t)i * k + j] = G[(size_t)j * k + i] = 0.5 * (G[(size_t)i * k + j] + G[(size_t)j * k + i]);
+            for (int j = 0; j < k; ++j) G[(size_t)i * k + j] = d.G[(size_t)i * d.ldg + j];
         jacobi_eigh(k, G, w, C);
         // Ct[r][i] = C[i][r] for the lowest nroots
         std::vector<double> Ct((size_t)nroots * k);
         for (int r = 0; r < nroots; ++r)
             for (int i = 0; i < k; ++i) Ct[(size_t)r * k + i] = C[(size_t)i * k + r];
         ADC_CUDA(cudaMemcpyAsync(Cd, Ct.data(), Ct.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
-        gemm(c, false, false, nroots, dim, k, 1.0, Cd, k, 0, d.V, dim, 0, 0.0, X, dim, 0, 1);
-        gemm(c, false, false, nroots, dim, k, 1.0, Cd, k, 0, d.W, dim, 0, 0.0, AX, dim, 0, 1);
+        lincomb(c, nroots, k, Cd, d.V, dim, dim, 1.0, 0.0, X, dim);
+        lincomb(c, nroots, k, Cd, d.W, dim, dim, 1.0, 0.0, AX, dim);
         // R = AX - w X
         ADC_CUDA(cudaMemcpyAsync(R, AX, (size_t)nroots * dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
         for (int r = 0; r < nroots; ++r) axpby(c, dim, -w[r], X + (long long)r * dim, 1.0, R + (long long)r * dim);
         d.metric(R, SR, nroots, 0);
-        std::vector<double> rr(nroots);
-        for (int r = 0; r < nroots; ++r)
-            gemm(c, false, true, 1, 1, dim, 1.0, R + (long long)r * dim, dim, 0, SR + (long long)r * dim, dim, 0, 0.0, Cd + r, 1, 0, 1);
-        ADC_CUDA(cudaMemcpyAsync(rr.data(), Cd, nroots * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        std::vector<double> rr(nroots), rrm((size_t)nroots * nroots);
+        multidot(c, nroots, R, dim, nroots, SR, dim, dim, Gd);
+        ADC_CUDA(cudaMemcpyAsync(rrm.data(), Gd, rrm.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
         ADC_CUDA(cudaStreamSynchronize(c.stream));
+        for (int r = 0; r < nroots; ++r) rr[r] = rrm[(size_t)r * nroots + r];
         bool all = true;
         std::vector<int> todo;
         for (int r = 0; r < nroots; ++r) {
@@ -1039,12 +1066,15 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
             double* Ckd = c.arena.dalloc((size_t)nkeep * k);
             double* tmp = c.arena.dalloc((size_t)nkeep * dim);
             ADC_CUDA(cudaMemcpyAsync(Ckd, Ck.data(), Ck.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
-            gemm(c, false, false, nkeep, dim, k, 1.0, Ckd, k, 0, d.V, dim, 0, 0.0, tmp, dim, 0, 1);
+            lincomb(c, nkeep, k, Ckd, d.V, dim, dim, 1.0, 0.0, tmp, dim);
             ADC_CUDA(cudaMemcpyAsync(d.V, tmp, (size_t)nkeep * dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
-            gemm(c, false, false, nkeep, dim, k, 1.0, Ckd, k, 0, d.W, dim, 0, 0.0, tmp, dim, 0, 1);
+            lincomb(c, nkeep, k, Ckd, d.W, dim, dim, 1.0, 0.0, tmp, dim);
             ADC_CUDA(cudaMemcpyAsync(d.W, tmp, (size_t)nkeep * dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
             d.metric(d.V, d.SV, nkeep, 0);
             d.k = nkeep;
+            // the collapsed basis diagonalises the subspace matrix: G = diag(w_0 .. w_nkeep-1)
+            std::fill(d.G.begin(), d.G.end(), 0.0);
+            for (int r = 0; r < nkeep; ++r) d.G[(size_t)r * d.ldg + r] = w[r];
         }
         // corrections for unconverged roots
         std::vector<double> wt(nnew);
@@ -1069,6 +1099,7 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
             break;
         }
         d.sigma(d.k, kept);
+        d.update_G(d.k, kept);
         d.k += kept;
     }
     // Final refinement (mixed precision): sigma of the Ritz vectors once more
@@ -1095,8 +1126,8 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
         c.gemm_mode = saved;
         const int n = nroots;
         d.metric(X, SR, n, 0);
-        gemm(c, false, true, n, n, dim, 1.0, SR, dim, 0, AX, dim, 0, 0.0, Gd, n, 0, 1);          // X S sigma(X)^T
-        gemm(c, false, true, n, n, dim, 1.0, SR, dim, 0, X, dim, 0, 0.0, Gd + n * n, n, 0, 1);   // X S X^T
+        multidot(c, n, SR, dim, n, AX, dim, dim, Gd);         // X S sigma(X)^T
+        multidot(c, n, SR, dim, n, X, dim, dim, Gd + n * n);  // X S X^T
         std::vector<double> GO((size_t)2 * n * n);
         ADC_CUDA(cudaMemcpyAsync(GO.data(), Gd, GO.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
         ADC_CUDA(cudaStreamSynchronize(c.stream));
@@ -1128,19 +1159,19 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
             for (int i = 0; i < n; ++i)
                 for (int k2 = 0; k2 < n; ++k2) Crt[(size_t)r * n + i] += Oi[(size_t)i * n + k2] * Z[(size_t)k2 * n + r];
         ADC_CUDA(cudaMemcpyAsync(Cd, Crt.data(), Crt.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
-        gemm(c, false, false, n, dim, n, 1.0, Cd, n, 0, X, dim, 0, 0.0, R, dim, 0, 1);
-        gemm(c, false, false, n, dim, n, 1.0, Cd, n, 0, AX, dim, 0, 0.0, SR, dim, 0, 1);
+        lincomb(c, n, n, Cd, X, dim, dim, 1.0, 0.0, R, dim);
+        lincomb(c, n, n, Cd, AX, dim, dim, 1.0, 0.0, SR, dim);
         ADC_CUDA(cudaMemcpyAsync(X, R, (size_t)n * dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
         ADC_CUDA(cudaMemcpyAsync(AX, SR, (size_t)n * dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
         // residuals of the refined pairs under the accurate operator
         ADC_CUDA(cudaMemcpyAsync(R, AX, (size_t)n * dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
         for (int r = 0; r < n; ++r) axpby(c, dim, -wr[r], X + (long long)r * dim, 1.0, R + (long long)r * dim);
         d.metric(R, SR, n, 0);
-        for (int r = 0; r < n; ++r)
-            gemm(c, false, true, 1, 1, dim, 1.0, R + (long long)r * dim, dim, 0, SR + (long long)r * dim, dim, 0, 0.0, Cd + r, 1, 0, 1);
-        std::vector<double> rr(n);
-        ADC_CUDA(cudaMemcpyAsync(rr.data(), Cd, n * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        std::vector<double> rr(n), rrm((size_t)n * n);
+        multidot(c, n, R, dim, n, SR, dim, dim, Gd);
+        ADC_CUDA(cudaMemcpyAsync(rrm.data(), Gd, rrm.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
         ADC_CUDA(cudaStreamSynchronize(c.stream));
+        for (int r = 0; r < n; ++r) rr[r] = rrm[(size_t)r * n + r];
         for (int r = 0; r < n; ++r) {
             refine_shift = std::max(refine_shift, std::fabs(wr[r] - w[r]));
             w[r] = wr[r];

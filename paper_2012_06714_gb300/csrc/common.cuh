@@ -119,7 +119,7 @@ struct Ctx {
     // split-BF16 GEMM (two planes, FP32 partial sums promoted every 16 K
     // blocks, FP64 result).
     int gemm_mode = 0;
-    double fp32_min_flops = 2e8;
+    double fp32_min_flops = 1e8;
     int emulation_ok = -1;  // -1 unknown, 1 BF16x9 emulation available, 0 plain FP32
     // live timing of the tensor-core GEMM launches (see adc_kernel_timing)
     bool timing = false;
