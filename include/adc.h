@@ -90,6 +90,9 @@ typedef struct {
                              /* span; 1 (default): other contractions as in sigma     */
                              /* (FP32-accurate), 2: FP64 for every other contraction, */
                              /* 0: no refinement                                      */
+    int transition_order;    /* order of T in the spectroscopic amplitudes (Eqs.      */
+                             /* T_ea, T_ip): 0 (default) = n, the method's order;     */
+                             /* 2 = second order also for ADC(3) (no t1(3), no t2(2)) */
 } adc_options;
 
 /* Fill *opt with the defaults listed above.  Returns ADC_OK or ADC_ERR_ARG (NULL). */
@@ -124,8 +127,8 @@ int adc_setup_batch(int nmol, const double* const* eps, const double* const* Bq,
                     const int* naux, int order, int kind, const adc_options* opt, int on_device, adc_handle** out);
 
 /* Replace the solver options of a handle (max_space_per_root, max_iter,
- * nguess_extra, res_tol, keep_per_root, refine); precision, contractions and
- * aux_chunk stay as set up.  Errors: ADC_ERR_ARG. */
+ * nguess_extra, res_tol, keep_per_root, refine, transition_order); precision,
+ * contractions and aux_chunk stay as set up.  Errors: ADC_ERR_ARG. */
 int adc_set_options(adc_handle* h, const adc_options* opt);
 
 /* Length of the spin-adapted vector (see layout above). */

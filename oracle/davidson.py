@@ -27,8 +27,8 @@ def dense_roots(adc, nroots):
     return w[:nroots], Y[:, :nroots].T
 
 
-def transition_moments(adc):
-    """Spatial T through order n = adc.order (Eqs. T_ea, T_ip, k + l <= n):
+def transition_moments(adc, torder=None):
+    """Spatial T through order n = torder, default adc.order (Eqs. T_ea, T_ip, k + l <= n):
     (T1 [nmo, n1], T2 [nmo, ...2p1h/2h1p shape]).
 
     Second order, with the density form B(x, y) (EA) / B'(x, y) (IP)
@@ -49,7 +49,7 @@ def transition_moments(adc):
     t = adc.t
     t1 = adc.t1_2 if hasattr(adc, "t1_2") else _t1_second_order(adc)
     nmo = o + v
-    third = adc.order >= 3
+    third = (adc.order if torder is None else torder) >= 3 and adc.order >= 3
     if third:
         t2 = adc.t_2
         tau = 2.0 * t - t.transpose(0, 1, 3, 2)
@@ -89,10 +89,10 @@ def _t1_second_order(adc):
     return (s1 - s2) / adc.D1
 
 
-def spectroscopic_factors(adc, Y):
-    """P for each row of Y[nroots, dim] (Appendix normalisation)."""
+def spectroscopic_factors(adc, Y, torder=None):
+    """P for each row of Y[nroots, dim] (Appendix normalisation), T through order torder (default n)."""
     Y = np.atleast_2d(Y)
-    T1, T2 = transition_moments(adc)
+    T1, T2 = transition_moments(adc, torder)
     SY = adc.apply_S(Y)
     norm = np.einsum("rk,rk->r", Y, SY)
     Yt = SY / np.sqrt(norm)[:, None]

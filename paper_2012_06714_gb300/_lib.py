@@ -49,6 +49,7 @@ class Options(ctypes.Structure):
         ("keep_per_root", ctypes.c_int),
         ("contractions", ctypes.c_int),
         ("refine", ctypes.c_int),
+        ("transition_order", ctypes.c_int),
     ]
 
 
@@ -136,7 +137,8 @@ class ADC:
     """
 
     def __init__(self, eps, B, nocc, order=3, kind="ea", precision="fp64", max_space_per_root=8, max_iter=100,
-                 nguess_extra=2, res_tol=0.0, aux_chunk=0, keep_per_root=2, contractions=-1, refine=1):
+                 nguess_extra=2, res_tol=0.0, aux_chunk=0, keep_per_root=2, contractions=-1, refine=1,
+                 transition_order=0):
         lib = load_library()
         self._lib = lib
         opt = Options()
@@ -150,8 +152,10 @@ class ADC:
         opt.keep_per_root = keep_per_root
         opt.contractions = contractions
         opt.refine = refine
+        opt.transition_order = transition_order
         self._solver = dict(max_space_per_root=max_space_per_root, max_iter=max_iter, nguess_extra=nguess_extra,
-                            res_tol=res_tol, keep_per_root=keep_per_root, refine=refine)
+                            res_tol=res_tol, keep_per_root=keep_per_root, refine=refine,
+                            transition_order=transition_order)
         if isinstance(eps, np.ndarray):
             eps = np.ascontiguousarray(eps, dtype=np.float64)
             B = np.ascontiguousarray(B, dtype=np.float64)
@@ -211,10 +215,12 @@ class ADC:
         return e, p, vec, stats
 
     def set_options(self, **kw):
-        """Change solver options (max_space_per_root, max_iter, nguess_extra, res_tol, keep_per_root, refine)."""
+        """Change solver options (max_space_per_root, max_iter, nguess_extra, res_tol, keep_per_root, refine,
+        transition_order)."""
         opt = Options()
         self._lib.adc_default_options(ctypes.byref(opt))
-        for k in ("max_space_per_root", "max_iter", "nguess_extra", "res_tol", "keep_per_root", "refine"):
+        for k in ("max_space_per_root", "max_iter", "nguess_extra", "res_tol", "keep_per_root", "refine",
+                  "transition_order"):
             setattr(opt, k, kw.pop(k, self._solver[k]))
         if kw:
             raise TypeError(f"not a solver option: {sorted(kw)}")

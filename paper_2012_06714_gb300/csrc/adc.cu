@@ -1215,7 +1215,7 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
         // ADC(3): T through third order (k + l <= 3): the density cross terms with
         // t2(2), t1(3) + 1/2 tau t1(2) in the one-particle rows of the other space,
         // and t2(2) beside t2(1) in the two-particle columns
-        const bool third = h->order >= 3;
+        const bool third = h->order >= 3 && h->opt.transition_order != 2;
         double* t1x = nullptr;  // t1(2) [+ t1(3) + 1/2 sum tau t1(2)], [o][v]
         if (third) {
             make_t1_third_order(h);
@@ -1388,7 +1388,7 @@ int adc_mlp_train(float* weights, const double* d, const unsigned char* blk, con
 int adc_set_options(adc_handle* h, const adc_options* opt) {
     if (!h || !opt) return ADC_ERR_ARG;
     if (opt->max_space_per_root < 1 || opt->max_iter < 1 || opt->nguess_extra < 0 || opt->keep_per_root < 1 ||
-        opt->refine < 0 || opt->refine > 2) {
+        opt->refine < 0 || opt->refine > 2 || (opt->transition_order != 0 && opt->transition_order != 2)) {
         h->err = "adc_set_options: invalid option";
         return ADC_ERR_ARG;
     }
@@ -1399,6 +1399,7 @@ int adc_set_options(adc_handle* h, const adc_options* opt) {
     h->opt.res_tol = opt->res_tol;
     h->opt.keep_per_root = opt->keep_per_root;
     h->opt.refine = opt->refine;
+    h->opt.transition_order = opt->transition_order;
     return ADC_OK;
 }
 
@@ -1430,6 +1431,7 @@ int adc_default_options(adc_options* opt) {
     opt->keep_per_root = 2;
     opt->contractions = -1;
     opt->refine = 1;
+    opt->transition_order = 0;
     return ADC_OK;
 }
 
@@ -1451,6 +1453,10 @@ static int setup_one(const double* eps, const double* Bq, int nocc, int nvir, in
     }
     if (opt && (opt->contractions < -1 || opt->contractions > 2 || opt->refine < 0 || opt->refine > 2)) {
         msg = "adc_setup: contractions must be -1..2 and refine 0..2";
+        return ADC_ERR_ARG;
+    }
+    if (opt && opt->transition_order != 0 && opt->transition_order != 2) {
+        msg = "adc_setup: transition_order must be 0 (the method's order) or 2";
         return ADC_ERR_ARG;
     }
     adc_handle* h = new adc_handle();

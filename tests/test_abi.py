@@ -50,6 +50,7 @@ def test_default_options_and_argument_errors(lib):
     o = Options()
     assert L.adc_default_options(ctypes.byref(o)) == 0
     assert o.precision == 0 and o.max_space_per_root == 8 and o.max_iter == 100
+    assert o.refine == 1 and o.transition_order == 0 and o.contractions == -1
     assert L.adc_default_options(None) == -1
     h = ctypes.c_void_p()
     # invalid sizes are rejected on the host before any device work

@@ -109,6 +109,12 @@ def test_davidson_fp64_small(lib, kind, order):
     pr = spectroscopic_factors(ref, vec)
     assert np.abs(p - pr).max() < 1e-10
     assert np.abs(p - spectroscopic_factors(ref, Y)).max() < 1e-7
+    if order == 3:
+        # second-order transition moments on request (transition_order = 2)
+        gpu.set_options(transition_order=2)
+        e2, p2, vec2, _ = gpu.davidson(4, tol=1e-10, want_vectors=True)
+        assert np.abs(p2 - spectroscopic_factors(ref, vec2, 2)).max() < 1e-10
+        assert np.abs(p2 - p).max() > 1e-6
     gpu.close()
 
 

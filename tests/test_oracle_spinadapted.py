@@ -67,24 +67,24 @@ def test_mp_energies_match_spin_orbital():
     assert abs(e3[1] - S.mp3_energy()) < 1e-14
 
 
-@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("order,torder", [(2, None), (3, None), (3, 2)])
 @pytest.mark.parametrize("kind", ["ea", "ip"])
-def test_transition_moments_match_spin_orbital(order, kind):
-    """X = T E Y~ for every S-normalised vector: the spatial T (through order n)
-    acting on a doublet vector equals the spin-orbital T on its embedding,
-    for the alpha (EA) / beta (IP) orbital rows the embedding addresses."""
+def test_transition_moments_match_spin_orbital(order, torder, kind):
+    """X = T E Y~ for every S-normalised vector: the spatial T (through order n,
+    or second order for ADC(3) on request) acting on a doublet vector equals the
+    spin-orbital T on its embedding (P summed over both spin components)."""
     o, v = 3, 4
     s = make_system(o, v, 16, seed=6)
     B = 2.0 * s.B
     T = SpinAdaptedADC(s.eps, o, B, order, kind)
     S = SpinOrbitalADC(s.eps, o, order, B=B)
     E = embedding(o, v, kind)
-    T1, T2 = S.ea_transition() if kind == "ea" else S.ip_transition()
+    T1, T2 = S.ea_transition(torder) if kind == "ea" else S.ip_transition(torder)
     _, two = S.basis_labels(kind)
     I = np.array(two)
     Tso = np.concatenate([T1, T2[:, I[:, 0], I[:, 1], I[:, 2]]], axis=1)
     Y = np.random.default_rng(0).standard_normal((5, T.dim))
-    P = spectroscopic_factors(T, Y)
+    P = spectroscopic_factors(T, Y, torder)
     for r in range(5):
         u = E @ Y[r]
         u /= np.linalg.norm(u)
