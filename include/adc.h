@@ -75,7 +75,8 @@ typedef struct {
     int max_iter;            /* Davidson iteration limit (default 100)                */
     int nguess_extra;        /* extra guess vectors beyond nroots (default 2)         */
     double res_tol;          /* S-norm residual tolerance; <= 0 means sqrt(tol)       */
-    int aux_chunk;           /* auxiliary functions per ladder chunk; 0 = automatic   */
+    int aux_chunk;           /* auxiliary functions per chunk of the ladder and of    */
+                             /* the t1(3) contraction; 0 = automatic                  */
     int keep_per_root;       /* Ritz vectors kept per root when the space is          */
                              /* collapsed (thick restart, default 2)                  */
     int contractions;        /* non-ladder contractions: -1 follow precision (default:*/

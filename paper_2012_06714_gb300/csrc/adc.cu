@@ -405,7 +405,8 @@ static void setup_m11_ip(adc_handle* h) {
 // A1, A2: the CC-like singles terms of t1(2) and t2(2); E1..E4 and F1..F4:
 // the connected-triples term 1/4 t_jk^bc W_ijk^abc summed permutation by
 // permutation (particle and hole halves).  The costliest pieces are the ring
-// products R1, R2 (o^3 v^3) and E2 (4 naux o^3 v^2, auxiliary index chunked).
+// products R1, R2 (o^3 v^3) and E2 (4 naux o^3 v^2, auxiliary index chunked by
+// aux_chunk, or into slabs of W of at most 2^29 elements).
 // --------------------------------------------------------------------------
 static void make_t1_third_order(adc_handle* h) {
     if (h->t1_3 || h->order < 3) return;
@@ -454,8 +455,10 @@ static void make_t1_third_order(adc_handle* h) {
             double* tauS = c.arena.dalloc(o2v2);  // tau_jk^cb stored [j][k][b][c]
             permute(c, tau, s4, swp, tauS, 1.0, 0.0);
             double* V = c.arena.dalloc(v * o * o * o);  // [d][j][k][i]
+            // auxiliary functions per chunk: the aux_chunk option if set, else a 4 GiB slab of W
             const long long per = v * o * o * o;
-            const long long qc = std::max(1LL, std::min(Q, (1LL << 27) / std::max(per, 1LL)));
+            const long long qc = h->opt.aux_chunk > 0 ? std::min<long long>(Q, h->opt.aux_chunk)
+                                                      : std::max(1LL, std::min(Q, (1LL << 29) / std::max(per, 1LL)));
             double* W = c.arena.dalloc(qc * per);  // [Q][b][j][k][i]
             for (long long q0 = 0; q0 < Q; q0 += qc) {
                 const long long nq = std::min(qc, Q - q0);
@@ -925,11 +928,32 @@ struct Davidson {
         Scope os(c.arena);
         double* D = V + (long long)first * dim;
         double* cf = c.arena.dalloc((size_t)std::max(1, count) * std::max(1, first + count));
-        if (first > 0)
+        if (first > 0) {
+            // second pass only where the first removed more than 1 - 1/sqrt(2) of a vector's
+            // S-norm (the Daniel-Gragg-Kaufman-Stewart criterion)
+            double* SD = c.arena.dalloc((size_t)count * dim);
+            double* nn = c.arena.dalloc((size_t)count * count);
+            auto snorms = [&](std::vector<double>& out) {
+                metric(D, SD, count, 0);
+                multidot(c, count, D, dim, count, SD, dim, dim, nn);
+                std::vector<double> m((size_t)count * count);
+                ADC_CUDA(cudaMemcpyAsync(m.data(), nn, m.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+                ADC_CUDA(cudaStreamSynchronize(c.stream));
+                out.resize(count);
+                for (int r = 0; r < count; ++r) out[r] = m[(size_t)r * count + r];
+            };
+            std::vector<double> before, after;
+            snorms(before);
             for (int pass = 0; pass < 2; ++pass) {
                 multidot(c, count, D, dim, first, SV, dim, dim, cf);           // cf[r][i] = D_r . (S V)_i
                 lincomb(c, count, first, cf, V, dim, dim, -1.0, 1.0, D, dim);  // D_r -= sum_i cf[r][i] V_i
+                if (pass == 1) break;
+                snorms(after);
+                bool again = false;
+                for (int r = 0; r < count; ++r) again = again || !(after[r] >= 0.5 * before[r]);
+                if (!again) break;
             }
+        }
         int kept = 0;
         for (int r = 0; r < count; ++r) {
             double* x = D + (long long)r * dim;

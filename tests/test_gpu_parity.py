@@ -79,18 +79,23 @@ def chunked_case():
 @pytest.mark.parametrize("precision", ["fp64", "bf16x3"])
 def test_third_order_singles_auxiliary_chunks(lib, chunked_case, precision):
     """t_i^a(3) with the auxiliary index split into two chunks (1500 = 1039 + 461
-    at nocc 11, nvir 97) against the oracle; the mixed path forms it in the
-    setup's FP32-accurate contractions (relative 1e-6 of the largest element)."""
+    at nocc 11, nvir 97, chunk set through aux_chunk) against the oracle, and in
+    one chunk (the automatic size); the mixed path forms it in the setup's
+    FP32-accurate contractions (relative 1e-6 of the largest element)."""
     from paper_2012_06714_gb300 import ADC
 
     s, ref = chunked_case
     o, v = 11, 97
-    gpu = ADC(s.eps, s.B, o, order=3, kind="ip", precision=precision)
+    one = ADC(s.eps, s.B, o, order=3, kind="ip", precision=precision)
+    whole = one.get("t1_3", (o, v))
+    one.close()
+    gpu = ADC(s.eps, s.B, o, order=3, kind="ip", precision=precision, aux_chunk=1039)
     got = gpu.get("t1_3", (o, v))
     gpu.close()
     scale = np.abs(ref.t1_3).max()
     assert scale > 1e-4
     assert np.abs(got - ref.t1_3).max() <= (1e-12 if precision == "fp64" else 1e-6) * scale
+    assert np.abs(whole - ref.t1_3).max() <= (1e-12 if precision == "fp64" else 1e-6) * scale
 
 
 @pytest.mark.parametrize("kind", ["ea", "ip"])
