@@ -236,6 +236,32 @@ def run_ladder_case(args):
     return 0
 
 
+def run_davidson_case(args):
+    """Small profiling case of the Davidson subspace kernels (for ncu):
+    EA-ADC(3) mixed precision with nocc=24, nvir=240, naux=500 (1.38e6-element
+    vectors, so a subspace of 16-32 vectors exceeds L2; about 2.5 GB on the
+    device), 4 roots, at most 8 vectors per root, `--steps` Davidson
+    iterations (not converged; the status is printed)."""
+    import torch
+
+    from adc_inputs import make_system
+    from paper_2012_06714_gb300 import ADC
+
+    o, v, naux = 24, 240, 500
+    s = make_system(o, v, naux, seed=0)
+    g = ADC(torch.from_numpy(s.eps).cuda(), torch.from_numpy(s.B).cuda(), o, order=3, kind="ea",
+            precision="bf16x3", max_iter=max(1, args.steps), refine=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e, p, _, st = g.davidson(4, tol=1e-12)
+    print(json.dumps({"case": "davidson EA-ADC(3) o=24 v=240 naux=500, 4 roots", "dim": g.dim,
+                      "iterations": st["iterations"], "sigma_vectors": st["sigma_vectors"],
+                      "seconds": time.perf_counter() - t0, "sigma_seconds": st["sigma_seconds"],
+                      "status": st["status"]}))
+    g.close()
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -416,7 +442,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-roots", action="store_true")
     ap.add_argument("--ladder-case", action="store_true", help="small ladder profiling case (for ncu)")
+    ap.add_argument("--davidson-case", action="store_true", help="small Davidson profiling case (for ncu)")
     args = ap.parse_args()
+    if args.davidson_case:
+        return run_davidson_case(args)
     if args.ladder_case:
         return run_ladder_case(args)
     if args.impl == "reference":
