@@ -104,8 +104,13 @@ def test_df_complete_auxiliary_set(kind):
     assert B.shape[0] <= nmo * (nmo + 1) // 2
     eps = make_system(o, v, 4, seed=1).eps
     T = SpinAdaptedADC(eps, o, B, 3, kind)
-    Msa, _ = _sa_from_so(SpinOrbitalADC(eps, o, 3, eri=eri), kind, o, v)
+    S = SpinOrbitalADC(eps, o, 3, eri=eri)
+    Msa, _ = _sa_from_so(S, kind, o, v)
     assert np.abs(T.dense() - Msa).max() < 1e-12
+    # the DF forms of t1(3) and of the MP energies reproduce the four-index ones
+    assert np.abs(T.t1_3 - S.t1_3[0::2, 0::2]).max() < 1e-13
+    assert abs(T.mp_energies()[0] - S.mp2_energy()) < 1e-13
+    assert abs(T.mp_energies()[1] - S.mp3_energy()) < 1e-13
 
 
 @pytest.mark.parametrize("kind", ["ea", "ip"])
