@@ -73,6 +73,48 @@ def make_psd_eri(nmo: int, seed: int = 3, scale: float = 0.05) -> np.ndarray:
     return G[pair[:, :, None, None], pair[None, None, :, :]]
 
 
+@dataclasses.dataclass
+class OpenShellSystem:
+    nocc_a: int
+    nocc_b: int
+    eps_a: np.ndarray  # [nmo] alpha orbital energies, occupied first, each block ascending
+    eps_b: np.ndarray  # [nmo] beta orbital energies
+    B_a: np.ndarray  # [naux, nmo, nmo] alpha-orbital DF factors, symmetric in the last two indices
+    B_b: np.ndarray  # [naux, nmo, nmo] beta-orbital DF factors
+
+    @property
+    def nmo(self) -> int:
+        return len(self.eps_a)
+
+
+def make_open_shell_system(nocc_a: int, nocc_b: int, nmo: int, naux: int, seed: int = 0) -> OpenShellSystem:
+    """Synthetic unrestricted (open-shell) reference: alpha and beta orbitals
+    share one auxiliary-basis tensor b^Q (drawn as in make_system) but have
+    their own orthonormal orbital coefficients C_s = Q factor of
+    (1 + 0.2 N(0,1)), so that B_s^Q = C_s^T b^Q C_s; orbital energies are drawn
+    per spin as in make_system with nocc_a / nocc_b occupied.  Draw order:
+    eps (alpha occ, alpha vir, beta occ, beta vir), b^Q (Q-major), C_a, C_b."""
+    rng = np.random.default_rng(seed)
+
+    def energies(no):
+        return np.concatenate([np.sort(rng.uniform(-1.5, -0.3, size=no)),
+                               np.sort(0.05 + rng.uniform(0.0, 1.0, size=nmo - no) ** 2 * 4.95)])
+
+    eps_a, eps_b = energies(nocc_a), energies(nocc_b)
+    s = 0.3 / np.sqrt(naux)
+    b = np.empty((naux, nmo, nmo))
+    for q in range(naux):
+        g = rng.standard_normal((nmo, nmo))
+        b[q] = (s * 0.5) * (g + g.T)
+    C = []
+    for _ in range(2):
+        Cq, _r = np.linalg.qr(np.eye(nmo) + 0.2 * rng.standard_normal((nmo, nmo)))
+        C.append(Cq)
+    B_a = np.einsum("pm,Qpq,qn->Qmn", C[0], b, C[0])
+    B_b = np.einsum("pm,Qpq,qn->Qmn", C[1], b, C[1])
+    return OpenShellSystem(nocc_a, nocc_b, eps_a, eps_b, B_a, B_b)
+
+
 # Named workloads (sizes of the paper-shaped synthetic cases).
 CONFIGS = {
     "ea2_small": dict(nocc=5, nvir=20, naux=80, order=2, kind="ea", nroots=4),

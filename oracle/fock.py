@@ -129,15 +129,25 @@ class ADCFock:
 
     def __init__(self, eps, nocc, order, B=None, eri=None):
         eps = np.asarray(eps, dtype=float)
-        self.nmo = len(eps)
-        self.nocc = nocc
-        self.order = order
-        self.nso = 2 * self.nmo
-        self.no = 2 * nocc
-        self.eps_so = np.repeat(eps, 2)
         if eri is None:
             eri = np.einsum("Qpq,Qrs->pqrs", B, B)
-        self.asym = spin_orbital_antisym(np.asarray(eri, dtype=float))
+        self._init_spin_orbitals(np.repeat(eps, 2), 2 * nocc, spin_orbital_antisym(np.asarray(eri, dtype=float)), order)
+
+    @classmethod
+    def from_spin_orbitals(cls, eps_so, no, asym, order):
+        """Any reference given in spin orbitals: energies eps_so [nso], the
+        first `no` spin orbitals occupied, antisymmetrised <PQ||RS> [nso]^4
+        (unrestricted open-shell references, Sec. II)."""
+        self = cls.__new__(cls)
+        self._init_spin_orbitals(np.asarray(eps_so, dtype=float), no, np.asarray(asym, dtype=float), order)
+        return self
+
+    def _init_spin_orbitals(self, eps_so, no, asym, order):
+        self.order = order
+        self.nso = len(eps_so)
+        self.no = no
+        self.eps_so = eps_so
+        self.asym = asym
         self.fs = FockSpace(self.nso)
         self.N = self.no
         self.occ = list(range(self.no))

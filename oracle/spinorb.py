@@ -66,16 +66,25 @@ class SpinOrbitalADC:
         eps = np.asarray(eps, dtype=float)
         if eri is None:
             eri = np.einsum("Qpq,Qrs->pqrs", B, B)
+        self._init_spin_orbitals(np.repeat(eps, 2), 2 * nocc, antisym_integrals(np.asarray(eri, dtype=float)), order)
+
+    @classmethod
+    def from_spin_orbitals(cls, eps_so, no, g, order):
+        """Any reference given in spin orbitals (eps_so [nso], the first `no`
+        occupied, g = <PQ||RS>): the same working equations serve the
+        unrestricted open-shell case (UADC, Sec. II)."""
+        self = cls.__new__(cls)
+        self._init_spin_orbitals(np.asarray(eps_so, dtype=float), no, np.asarray(g, dtype=float), order)
+        return self
+
+    def _init_spin_orbitals(self, e, no, g, order):
         self.order = order
-        self.nmo = len(eps)
-        self.no = 2 * nocc
-        self.nso = 2 * self.nmo
+        self.no = no
+        self.nso = len(e)
         self.nv = self.nso - self.no
-        g = antisym_integrals(np.asarray(eri, dtype=float))
         o, v = slice(0, self.no), slice(self.no, self.nso)
         self._sl = {"o": o, "v": v}
         self.g = g
-        e = np.repeat(eps, 2)
         self.eo, self.ev = e[o], e[v]
         self.D2 = self.eo[:, None, None, None] + self.eo[None, :, None, None] - self.ev[None, None, :, None] - self.ev[None, None, None, :]
         self.D1 = self.eo[:, None] - self.ev[None, :]

@@ -1,0 +1,77 @@
+"""Unrestricted (open-shell) references in the spin-orbital oracles (UADC).
+
+* Tier 1 (explicit spin-orbital equations) against tier 0 (operator
+  definitions in Fock space) on open-shell references with nocc_a != nocc_b:
+  amplitudes through t1(3), the EA/IP-ADC(2) and ADC(3) matrices and the
+  transition moments, element by element.
+* Restricted limit: an unrestricted reference built from one set of orbitals
+  for both spins reproduces the restricted spectrum and MP energies.
+"""
+import numpy as np
+import pytest
+
+from adc_inputs import make_open_shell_system, make_system
+from oracle.fock import ADCFock
+from oracle.spinorb import SpinOrbitalADC
+from oracle.unrestricted import unrestricted_spin_orbitals
+
+OPEN = [(2, 1, 5, 10, 3), (3, 2, 5, 12, 4)]  # nocc_a, nocc_b, nmo, naux, seed
+
+
+@pytest.fixture(scope="module", params=OPEN, ids=lambda c: f"a{c[0]}b{c[1]}n{c[2]}")
+def open_pair(request):
+    na, nb, nmo, naux, seed = request.param
+    s = make_open_shell_system(na, nb, nmo, naux, seed=seed)
+    eps, no, g = unrestricted_spin_orbitals(s.eps_a, s.eps_b, na, nb, 2.0 * s.B_a, 2.0 * s.B_b)
+    return ADCFock.from_spin_orbitals(eps, no, g, 3), SpinOrbitalADC.from_spin_orbitals(eps, no, g, 3), (eps, no, g)
+
+
+def test_open_shell_amplitudes(open_pair):
+    F, S, _ = open_pair
+    assert np.abs(F.t2_tensor(1) - S.t2_1).max() < 1e-13
+    assert np.abs(F.t2_tensor(2) - S.t2_2).max() < 1e-13
+    assert np.abs(F.t1_tensor(2) - S.t1_2).max() < 1e-13
+    assert np.abs(F.t1_tensor(3)).max() > 1e-4
+    assert np.abs(F.t1_tensor(3) - S.t1_3).max() < 1e-13
+    assert abs(F.energy(2) - S.mp2_energy()) < 1e-13
+    assert abs(F.energy(3) - S.mp3_energy()) < 1e-13
+
+
+@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("kind", ["ea", "ip"])
+def test_open_shell_matrices(open_pair, kind, order):
+    F, _, (eps, no, g) = open_pair
+    mats, _ = F.adc_matrices(kind)
+    S = SpinOrbitalADC.from_spin_orbitals(eps, no, g, order)
+    M = sum(mats[k] for k in range(order + 1))
+    assert np.abs(M - S.matrix(kind)).max() < 1e-12
+    assert np.abs(M - M.T).max() < 1e-12
+
+
+@pytest.mark.parametrize("kind", ["ea", "ip"])
+def test_open_shell_transition_moments(open_pair, kind):
+    F, S, _ = open_pair
+    T, _ = F.adc_transition(kind, 3)
+    one, two = S.basis_labels(kind)
+    I = np.array(two)
+    tr = S.ea_transition if kind == "ea" else S.ip_transition
+    for torder in (2, 3):
+        T1, T2 = tr(torder)
+        Ts = np.concatenate([T1, T2[:, I[:, 0], I[:, 1], I[:, 2]]], axis=1)
+        assert np.abs(sum(T[k] for k in range(torder + 1)) - Ts).max() < 1e-13
+
+
+@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("kind", ["ea", "ip"])
+def test_restricted_limit(kind, order):
+    s = make_system(3, 5, 14, seed=2)
+    B = 2.0 * s.B
+    R = SpinOrbitalADC(s.eps, 3, order, B=B)
+    eps, no, g = unrestricted_spin_orbitals(s.eps, s.eps, 3, 3, B, B)
+    U = SpinOrbitalADC.from_spin_orbitals(eps, no, g, order)
+    wr = np.linalg.eigvalsh(R.matrix(kind))
+    wu = np.linalg.eigvalsh(U.matrix(kind))
+    assert np.abs(wr - wu).max() < 1e-11
+    assert abs(R.mp2_energy() - U.mp2_energy()) < 1e-13
+    if order == 3:
+        assert abs(R.mp3_energy() - U.mp3_energy()) < 1e-13
