@@ -75,3 +75,35 @@ def test_restricted_limit(kind, order):
     assert abs(R.mp2_energy() - U.mp2_energy()) < 1e-13
     if order == 3:
         assert abs(R.mp3_energy() - U.mp3_energy()) < 1e-13
+
+
+@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("kind", ["ea", "ip"])
+def test_matrix_free_sigma_matches_tier1(kind, order):
+    """The matrix-free UADC sigma (two-particle block applied through the DF
+    ladder of the per-spin factors) equals the tier-1 spin-orbital matrix."""
+    from oracle.unrestricted import UnrestrictedADC
+
+    s = make_open_shell_system(3, 2, 7, 20, seed=5)
+    s.B_a *= 2.0
+    s.B_b *= 2.0
+    U = UnrestrictedADC(s, order, kind)
+    eps, no, g = unrestricted_spin_orbitals(s.eps_a, s.eps_b, 3, 2, s.B_a, s.B_b)
+    M = SpinOrbitalADC.from_spin_orbitals(eps, no, g, order).matrix(kind)
+    assert U.dim == M.shape[0]
+    assert np.abs(U.dense() - M).max() < 1e-12
+
+
+@pytest.mark.parametrize("kind", ["ea", "ip"])
+def test_davidson_on_unrestricted_sigma(kind):
+    """The oracle Davidson (S = 1 for the spin-orbital basis) on the matrix-free
+    UADC(3) sigma reproduces the lowest eigenvalues of its dense matrix."""
+    from oracle.davidson import davidson
+    from oracle.unrestricted import UnrestrictedADC
+
+    s = make_open_shell_system(3, 2, 9, 24, seed=6)
+    U = UnrestrictedADC(s, 3, kind)
+    M = U.dense()
+    w = np.linalg.eigvalsh(0.5 * (M + M.T))[:4]
+    wd, _, _, _ = davidson(U, 4, tol=1e-10)
+    assert np.abs(wd - w).max() < 1e-8
