@@ -386,6 +386,26 @@ class UnrestrictedDFADC:
         out = np.concatenate([s1, S2[:, i0, i1, i2]], axis=1)
         return out if self.kind == "ea" else -out
 
+    def dense(self):
+        return self.sigma(np.eye(self.dim)).T
+
+    def spectroscopic_factors(self, Y, torder=None):
+        """P_mu = sum_p |X_p mu|^2 (Eq. spec_factors, one spin-orbital component,
+        so a Koopmans state has P = 1) for rows of Y normalised here, with T
+        through order torder (default n) from the tier-1 expressions
+        (Eqs. T_ea, T_ip), which need only the amplitudes."""
+        from oracle.spinorb import SpinOrbitalADC
+
+        Y = np.atleast_2d(np.asarray(Y, dtype=float))
+        Y = Y / np.linalg.norm(Y, axis=1)[:, None]
+        self.nso = self.no + self.nv
+        tr = SpinOrbitalADC.ea_transition if self.kind == "ea" else SpinOrbitalADC.ip_transition
+        T1, T2 = tr(self, torder)
+        i0, i1, i2 = self.I
+        T = np.concatenate([T1, T2[:, i0, i1, i2]], axis=1)
+        X = Y @ T.T
+        return np.einsum("rp,rp->r", X, X)
+
     def apply_S(self, Y):
         return np.array(Y, dtype=float)
 

@@ -144,3 +144,38 @@ def test_density_fitted_davidson_larger(kind):
     R = D.sigma(Y) - w[:, None] * Y
     assert np.abs(np.linalg.norm(R, axis=1)).max() < 1e-5
     assert np.all(np.diff(w) >= -1e-12)
+
+
+@pytest.mark.parametrize("kind", ["ea", "ip"])
+def test_open_shell_koopmans_limit(kind):
+    """B -> 0: the UADC(3) roots approach the orbital energies (EA: the lowest
+    virtual spin orbitals; IP: minus the highest occupied ones) with spectroscopic
+    factor 1 each (one spin-orbital component)."""
+    from oracle.davidson import dense_roots
+    from oracle.unrestricted import UnrestrictedDFADC, spin_orbital_df
+
+    s = make_open_shell_system(3, 2, 6, 12, seed=8)
+    s.B_a *= 1e-4
+    s.B_b *= 1e-4
+    D = UnrestrictedDFADC(s, 3, kind)
+    eps, no, _ = spin_orbital_df(s)
+    ref = np.sort(eps[no:])[:2] if kind == "ea" else np.sort(-eps[:no])[:2]
+    w, Y = dense_roots(D, 2)
+    assert np.abs(w - ref).max() < 1e-6
+    assert np.abs(D.spectroscopic_factors(Y) - 1.0).max() < 1e-6
+
+
+def test_spectroscopic_factors_match_tier1():
+    from oracle.unrestricted import UnrestrictedDFADC
+
+    s = make_open_shell_system(3, 2, 7, 20, seed=5)
+    D = UnrestrictedDFADC(s, 3, "ea")
+    eps, no, g = unrestricted_spin_orbitals(s.eps_a, s.eps_b, 3, 2, s.B_a, s.B_b)
+    S = SpinOrbitalADC.from_spin_orbitals(eps, no, g, 3)
+    T1, T2 = S.ea_transition()
+    _, two = S.basis_labels("ea")
+    I = np.array(two)
+    T = np.concatenate([T1, T2[:, I[:, 0], I[:, 1], I[:, 2]]], axis=1)
+    Y = np.random.default_rng(1).standard_normal((3, D.dim))
+    Yn = Y / np.linalg.norm(Y, axis=1)[:, None]
+    assert np.abs(D.spectroscopic_factors(Y) - ((Yn @ T.T) ** 2).sum(axis=1)).max() < 1e-13
