@@ -132,6 +132,23 @@ int adc_setup_batch(int nmol, const double* const* eps, const double* const* Bq,
  * contractions and aux_chunk stay as set up.  Errors: ADC_ERR_ARG. */
 int adc_set_options(adc_handle* h, const adc_options* opt);
 
+/*
+ * Set up an unrestricted (open-shell) reference for EA/IP-UADC(n) sigma
+ * products (the paper's UADC, Sec. II; FP64 only).  Spin orbitals are ordered
+ * occupied alpha, occupied beta, virtual alpha, virtual beta; with o = nocc_a +
+ * nocc_b and v = 2 nmo - o spin orbitals the vector is
+ *   EA  [Y_a (v) | Y_iab (i, a<b), i-major, pairs in lexicographic order]
+ *   IP  [Y_i (o) | Y_ija (i<j, a), a-major, pairs in lexicographic order]
+ * and adc_sigma applies M (EA) or -M_- (IP).  The two-electron integrals are
+ * (p_s q_s | r_t s_t) = sum_Q B^Q_{s,pq} B^Q_{t,rs} (Eq. 19 per spin pair).
+ *   eps_a, eps_b  host [nmo] alpha / beta orbital energies, occupied first
+ *   Ba, Bb        host [naux][nmo][nmo] alpha / beta DF factors, symmetric in pq
+ * adc_davidson and adc_mp_energy are not available on these handles yet.
+ * Errors: ADC_ERR_ARG, ADC_ERR_OOM, ADC_ERR_CUDA (message: adc_last_error(NULL)).
+ */
+int adc_setup_unrestricted(const double* eps_a, const double* eps_b, const double* Ba, const double* Bb, int nocc_a,
+                           int nocc_b, int nmo, int naux, int order, int kind, adc_handle** out);
+
 /* Length of the spin-adapted vector (see layout above). */
 int adc_dim(const adc_handle* h, long long* dim);
 

@@ -31,6 +31,7 @@ EXPORTED = [
     "adc_davidson",
     "adc_get_tensor",
     "adc_mp_energy",
+    "adc_setup_unrestricted",
     "adc_kernel_timing",
     "adc_ladder_noalloc",
     "adc_last_error",
@@ -86,6 +87,7 @@ def load_library():
     lib.adc_davidson.argtypes = [P, I, D, P, P, P, P, P]
     lib.adc_get_tensor.argtypes = [P, ctypes.c_char_p, P, LL]
     lib.adc_mp_energy.argtypes = [P, P, ctypes.c_int]
+    lib.adc_setup_unrestricted.argtypes = [P, P, P, P, I, I, I, I, I, I, ctypes.POINTER(P)]
     lib.adc_kernel_timing.argtypes = [P, I, P]
     lib.adc_ladder_noalloc.argtypes = [P, P, P, LL]
     lib.adc_spectrum.argtypes = [P, P, I, D, P, I, P]
@@ -373,3 +375,57 @@ def mlp_train(weights, d, blk, r, t, steps=500, lr=1e-3):
     if rc != ADC_OK:
         raise ADCError(rc, lib.adc_last_error(None).decode())
     return w, hist[:steps]
+
+
+class ADCUnrestricted:
+    """Unrestricted (open-shell) reference for EA/IP-UADC(n) sigma products (FP64).
+
+    eps_a, eps_b [nmo] and B_a, B_b [naux, nmo, nmo] are float64 numpy arrays
+    (alpha / beta orbitals, occupied first).  The vector layout is the one of
+    adc_setup_unrestricted: spin orbitals ordered occupied alpha, occupied
+    beta, virtual alpha, virtual beta; EA [1p | (i, a<b)], IP [1h | (i<j, a)].
+    """
+
+    def __init__(self, eps_a, eps_b, B_a, B_b, nocc_a, nocc_b, order=3, kind="ea"):
+        lib = load_library()
+        self._lib = lib
+        arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (eps_a, eps_b, B_a, B_b)]
+        naux, nmo = arrs[2].shape[0], arrs[2].shape[1]
+        self.order, self.kind = order, kind
+        h = ctypes.c_void_p()
+        rc = lib.adc_setup_unrestricted(*[a.ctypes.data for a in arrs], nocc_a, nocc_b, nmo, naux, order,
+                                        ADC_EA if kind == "ea" else ADC_IP, ctypes.byref(h))
+        if rc != ADC_OK:
+            raise ADCError(rc, lib.adc_last_error(None).decode())
+        self._h = h
+        d = ctypes.c_longlong()
+        lib.adc_dim(h, ctypes.byref(d))
+        self.dim = d.value
+
+    def _check(self, rc):
+        if rc != ADC_OK:
+            raise ADCError(rc, self._lib.adc_last_error(self._h).decode())
+
+    def sigma(self, X):
+        """sigma = M X (EA) or -M_- X (IP) for host X [nvec, dim]."""
+        X = np.ascontiguousarray(np.atleast_2d(X), dtype=np.float64)
+        assert X.shape[-1] == self.dim
+        S = np.empty_like(X)
+        self._check(self._lib.adc_sigma(self._h, X.ctypes.data, S.ctypes.data, X.shape[0], 0))
+        return S
+
+    def get(self, name, shape):
+        out = np.zeros(int(np.prod(shape)))
+        self._check(self._lib.adc_get_tensor(self._h, name.encode(), out.ctypes.data, out.size))
+        return out.reshape(shape)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.adc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

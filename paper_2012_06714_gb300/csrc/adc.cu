@@ -40,6 +40,12 @@ struct adc_handle {
     double *t = nullptr, *tau = nullptr, *t_2 = nullptr, *t1_2 = nullptr, *M11 = nullptr, *diag = nullptr;
     double* t1_3 = nullptr;  // third-order singles (ADC(3) transition moments only), made on first use
     double emp[2] = {0.0, 0.0};  // MP correlation energy E(2), E(3) (Sec. III A step 2)
+    // unrestricted (open-shell) reference: o, v count spin orbitals, the 2p1h / 2h1p basis
+    // holds the restricted pairs (i, a<b) / (i<j, a), and the <pq||rs> blocks are kept
+    bool unrestricted = false;
+    double *g_oovv = nullptr, *g_oooo = nullptr, *g_ooov = nullptr, *g_ovov = nullptr, *g_vovo = nullptr,
+           *g_vooo = nullptr, *m12 = nullptr;
+    int* pair_idx = nullptr;  // [3][npairs] (i, a, b) for EA, (i, j, a) for IP
     LadderTC* tc = nullptr;  // tensor-core ladder state (BF16x3 operands of B^Q_vv)
     // tensor-core ladder arithmetic: Davidson sigma, the setup ladder of t, and
     // the final refinement of converged roots
@@ -54,7 +60,11 @@ struct adc_handle {
     std::vector<void*> owned;
     cudaStream_t own_stream = nullptr;  // created by adc_setup_batch, destroyed with the handle
     std::string err;
+    long long npairs() const {
+        return kind == ADC_EA ? (long long)o * v * (v - 1) / 2 : (long long)o * (o - 1) / 2 * v;
+    }
     long long dim() const {
+        if (unrestricted) return n1() + npairs();
         return kind == ADC_EA ? (long long)v + (long long)o * v * v : (long long)o + (long long)o * o * v;
     }
     int n1() const { return kind == ADC_EA ? v : o; }
@@ -804,8 +814,14 @@ static void sigma_ip(adc_handle* h, const double* Xin, double* Sout, long long n
     launch_check(c);
 }
 
+static void sigma_unrestricted(adc_handle* h, const double* Xin, double* Sout, long long n);
+
 static void sigma_device(adc_handle* h, const double* X, double* S, long long nvec) {
     Ctx& c = h->ctx;
+    if (h->unrestricted) {
+        sigma_unrestricted(h, X, S, nvec);
+        return;
+    }
     if (!h->refining) c.gemm_mode = h->cmode_sigma;
     if (h->kind == ADC_EA)
         sigma_ea(h, X, S, nvec);
@@ -1348,6 +1364,356 @@ bool handle_ladder_view(adc_handle* h, LadderTC** tc, Ctx** c, int* nvir, std::s
 // --------------------------------------------------------------------------
 // C ABI
 // --------------------------------------------------------------------------
+// --------------------------------------------------------------------------
+// Unrestricted (open-shell) references: EA/IP-UADC(n) sigma (Sec. II, the
+// UADC runs of Sec. IV), FP64.  The spin orbitals are ordered occupied alpha,
+// occupied beta, virtual alpha, virtual beta; B^Q_PR is the per-spin DF factor
+// on the spin-diagonal blocks and zero between spins, so (PR|QS) = sum_Q
+// B^Q_PR B^Q_QS (Eq. 19 for each spin pair) and the ladder over its virtual
+// block is the alpha-alpha, beta-beta and alpha-beta ladder at once.  The
+// working equations are the spin-orbital ones (<pq||rs>, t antisymmetric);
+// every integral with three or four virtual indices goes through B^Q.  The
+// two-particle basis is (i, a<b) i-major (EA) and (i<j, a) a-major (IP);
+// IP applies -M_-, as the closed-shell path does.
+// --------------------------------------------------------------------------
+namespace {
+
+// F[r][i][a][b] = y, F[r][i][b][a] = -y (EA) / F[r][i][j][a] = y, F[r][j][i][a] = -y (IP)
+__global__ void k_pairs_to_full(int ea, long long n, long long np, int o, int v, const int* __restrict__ idx,
+                                const double* __restrict__ Y, long long ldy, long long off, double* __restrict__ F) {
+    const long long blk = ea ? (long long)o * v * v : (long long)o * o * v;
+    GRID_STRIDE(x, n * np) {
+        const long long r = x / np, q = x % np;
+        const int p0 = idx[q], p1 = idx[np + q], p2 = idx[2 * np + q];
+        const double y = Y[r * ldy + off + q];
+        if (ea) {
+            F[r * blk + ((long long)p0 * v + p1) * v + p2] = y;
+            F[r * blk + ((long long)p0 * v + p2) * v + p1] = -y;
+        } else {
+            F[r * blk + ((long long)p0 * o + p1) * v + p2] = y;
+            F[r * blk + ((long long)p1 * o + p0) * v + p2] = -y;
+        }
+    }
+}
+
+// S[r][off + q] = alpha * F[r][pair q]
+__global__ void k_full_to_pairs(int ea, long long n, long long np, int o, int v, const int* __restrict__ idx,
+                                const double* __restrict__ F, double alpha, double* __restrict__ S, long long lds, long long off) {
+    const long long blk = ea ? (long long)o * v * v : (long long)o * o * v;
+    GRID_STRIDE(x, n * np) {
+        const long long r = x / np, q = x % np;
+        const int p0 = idx[q], p1 = idx[np + q], p2 = idx[2 * np + q];
+        const long long e = ea ? ((long long)p0 * v + p1) * v + p2 : ((long long)p0 * o + p1) * v + p2;
+        S[r * lds + off + q] = alpha * F[r * blk + e];
+    }
+}
+
+// out = alpha * perm(in) + beta * out for a 4-index tensor
+void perm4(Ctx& c, const double* in, std::initializer_list<long long> d, std::initializer_list<int> p, double* out,
+           double alpha, double beta) {
+    Shape s{4, {0, 0, 0, 0}};
+    int k = 0;
+    for (long long x : d) s.d[k++] = x;
+    int pp[4];
+    k = 0;
+    for (int x : p) pp[k++] = x;
+    permute(c, in, s, pp, out, alpha, beta);
+}
+
+}  // namespace
+
+// M += alpha (X + X^T) for an n x n X
+static void sym_add_n(adc_handle* h, const double* X, double* M, long long n, double alpha) { sym_add(h, X, M, (int)n, alpha); }
+
+static void setup_unrestricted(adc_handle* h, const double* eps_so, const double* Bso) {
+    Ctx& c = h->ctx;
+    ADC_BLAS(cublasCreate(&c.blas));
+    ADC_BLAS(cublasSetStream(c.blas, c.stream));
+    ADC_BLAS(cublasSetMathMode(c.blas, CUBLAS_DEFAULT_MATH));
+    c.gemm_mode = 0;
+    h->cmode_setup = h->cmode_sigma = 0;
+    const long long o = h->o, v = h->v, Q = h->naux, nso = o + v;
+    const long long o2v2 = o * o * v * v;
+    h->eps = h->dmalloc(nso);
+    ADC_CUDA(cudaMemcpyAsync(h->eps, eps_so, nso * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    h->Boo = h->dmalloc(Q * o * o);
+    h->Bov = h->dmalloc(Q * o * v);
+    h->Bvv = h->dmalloc(Q * v * v);
+    for (long long q = 0; q < Q; ++q) {
+        const double* src = Bso + q * nso * nso;
+        ADC_CUDA(cudaMemcpy2DAsync(h->Boo + q * o * o, o * sizeof(double), src, nso * sizeof(double), o * sizeof(double), o,
+                                   cudaMemcpyHostToDevice, c.stream));
+        ADC_CUDA(cudaMemcpy2DAsync(h->Bov + q * o * v, v * sizeof(double), src + o, nso * sizeof(double), v * sizeof(double), o,
+                                   cudaMemcpyHostToDevice, c.stream));
+        ADC_CUDA(cudaMemcpy2DAsync(h->Bvv + q * v * v, v * sizeof(double), src + o * nso + o, nso * sizeof(double),
+                                   v * sizeof(double), v, cudaMemcpyHostToDevice, c.stream));
+    }
+    // pair basis
+    {
+        const long long np = h->npairs();
+        std::vector<int> idx((size_t)3 * np);
+        long long q = 0;
+        if (h->kind == ADC_EA) {
+            for (int i = 0; i < o; ++i)
+                for (int a = 0; a < v; ++a)
+                    for (int b = a + 1; b < v; ++b, ++q) idx[q] = i, idx[np + q] = a, idx[2 * np + q] = b;
+        } else {
+            for (int a = 0; a < v; ++a)
+                for (int i = 0; i < o; ++i)
+                    for (int j = i + 1; j < o; ++j, ++q) idx[q] = i, idx[np + q] = j, idx[2 * np + q] = a;
+        }
+        h->pair_idx = (int*)dev_alloc(std::max<size_t>(idx.size(), 1) * sizeof(int), c.stream);
+        h->owned.push_back(h->pair_idx);
+        if (!idx.empty())
+            ADC_CUDA(cudaMemcpyAsync(h->pair_idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice, c.stream));
+        ADC_CUDA(cudaStreamSynchronize(c.stream));  // idx is a host temporary
+    }
+    const T Boo = tn(h->Boo, {Q, o, o}), Bov = tn(h->Bov, {Q, o, v}), Bvv = tn(h->Bvv, {Q, v, v});
+    h->ovov = h->dmalloc(o2v2);
+    h->oovv = h->dmalloc(o2v2);
+    h->oooo = h->dmalloc(o * o * o * o);
+    h->ooov = h->dmalloc(o * o * o * v);
+    einsum(c, "Qia,Qjb->iajb", 1.0, Bov, Bov, 0.0, h->ovov, {o, v, o, v});
+    einsum(c, "Qij,Qab->ijab", 1.0, Boo, Bvv, 0.0, h->oovv, {o, o, v, v});
+    einsum(c, "Qij,Qkl->ijkl", 1.0, Boo, Boo, 0.0, h->oooo, {o, o, o, o});
+    einsum(c, "Qij,Qka->ijka", 1.0, Boo, Bov, 0.0, h->ooov, {o, o, o, v});
+    // antisymmetrised blocks with at most two virtual indices
+    h->g_oovv = h->dmalloc(o2v2);  // <ij||ab> = (ia|jb) - (ib|ja)
+    perm4(c, h->ovov, {o, v, o, v}, {0, 2, 1, 3}, h->g_oovv, 1.0, 0.0);
+    perm4(c, h->ovov, {o, v, o, v}, {0, 2, 3, 1}, h->g_oovv, -1.0, 1.0);
+    h->g_oooo = h->dmalloc(o * o * o * o);  // <ij||kl> = (ik|jl) - (il|jk)
+    perm4(c, h->oooo, {o, o, o, o}, {0, 2, 1, 3}, h->g_oooo, 1.0, 0.0);
+    perm4(c, h->oooo, {o, o, o, o}, {0, 2, 3, 1}, h->g_oooo, -1.0, 1.0);
+    h->g_ooov = h->dmalloc(o * o * o * v);  // <ij||ka> = (ik|ja) - (ia|jk)
+    perm4(c, h->ooov, {o, o, o, v}, {0, 2, 1, 3}, h->g_ooov, 1.0, 0.0);
+    perm4(c, h->ooov, {o, o, o, v}, {2, 0, 1, 3}, h->g_ooov, -1.0, 1.0);
+    h->g_ovov = h->dmalloc(o2v2);  // <ia||jb> = (ij|ab) - (ib|ja)
+    perm4(c, h->oovv, {o, o, v, v}, {0, 2, 1, 3}, h->g_ovov, 1.0, 0.0);
+    perm4(c, h->ovov, {o, v, o, v}, {0, 3, 2, 1}, h->g_ovov, -1.0, 1.0);
+    h->g_vovo = h->dmalloc(o2v2);  // <ai||bj> = (ab|ij) - (aj|ib)
+    perm4(c, h->oovv, {o, o, v, v}, {2, 0, 3, 1}, h->g_vovo, 1.0, 0.0);
+    perm4(c, h->ovov, {o, v, o, v}, {1, 2, 3, 0}, h->g_vovo, -1.0, 1.0);
+    h->g_vooo = h->dmalloc(o * o * o * v);  // <ai||jk> = (aj|ik) - (ak|ij)
+    perm4(c, h->ooov, {o, o, o, v}, {3, 0, 2, 1}, h->g_vooo, 1.0, 0.0);
+    perm4(c, h->ooov, {o, o, o, v}, {3, 0, 1, 2}, h->g_vooo, -1.0, 1.0);
+    // first-order doubles t_ij^ab = <ij||ab> / D_ij^ab
+    h->t = h->dmalloc(o2v2);
+    ADC_CUDA(cudaMemcpyAsync(h->t, h->g_oovv, o2v2 * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    k_div_D2<<<grid_for(o2v2), 256, 0, c.stream>>>((int)o, (int)v, h->eps, h->t);
+    launch_check(c);
+    const double* t = h->t;
+    const T T4 = tn(t, {o, o, v, v}), goovv = tn(h->g_oovv, {o, o, v, v});
+    Scope sc(c.arena);
+    if (h->order >= 3) {
+        // t2(2) = [sum (ac|bd) t_ij^cd + 1/2 <kl||ij> t_kl^ab + P(ij)P(ab) <kb||cj> t_ik^ac] / D
+        h->t_2 = h->dmalloc(o2v2);
+        double* N = h->t_2;
+        fill(c, o2v2, 0.0, N);
+        ladder(h, t, o * o, N, h->lm_setup);
+        einsum(c, "klij,klab->ijab", 0.5, tn(h->g_oooo, {o, o, o, o}), T4, 1.0, N, {o, o, v, v});
+        // <kb||cj> = <kb||cj> from g_ovvo[k,b,c,j] = (kc|jb) - (kj|bc)
+        double* gvo = c.arena.dalloc(o2v2);  // [k,b,c,j]
+        perm4(c, h->ovov, {o, v, o, v}, {0, 3, 1, 2}, gvo, 1.0, 0.0);
+        perm4(c, h->oovv, {o, o, v, v}, {0, 2, 3, 1}, gvo, -1.0, 1.0);
+        double* X = c.arena.dalloc(o2v2);
+        einsum(c, "kbcj,ikac->ijab", 1.0, tn(gvo, {o, v, v, o}), T4, 0.0, X, {o, o, v, v});
+        axpby(c, o2v2, 1.0, X, 1.0, N);
+        perm4(c, X, {o, o, v, v}, {1, 0, 2, 3}, N, -1.0, 1.0);
+        perm4(c, X, {o, o, v, v}, {0, 1, 3, 2}, N, -1.0, 1.0);
+        perm4(c, X, {o, o, v, v}, {1, 0, 3, 2}, N, 1.0, 1.0);
+        k_div_D2<<<grid_for(o2v2), 256, 0, c.stream>>>((int)o, (int)v, h->eps, N);
+        launch_check(c);
+        // t1(2) = [-(kc|ad) t_ik^cd - 1/2 <kl||ic> t_kl^ac] / D
+        h->t1_2 = h->dmalloc(o * v);
+        double* G = c.arena.dalloc(Q * o * v);
+        einsum(c, "Qkc,ikcd->Qid", 1.0, Bov, T4, 0.0, G, {Q, o, v});
+        einsum(c, "Qid,Qad->ia", -1.0, tn(G, {Q, o, v}), Bvv, 0.0, h->t1_2, {o, v});
+        einsum(c, "klic,klac->ia", -0.5, tn(h->g_ooov, {o, o, o, v}), T4, 1.0, h->t1_2, {o, v});
+        k_div_D1<<<grid_for(o * v), 256, 0, c.stream>>>((int)o, (int)v, h->eps, h->t1_2);
+        launch_check(c);
+    }
+    // one-particle block (EA: M_ab; IP: the paper's M_ij, negated when applied)
+    const long long n1 = h->n1();
+    h->M11 = h->dmalloc(n1 * n1);
+    {
+        std::vector<double> e0((size_t)n1 * n1, 0.0), eh(nso);
+        for (long long k = 0; k < nso; ++k) eh[k] = eps_so[k];
+        for (long long k = 0; k < n1; ++k) e0[k * n1 + k] = h->kind == ADC_EA ? eh[o + k] : eh[k];
+        ADC_CUDA(cudaMemcpyAsync(h->M11, e0.data(), e0.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+        ADC_CUDA(cudaStreamSynchronize(c.stream));
+    }
+    double* M = h->M11;
+    double* X = c.arena.dalloc(std::max(v * v, o * o));
+    const bool third = h->order >= 3;
+    if (h->kind == ADC_EA) {
+        einsum(c, "klac,klbc->ab", 1.0, T4, goovv, 0.0, X, {v, v});
+        sym_add_n(h, X, M, v, -0.25);
+        if (third) {
+            const T t1 = tn(h->t1_2, {o, v}), T2 = tn(h->t_2, {o, o, v, v});
+            // t_k^c <ka||cb>, <ka||cb> = (kc|ab) - (kb|ac)
+            double* r = c.arena.dalloc(Q);
+            einsum(c, "kc,Qkc->Q", 1.0, t1, Bov, 0.0, r, {Q});
+            einsum(c, "Q,Qab->ab", 1.0, tn(r, {Q}), Bvv, 0.0, X, {v, v});
+            double* Z = c.arena.dalloc(Q * v * v);
+            einsum(c, "kc,Qkb->Qbc", 1.0, t1, Bov, 0.0, Z, {Q, v, v});
+            einsum(c, "Qac,Qbc->ab", -1.0, Bvv, tn(Z, {Q, v, v}), 1.0, X, {v, v});
+            sym_add_n(h, X, M, v, 1.0);
+            einsum(c, "klac,klbc->ab", 1.0, T2, goovv, 0.0, X, {v, v});
+            sym_add_n(h, X, M, v, -0.25);
+            // t_kl^ac <bc||de> t_kl^de = 2 t_kl^ac (sum_Q B^Q t_kl B^Q)^bc
+            double* L = c.arena.dalloc(o2v2);
+            fill(c, o2v2, 0.0, L);
+            ladder(h, t, o * o, L, h->lm_setup);
+            einsum(c, "klac,klbc->ab", 2.0, T4, tn(L, {o, o, v, v}), 0.0, X, {v, v});
+            sym_add_n(h, X, M, v, -0.125);
+            // 1/2 <ac||bd> rho_cd, <ac||bd> = (ab|cd) - (ad|cb), rho_cd = t_kl^ce t_kl^de
+            double* rho = c.arena.dalloc(v * v);
+            einsum(c, "klce,klde->cd", 1.0, T4, T4, 0.0, rho, {v, v});
+            einsum(c, "Qcd,cd->Q", 1.0, Bvv, tn(rho, {v, v}), 0.0, r, {Q});
+            einsum(c, "Q,Qab->ab", 0.5, tn(r, {Q}), Bvv, 1.0, M, {v, v});
+            einsum(c, "Qad,cd->Qac", 1.0, Bvv, tn(rho, {v, v}), 0.0, Z, {Q, v, v});
+            einsum(c, "Qac,Qcb->ab", -0.5, tn(Z, {Q, v, v}), Bvv, 1.0, M, {v, v});
+            // ring terms with <kd||lb>
+            const T gov = tn(h->g_ovov, {o, v, o, v});
+            double* V1 = c.arena.dalloc(o2v2);  // [k,a,l,d]
+            einsum(c, "kmac,lmcd->kald", 1.0, T4, T4, 0.0, V1, {o, v, o, v});
+            einsum(c, "kald,kdlb->ab", 1.0, tn(V1, {o, v, o, v}), gov, 0.0, X, {v, v});
+            sym_add_n(h, X, M, v, -0.5);
+            double* u = c.arena.dalloc(o * o);
+            einsum(c, "kmcd,lmcd->kl", 1.0, T4, T4, 0.0, u, {o, o});
+            einsum(c, "kalb,kl->ab", -0.5, gov, tn(u, {o, o}), 1.0, M, {v, v});
+        }
+    } else {
+        einsum(c, "ilcd,jlcd->ij", 1.0, T4, goovv, 0.0, X, {o, o});
+        sym_add_n(h, X, M, o, 0.25);
+        if (third) {
+            const T t1 = tn(h->t1_2, {o, v}), T2 = tn(h->t_2, {o, o, v, v});
+            const T gvooo = tn(h->g_vooo, {v, o, o, o}), goooo = tn(h->g_oooo, {o, o, o, o});
+            einsum(c, "kc,cikj->ij", 1.0, t1, gvooo, 0.0, X, {o, o});
+            sym_add_n(h, X, M, o, 1.0);
+            einsum(c, "ikcd,jkcd->ij", 1.0, T2, goovv, 0.0, X, {o, o});
+            sym_add_n(h, X, M, o, 0.25);
+            double* Z = c.arena.dalloc(o * o * o * o);
+            einsum(c, "ikcd,lmcd->iklm", 1.0, T4, T4, 0.0, Z, {o, o, o, o});
+            einsum(c, "iklm,jklm->ij", 1.0, tn(Z, {o, o, o, o}), goooo, 0.0, X, {o, o});
+            sym_add_n(h, X, M, o, 0.125);
+            double* u = c.arena.dalloc(o * o);
+            einsum(c, "kmcd,lmcd->kl", 1.0, T4, T4, 0.0, u, {o, o});
+            einsum(c, "ikjl,kl->ij", -0.5, goooo, tn(u, {o, o}), 1.0, M, {o, o});
+            const T gvovo = tn(h->g_vovo, {v, o, v, o});
+            double* A = c.arena.dalloc(o2v2);  // [i,c,l,d]
+            einsum(c, "ikce,klde->icld", 1.0, T4, T4, 0.0, A, {o, v, o, v});
+            einsum(c, "icld,cldj->ij", 1.0, tn(A, {o, v, o, v}), gvovo, 0.0, X, {o, o});
+            sym_add_n(h, X, M, o, 0.5);
+            double* rho = c.arena.dalloc(v * v);
+            einsum(c, "klce,klde->cd", 1.0, T4, T4, 0.0, rho, {v, v});
+            einsum(c, "cidj,cd->ij", 0.5, gvovo, tn(rho, {v, v}), 1.0, M, {o, o});
+        }
+        // coupling M[i,j,k,a] = <jk||ia> (- 1/2 <ai||de> t_jk^de - (X - X^jk), X = <il||kc> t_jl^ac)
+        const long long o3v = o * o * o * v;
+        h->m12 = h->dmalloc(o3v);
+        perm4(c, h->g_ooov, {o, o, o, v}, {2, 0, 1, 3}, h->m12, 1.0, 0.0);
+        if (third) {
+            double* G = c.arena.dalloc(Q * o3v);  // [Q,i,j,k,d] = sum_e B^Q_ie t_jk^de
+            einsum(c, "Qie,jkde->Qijkd", 1.0, Bov, T4, 0.0, G, {Q, o, o, o, v});
+            einsum(c, "Qijkd,Qad->ijka", -1.0, tn(G, {Q, o, o, o, v}), Bvv, 1.0, h->m12, {o, o, o, v});
+            double* Xc = c.arena.dalloc(o3v);
+            einsum(c, "ilkc,jlac->ijka", 1.0, tn(h->g_ooov, {o, o, o, v}), T4, 0.0, Xc, {o, o, o, v});
+            axpby(c, o3v, -1.0, Xc, 1.0, h->m12);
+            perm4(c, Xc, {o, o, o, v}, {0, 2, 1, 3}, h->m12, 1.0, 1.0);
+        }
+    }
+    ADC_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+static void sigma_unrestricted(adc_handle* h, const double* Xin, double* Sout, long long n) {
+    Ctx& c = h->ctx;
+    c.gemm_mode = 0;
+    const long long o = h->o, v = h->v, Q = h->naux, dim = h->dim(), np = h->npairs(), n1 = h->n1();
+    const int ea = h->kind == ADC_EA;
+    const long long blk = ea ? o * v * v : o * o * v;
+    const bool third = h->order >= 3;
+    Scope sc(c.arena);
+    double* y1 = c.arena.dalloc(n * n1);
+    double* s1 = c.arena.dalloc(n * n1);
+    double* F = c.arena.dalloc(n * blk);
+    double* S2 = c.arena.dalloc(n * blk);
+    k_gather<<<grid_for(n * n1), 256, 0, c.stream>>>(n, n1, Xin, dim, 0, y1, n1, 0, 0.0);
+    launch_check(c);
+    fill(c, n * blk, 0.0, F);
+    k_pairs_to_full<<<grid_for(n * np), 256, 0, c.stream>>>(ea, n, np, (int)o, (int)v, h->pair_idx, Xin, dim, n1, F);
+    launch_check(c);
+    const T Bov = tn(h->Bov, {Q, o, v}), Bvv = tn(h->Bvv, {Q, v, v});
+    const T T4 = tn(h->t, {o, o, v, v});
+    if (ea) {
+        const T Y1 = tn(y1, {n, v}), F4 = tn(F, {n, o, v, v});
+        einsum(c, "nb,ab->na", 1.0, Y1, tn(h->M11, {v, v}), 0.0, s1, {n, v});
+        // coupling, first order: -<aj||cd>, <aj||cd> = (ac|jd) - (ad|jc)
+        double* W = c.arena.dalloc(n * Q * v);
+        einsum(c, "Qjd,njcd->nQc", 1.0, Bov, F4, 0.0, W, {n, Q, v});
+        einsum(c, "nQc,Qac->na", -1.0, tn(W, {n, Q, v}), Bvv, 1.0, s1, {n, v});
+        double* P = c.arena.dalloc(n * Q * v);
+        einsum(c, "na,Qac->nQc", 1.0, Y1, Bvv, 0.0, P, {n, Q, v});
+        einsum(c, "nQc,Qjd->njcd", -1.0, tn(P, {n, Q, v}), Bov, 0.0, S2, {n, o, v, v});
+        einsum(c, "nQd,Qjc->njcd", 1.0, tn(P, {n, Q, v}), Bov, 1.0, S2, {n, o, v, v});
+        if (third) {
+            const T gvooo = tn(h->g_vooo, {v, o, o, o});
+            // -1/2 <aj||lm> t_lm^cd
+            double* G = c.arena.dalloc(n * o * o * o);
+            einsum(c, "lmcd,njcd->njlm", 1.0, T4, F4, 0.0, G, {n, o, o, o});
+            einsum(c, "ajlm,njlm->na", -0.25, gvooo, tn(G, {n, o, o, o}), 1.0, s1, {n, v});
+            einsum(c, "na,ajlm->njlm", 1.0, Y1, gvooo, 0.0, G, {n, o, o, o});
+            einsum(c, "njlm,lmcd->njcd", -0.5, tn(G, {n, o, o, o}), T4, 1.0, S2, {n, o, v, v});
+            // -(X - X^cd), X[a,j,c,d] = <ae||cm> t_jm^de, <ae||cm> = (ac|em) - (am|ec)
+            double* H = c.arena.dalloc(n * o * v * v);  // [n,m,e,c]
+            einsum(c, "jmde,njcd->nmec", 1.0, T4, F4, 0.0, H, {n, o, v, v});
+            double* Hq = c.arena.dalloc(n * Q * std::max(o, v));
+            einsum(c, "Qme,nmec->nQc", 1.0, Bov, tn(H, {n, o, v, v}), 0.0, Hq, {n, Q, v});
+            einsum(c, "nQc,Qac->na", -1.0, tn(Hq, {n, Q, v}), Bvv, 1.0, s1, {n, v});
+            einsum(c, "Qec,nmec->nQm", 1.0, Bvv, tn(H, {n, o, v, v}), 0.0, Hq, {n, Q, o});
+            einsum(c, "nQm,Qma->na", 1.0, tn(Hq, {n, Q, o}), Bov, 1.0, s1, {n, v});
+            double* K = c.arena.dalloc(n * v * v * o);  // [n,e,c,m]
+            einsum(c, "nQc,Qme->necm", 1.0, tn(P, {n, Q, v}), Bov, 0.0, K, {n, v, v, o});
+            einsum(c, "na,Qma->nQm", 1.0, Y1, Bov, 0.0, Hq, {n, Q, o});
+            einsum(c, "nQm,Qec->necm", -1.0, tn(Hq, {n, Q, o}), Bvv, 1.0, K, {n, v, v, o});
+            double* Xc = c.arena.dalloc(n * blk);
+            einsum(c, "necm,jmde->njcd", 1.0, tn(K, {n, v, v, o}), T4, 0.0, Xc, {n, o, v, v});
+            axpby(c, n * blk, -1.0, Xc, 1.0, S2);
+            perm4(c, Xc, {n, o, v, v}, {0, 1, 3, 2}, S2, 1.0, 1.0);
+        }
+        k_diag22<<<grid_for(n * blk), 256, 0, c.stream>>>(1, (int)o, (int)v, n, h->eps, F, S2);
+        launch_check(c);
+        if (third) {
+            ladder(h, F, n * o, S2, h->lm_setup);
+            double* R = c.arena.dalloc(n * blk);
+            einsum(c, "ajci,njcb->niab", 1.0, tn(h->g_vovo, {v, o, v, o}), F4, 0.0, R, {n, o, v, v});
+            axpby(c, n * blk, -1.0, R, 1.0, S2);
+            perm4(c, R, {n, o, v, v}, {0, 1, 3, 2}, S2, 1.0, 1.0);
+        }
+    } else {
+        const T Y1 = tn(y1, {n, o}), F4 = tn(F, {n, o, o, v});
+        const T M12 = tn(h->m12, {o, o, o, v});
+        einsum(c, "nj,ij->ni", 1.0, Y1, tn(h->M11, {o, o}), 0.0, s1, {n, o});
+        einsum(c, "ijka,njka->ni", 0.5, M12, F4, 1.0, s1, {n, o});
+        einsum(c, "ijka,ni->njka", 1.0, M12, Y1, 0.0, S2, {n, o, o, v});
+        k_diag22<<<grid_for(n * blk), 256, 0, c.stream>>>(0, (int)o, (int)v, n, h->eps, F, S2);
+        launch_check(c);
+        if (third) {
+            einsum(c, "ijkl,nkla->nija", -0.5, tn(h->g_oooo, {o, o, o, o}), F4, 1.0, S2, {n, o, o, v});
+            double* R = c.arena.dalloc(n * blk);
+            einsum(c, "kaib,nkjb->nija", 1.0, tn(h->g_ovov, {o, v, o, v}), F4, 0.0, R, {n, o, o, v});
+            axpby(c, n * blk, 1.0, R, 1.0, S2);
+            perm4(c, R, {n, o, o, v}, {0, 2, 1, 3}, S2, -1.0, 1.0);
+        }
+    }
+    const double sign = ea ? 1.0 : -1.0;  // IP applies -M_-
+    if (!ea) axpby(c, n * n1, 0.0, s1, -1.0, s1);
+    k_gather<<<grid_for(n * n1), 256, 0, c.stream>>>(n, n1, s1, n1, 0, Sout, dim, 0, 0.0);
+    launch_check(c);
+    k_full_to_pairs<<<grid_for(n * np), 256, 0, c.stream>>>(ea, n, np, (int)o, (int)v, h->pair_idx, S2, sign, Sout, dim, n1);
+    launch_check(c);
+}
+
 #define GUARD(h, ...)                                    \
     try {                                                \
         __VA_ARGS__                                      \
@@ -1569,6 +1935,57 @@ int adc_setup_batch(int nmol, const double* const* eps, const double* const* Bq,
     return ADC_OK;
 }
 
+int adc_setup_unrestricted(const double* eps_a, const double* eps_b, const double* Ba, const double* Bb, int nocc_a,
+                           int nocc_b, int nmo, int naux, int order, int kind, adc_handle** out) {
+    if (!out) return ADC_ERR_ARG;
+    *out = nullptr;
+    const int no = nocc_a + nocc_b, nso = 2 * nmo, nv = nso - no;
+    const bool pairs_ok = kind == ADC_EA ? nv >= 2 : no >= 2;
+    if (!eps_a || !eps_b || !Ba || !Bb || nmo < 1 || nocc_a < 0 || nocc_b < 0 || nocc_a > nmo || nocc_b > nmo || no < 1 ||
+        nv < 1 || naux < 1 || (order != 2 && order != 3) || (kind != ADC_EA && kind != ADC_IP) || !pairs_ok) {
+        g_setup_error = "adc_setup_unrestricted: invalid argument";
+        return ADC_ERR_ARG;
+    }
+    // spin orbitals: occupied alpha, occupied beta, virtual alpha, virtual beta
+    std::vector<int> spin(nso), idx(nso);
+    int k = 0;
+    for (int p = 0; p < nocc_a; ++p, ++k) spin[k] = 0, idx[k] = p;
+    for (int p = 0; p < nocc_b; ++p, ++k) spin[k] = 1, idx[k] = p;
+    for (int p = nocc_a; p < nmo; ++p, ++k) spin[k] = 0, idx[k] = p;
+    for (int p = nocc_b; p < nmo; ++p, ++k) spin[k] = 1, idx[k] = p;
+    std::vector<double> eps_so(nso), Bso((size_t)naux * nso * nso, 0.0);
+    for (int P = 0; P < nso; ++P) eps_so[P] = spin[P] ? eps_b[idx[P]] : eps_a[idx[P]];
+    for (long long q = 0; q < naux; ++q)
+        for (int P = 0; P < nso; ++P)
+            for (int R = 0; R < nso; ++R)
+                if (spin[P] == spin[R]) {
+                    const double* B = spin[P] ? Bb : Ba;
+                    Bso[((size_t)q * nso + P) * nso + R] = B[((size_t)q * nmo + idx[P]) * nmo + idx[R]];
+                }
+    adc_handle* h = new adc_handle();
+    h->o = no;
+    h->v = nv;
+    h->naux = naux;
+    h->order = order;
+    h->kind = kind;
+    h->unrestricted = true;
+    adc_default_options(&h->opt);
+    try {
+        setup_unrestricted(h, eps_so.data(), Bso.data());
+    } catch (const adc::Error& e) {
+        g_setup_error = e.what();
+        const int code = e.code;
+        delete h;
+        return code;
+    } catch (const std::exception& e) {
+        g_setup_error = e.what();
+        delete h;
+        return ADC_ERR_CUDA;
+    }
+    *out = h;
+    return ADC_OK;
+}
+
 int adc_dim(const adc_handle* h, long long* dim) {
     if (!h || !dim) return ADC_ERR_ARG;
     *dim = h->dim();
@@ -1576,7 +1993,7 @@ int adc_dim(const adc_handle* h, long long* dim) {
 }
 
 int adc_mp_energy(const adc_handle* h, double* e, int n_out) {
-    if (!h || !e || n_out < 1) return ADC_ERR_ARG;
+    if (!h || !e || n_out < 1 || h->unrestricted) return ADC_ERR_ARG;
     const int n = std::min(n_out, h->order - 1);
     for (int k = 0; k < n; ++k) e[k] = h->emp[k];
     return ADC_OK;
@@ -1619,6 +2036,10 @@ int adc_sigma(adc_handle* h, const double* X, double* S, int nvec, int on_device
 int adc_davidson(adc_handle* h, int nroots, double tol, const double* guess, double* energies, double* specfac,
                  double* vectors, double* stats) {
     if (!h) return ADC_ERR_ARG;
+    if (h->unrestricted) {
+        h->err = "adc_davidson: handles of unrestricted references support adc_sigma only";
+        return ADC_ERR_ARG;
+    }
     if (nroots < 1 || !energies || !(tol > 0) || nroots > h->dim()) {
         h->err = "adc_davidson: invalid argument";
         return ADC_ERR_ARG;
@@ -1665,7 +2086,7 @@ int adc_get_tensor(adc_handle* h, const char* name, double* out, long long n) {
         } else if (s == "t1_2") {
             src = h->t1_2;
             cnt = o * v;
-        } else if (s == "t1_3") {
+        } else if (s == "t1_3" && !h->unrestricted) {
             make_t1_third_order(h);
             src = h->t1_3;
             cnt = o * v;

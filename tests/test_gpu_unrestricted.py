@@ -1,0 +1,58 @@
+"""GPU EA/IP-UADC(n) sigma (unrestricted open-shell references, FP64) against
+the density-fitted unrestricted oracle, element by element: amplitudes, the
+one-particle block and sigma = M Y on random vectors, for nocc_a != nocc_b and
+a case with ragged sizes."""
+import numpy as np
+import pytest
+
+from adc_inputs import make_open_shell_system
+
+pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CASES = [(3, 2, 7, 20, 5, 2.0), (5, 4, 23, 41, 2, 1.0)]  # nocc_a, nocc_b, nmo, naux, seed, B scale
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"a{c[0]}b{c[1]}n{c[2]}")
+@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("kind", ["ea", "ip"])
+def test_unrestricted_sigma_fp64(kind, order, case):
+    from oracle.unrestricted import UnrestrictedDFADC
+    from paper_2012_06714_gb300 import ADCUnrestricted
+
+    na, nb, nmo, naux, seed, scale = case
+    s = make_open_shell_system(na, nb, nmo, naux, seed=seed)
+    s.B_a *= scale
+    s.B_b *= scale
+    ref = UnrestrictedDFADC(s, order, kind)
+    gpu = ADCUnrestricted(s.eps_a, s.eps_b, s.B_a, s.B_b, na, nb, order=order, kind=kind)
+    assert gpu.dim == ref.dim
+    o, v = ref.no, ref.nv
+    assert np.abs(gpu.get("t2", (o, o, v, v)) - ref.t2_1).max() < 1e-13
+    if order == 3:
+        assert np.abs(gpu.get("t2_2", (o, o, v, v)) - ref.t2_2).max() < 1e-13
+        assert np.abs(gpu.get("t1_2", (o, v)) - ref.t1_2).max() < 1e-13
+    n1 = ref.n1
+    assert np.abs(gpu.get("M11", (n1, n1)) - ref.M11).max() < 1e-12
+    X = np.random.default_rng(3).standard_normal((3, gpu.dim))
+    Sg = gpu.sigma(X)
+    Sr = ref.sigma(X)
+    gpu.close()
+    assert np.abs(Sg - Sr).max() <= 1e-11 * np.abs(Sr).max()
+
+
+def test_unrestricted_argument_errors():
+    import ctypes
+
+    from paper_2012_06714_gb300 import ADCUnrestricted
+    from paper_2012_06714_gb300._lib import ADCError, load_library
+
+    s = make_open_shell_system(1, 0, 2, 4, seed=0)
+    with pytest.raises(ADCError):  # one occupied spin orbital: no 2h1p pair
+        ADCUnrestricted(s.eps_a, s.eps_b, s.B_a, s.B_b, 1, 0, kind="ip")
+    g = ADCUnrestricted(s.eps_a, s.eps_b, s.B_a, s.B_b, 1, 0, order=2, kind="ea")
+    L = load_library()
+    e = np.zeros(2)
+    assert L.adc_davidson(g._h, 1, 1e-6, None, e.ctypes.data, None, None, None) != 0
+    assert L.adc_mp_energy(g._h, e.ctypes.data, 2) != 0
+    g.close()
