@@ -143,7 +143,9 @@ int adc_set_options(adc_handle* h, const adc_options* opt);
  * (p_s q_s | r_t s_t) = sum_Q B^Q_{s,pq} B^Q_{t,rs} (Eq. 19 per spin pair).
  *   eps_a, eps_b  host [nmo] alpha / beta orbital energies, occupied first
  *   Ba, Bb        host [naux][nmo][nmo] alpha / beta DF factors, symmetric in pq
- * adc_davidson and adc_mp_energy are not available on these handles yet.
+ * adc_get_tensor returns "t2", "t2_2", "t1_2" and "M11" in these spin-orbital
+ * dimensions (M11: the paper's M_+ / M_- one-particle block).  adc_davidson and
+ * adc_mp_energy are not available on these handles yet.
  * Errors: ADC_ERR_ARG, ADC_ERR_OOM, ADC_ERR_CUDA (message: adc_last_error(NULL)).
  */
 int adc_setup_unrestricted(const double* eps_a, const double* eps_b, const double* Ba, const double* Bb, int nocc_a,
