@@ -27,7 +27,8 @@
  *       EA  M_+ (w = E_{N+1} - E_N; the paper's electron affinity is -w),
  *       IP  -M_- (w = E_{N-1} - E_N, the ionisation energy).
  *   - Spectroscopic factors use the Appendix normalisation (P = 2 sum_p X_p^2,
- *     so a Koopmans state has P = 2), with T through second order.
+ *     so a Koopmans state has P = 2), with T through the method's order n
+ *     (transition_order selects second order also for ADC(3)).
  *
  * Ownership: all inputs are caller-owned and copied; the handle owns every
  * device allocation it makes and releases it in adc_destroy.  Pointers marked
@@ -53,7 +54,13 @@ extern "C" {
 #define ADC_ERR_CUDA (-3)           /* CUDA runtime / cuBLAS failure          */
 #define ADC_ERR_NOT_CONVERGED (-4)  /* Davidson hit max_iter; outputs filled  */
                                     /* with the best estimates                */
-#define ADC_ERR_TIMEOUT (-5)        /* a bounded device wait gave up          */
+#define ADC_ERR_TIMEOUT (-5)        /* a bounded device wait gave up; the     */
+                                    /* kernel returned and the handle stays   */
+                                    /* usable (the device flag is cleared at  */
+                                    /* the start of the next call)            */
+#define ADC_ERR_NONFINITE (-6)      /* a non-finite value: in a guess vector, */
+                                    /* or a Ritz value / residual (non-finite */
+                                    /* sigma, e.g. from non-finite inputs)    */
 
 #define ADC_EA 1
 #define ADC_IP (-1)
@@ -191,7 +198,11 @@ int adc_sigma(adc_handle* h, const double* X, double* S, int nvec, int on_device
  *             final refinement, refinement seconds, roots that fell back from
  *             the learned to the diagonal preconditioner}; with refinement the
  *             residual is that of the refined pairs under the accurate sigma
- * Errors: ADC_ERR_ARG, ADC_ERR_OOM, ADC_ERR_CUDA, ADC_ERR_NOT_CONVERGED.
+ * Errors: ADC_ERR_ARG, ADC_ERR_OOM, ADC_ERR_CUDA, ADC_ERR_TIMEOUT,
+ * ADC_ERR_NONFINITE (non-finite guess element, or a non-finite Ritz value or
+ * residual), ADC_ERR_NOT_CONVERGED (max_iter reached, or no correction vector
+ * survived orthonormalisation while roots were unconverged; energies,
+ * specfac, vectors and stats are still filled with the best estimates).
  */
 int adc_davidson(adc_handle* h, int nroots, double tol, const double* guess, double* energies, double* specfac,
                  double* vectors, double* stats);
@@ -244,15 +255,17 @@ int adc_kernel_timing(adc_handle* h, int enable, double* out);
  * memory during the call (a host framework that owns all device memory and
  * forbids cudaMalloc/cudaFree inside library calls, which may synchronise the
  * device).  It allocates nothing: its intermediates live in a fixed 64 MiB
- * device array that every GPU loading this library holds until process exit.
+ * device array.  The setup of a BF16X3 handle looks up that array's device
+ * address on its device (once per device, with that device current), which
+ * loads the array with its module; the GPU then holds the 64 MiB until process
+ * exit, and this call performs no lookup or module load of its own.
  *   h    handle set up with precision ADC_PREC_BF16X3 (uses its split B^Q)
  *   X    device [nmat][nvir][nvir] FP64;  out  device [nmat][nvir][nvir] FP64,
  *        overwritten; X and out must not overlap
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls share the one array and it keeps the last call's
- * contents: calls that overlap on the GPU (other streams, other threads) race.
- * Work runs on the handle's stream and has completed when the call returns.
+ * All calls share the one array and it keeps the last call's contents: calls
+ * that overlap on the GPU (other streams, other threads) race.  Work runs on
+ * the handle's stream; before returning, the call reads the kernels' timeout
+ * flag back to the host and synchronises that stream.
  * Errors: ADC_ERR_ARG (NULL pointers, nmat < 0, handle not BF16X3, or nvir so
  * large that one matrix and one auxiliary function exceed the 64 MiB),
  * ADC_ERR_CUDA, ADC_ERR_TIMEOUT.

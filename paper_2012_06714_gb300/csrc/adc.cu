@@ -30,6 +30,10 @@
 
 using namespace adc;
 
+namespace adc {
+void noalloc_prepare();  // ladder_static.cu: resolve the allocation-free ladder's scratch on this device
+}
+
 struct adc_handle {
     int o = 0, v = 0, naux = 0, order = 3, kind = ADC_EA;
     adc_options opt{};
@@ -558,8 +562,10 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
                                        c.stream));
         }
     }
-    if (h->opt.precision != ADC_PREC_FP64)
+    if (h->opt.precision != ADC_PREC_FP64) {
         h->tc = ladder_tc_create(c, h->Bvv, (int)Q, (int)v, h->opt.aux_chunk);
+        noalloc_prepare();  // the allocation-free ladder's scratch address on this device, resolved up front
+    }
     // integrals (Eq. 19)
     h->ovov = h->dmalloc(o * v * o * v);
     h->oovv = h->dmalloc(o * o * v * v);
@@ -823,6 +829,8 @@ static void sigma_device(adc_handle* h, const double* X, double* S, long long nv
         return;
     }
     if (!h->refining) c.gemm_mode = h->cmode_sigma;
+    // a timeout of an earlier call left the flag raised; every call starts clean
+    if (c.d_err) ADC_CUDA(cudaMemsetAsync(c.d_err, 0, sizeof(int), c.stream));
     if (h->kind == ADC_EA)
         sigma_ea(h, X, S, nvec);
     else
@@ -1023,6 +1031,8 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
     double* wd = c.arena.dalloc(nroots);
     // guesses
     if (guess) {
+        for (long long x = 0; x < (long long)nroots * dim; ++x)
+            if (!std::isfinite(guess[x])) throw Error(ADC_ERR_NONFINITE, "davidson: non-finite element in the guess vectors");
         ADC_CUDA(cudaMemcpyAsync(d.V, guess, (size_t)nroots * dim * sizeof(double), cudaMemcpyHostToDevice, c.stream));
     } else {
         std::vector<double> D(dim);
@@ -1030,8 +1040,11 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
         ADC_CUDA(cudaStreamSynchronize(c.stream));
         std::vector<long long> idx(dim);
         std::iota(idx.begin(), idx.end(), 0LL);
+        // ascending diagonal, ties by index; a non-finite element sorts last (keeps the order strict)
+        auto key = [&](long long x) { return std::isfinite(D[x]) ? D[x] : INFINITY; };
         std::partial_sort(idx.begin(), idx.begin() + nstart, idx.end(), [&](long long a, long long b) {
-            return D[a] < D[b] || (D[a] == D[b] && a < b);
+            const double ka = key(a), kb = key(b);
+            return ka < kb || (ka == kb && a < b);
         });
         fill(c, (long long)nstart * dim, 0.0, d.V);
         long long* di = (long long*)c.arena.alloc(nstart * sizeof(long long));
@@ -1078,7 +1091,8 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
         for (int r = 0; r < nroots; ++r) {
             rn[r] = std::sqrt(std::max(rr[r], 0.0));
             bool cv = std::fabs(w[r] - wold[r]) <= tol && rn[r] <= rtol;
-            if (!std::isfinite(w[r]) || !std::isfinite(rn[r])) throw Error(ADC_ERR_CUDA, "davidson: non-finite residual");
+            if (!std::isfinite(w[r]) || !std::isfinite(rn[r]))
+                throw Error(ADC_ERR_NONFINITE, "davidson: non-finite Ritz value or residual (non-finite sigma)");
             if (!cv) {
                 all = false;
                 todo.push_back(r);
@@ -1126,16 +1140,24 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
         ADC_CUDA(cudaMemcpyAsync(wd, wt.data(), nnew * sizeof(double), cudaMemcpyHostToDevice, c.stream));
         for (int j = 0; j < nnew; ++j) {
             double* dst = d.V + (long long)(d.k + j) * dim;
-            if (diag_only[todo[j]]) {
-                k_precond<<<grid_for(dim), 256, 0, c.stream>>>(1, dim, SR + (long long)j * dim, wd + j, h->diag, dst);
-                launch_check(c);
-            } else {
+            if (!diag_only[todo[j]]) {
                 mlp_precondition(c, 1, dim, h->n1(), SR + (long long)j * dim, wd + j, h->diag, h->mlp_w, dst);
+                // a non-finite learned correction (bad weights) falls back to the diagonal one at once
+                double nrm2 = 0.0;
+                multidot(c, 1, dst, dim, 1, dst, dim, dim, Cd);
+                ADC_CUDA(cudaMemcpyAsync(&nrm2, Cd, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+                ADC_CUDA(cudaStreamSynchronize(c.stream));
+                if (std::isfinite(nrm2)) continue;
+                diag_only[todo[j]] = 1;
             }
+            k_precond<<<grid_for(dim), 256, 0, c.stream>>>(1, dim, SR + (long long)j * dim, wd + j, h->diag, dst);
+            launch_check(c);
         }
         int kept = d.orthonormalise(d.k, nnew);
         if (kept == 0) {
-            status = ADC_OK;
+            // no correction survives orthonormalisation while roots are unconverged: the space
+            // cannot grow, so the run stops with its best estimates and says so
+            status = ADC_ERR_NOT_CONVERGED;
             break;
         }
         d.sigma(d.k, kept);

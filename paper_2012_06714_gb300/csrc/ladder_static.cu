@@ -6,8 +6,11 @@
 // device and fragment a pool that the caller sizes up front), or code that runs
 // on a thread where the caller has promised not to enter the CUDA allocator.
 // For them this entry point computes the ladder with no allocation at all: its
-// scratch is the fixed array below, which every GPU that loads this library
-// holds from module load until process exit.
+// scratch is the fixed array below.  The array belongs to this file's device
+// module, which CUDA loads (lazily) when its symbol address is first looked
+// up; setup of a BF16X3 handle does that on its device (noalloc_prepare),
+// so the entry point itself never triggers the module load, and the GPU holds
+// the 64 MiB from then until process exit.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -52,6 +55,15 @@ cudaError_t scratch_address(void** out) {
 }
 
 }  // namespace
+
+namespace adc {
+// Resolve the scratch array's device address on the current device (loading
+// this module); called by the setup of every BF16X3 handle.
+void noalloc_prepare() {
+    void* p = nullptr;
+    ADC_CUDA(scratch_address(&p));
+}
+}  // namespace adc
 
 extern "C" int adc_ladder_noalloc(adc_handle* h, const double* X, double* out, long long nmat) {
     using namespace adc;

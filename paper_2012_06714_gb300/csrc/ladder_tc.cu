@@ -1242,6 +1242,7 @@ void ladder_tc_apply(LadderTC& L, Ctx& c, const double* X, long long nmat, doubl
     if (planes != 2 && planes != 3) throw Error(-1, "ladder: planes must be 2 or 3");
     if (md.epoch1 < 0 || md.epoch2 < 0) throw Error(-1, "ladder: negative epoch length");
     if (planes > L.nplanes) split_B(L, c, planes);  // the third plane only when first asked for
+    ADC_CUDA(cudaMemsetAsync(L.d_err, 0, sizeof(int), c.stream));  // clear a timeout of an earlier call
     // Scratch budget for Z (all planes): ~4 GiB.  Matrices are processed in
     // groups small enough that a chunk holds >= 8 auxiliary functions (long K
     // in GEMM2, fewer FP64 read-modify-write passes over the output); with
@@ -1293,6 +1294,7 @@ bool ladder_tc_apply_scratch(LadderTC& L, Ctx& c, const double* X, long long nma
     xt.p[1] = xt.p[0] + mg * vp * vp;
     zt.p[0] = (__nv_bfloat16*)(base + round256(mg * per_xt));
     zt.p[1] = zt.p[0] + mg * v * (long long)qc * vp;
+    ADC_CUDA(cudaMemsetAsync(L.d_err, 0, sizeof(int), c.stream));  // clear a timeout of an earlier call
     ADC_CUDA(cudaMemsetAsync(out, 0, (size_t)nmat * v * v * sizeof(double), c.stream));
     run_ladder(L, c, X, nmat, out, md, xt, zt, mg, qc);
     check_err(L, c);

@@ -28,10 +28,17 @@ def _vv_only_system(o, v, naux, seed):
     return s.eps, B
 
 
-def test_noalloc_ladder_matches_sigma_twice():
+# (nocc, nvir, naux, nvec): the first fits in one group of matrices and one auxiliary chunk;
+# in the second (12 matrices of 400 x 400) the 64 MiB holds 11 matrices' split X^T and Z,
+# so the matrices run in two groups and the 100 auxiliary functions in 13 chunks of 8.
+CASES = [(3, 70, 61, 2), (4, 400, 100, 3)]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"o{c[0]}v{c[1]}Q{c[2]}n{c[3]}")
+def test_noalloc_ladder_matches_sigma_twice(case):
     from paper_2012_06714_gb300 import ADC
 
-    o, v, naux, nvec = 3, 70, 61, 2
+    o, v, naux, nvec = case
     eps, B = _vv_only_system(o, v, naux, 4)
     gpu = ADC(eps, B, o, order=3, kind="ea", precision="bf16x3")
     dim = gpu.dim
