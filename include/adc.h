@@ -101,6 +101,12 @@ typedef struct {
     int transition_order;    /* order of T in the spectroscopic amplitudes (Eqs.      */
                              /* T_ea, T_ip): 0 (default) = n, the method's order;     */
                              /* 2 = second order also for ADC(3) (no t1(3), no t2(2)) */
+    double refine_res_tol;   /* BF16X3 with refine >= 1: > 0 continues the Davidson   */
+                             /* from the converged roots with the accurate operator   */
+                             /* (the refine arithmetic) until the S-norm residual is  */
+                             /* below this value (vectors and spectroscopic factors   */
+                             /* converged under that operator); 0 (default): one      */
+                             /* Rayleigh-Ritz step in the span of the converged roots */
 } adc_options;
 
 /* Fill *opt with the defaults listed above.  Returns ADC_OK or ADC_ERR_ARG (NULL). */
@@ -135,7 +141,8 @@ int adc_setup_batch(int nmol, const double* const* eps, const double* const* Bq,
                     const int* naux, int order, int kind, const adc_options* opt, int on_device, adc_handle** out);
 
 /* Replace the solver options of a handle (max_space_per_root, max_iter,
- * nguess_extra, res_tol, keep_per_root, refine, transition_order); precision,
+ * nguess_extra, res_tol, keep_per_root, refine, transition_order,
+ * refine_res_tol); precision,
  * contractions and aux_chunk stay as set up.  Errors: ADC_ERR_ARG. */
 int adc_set_options(adc_handle* h, const adc_options* opt);
 
@@ -150,13 +157,16 @@ int adc_set_options(adc_handle* h, const adc_options* opt);
  * (p_s q_s | r_t s_t) = sum_Q B^Q_{s,pq} B^Q_{t,rs} (Eq. 19 per spin pair).
  *   eps_a, eps_b  host [nmo] alpha / beta orbital energies, occupied first
  *   Ba, Bb        host [naux][nmo][nmo] alpha / beta DF factors, symmetric in pq
+ * aux_chunk: auxiliary functions per chunk of the IP third-order coupling
+ * intermediate sum_e B^Q_ie t_jk^de (naux x o^3 x v); 0 = automatic (chunks of
+ * at most 2^27 elements).
  * adc_get_tensor returns "t2", "t2_2", "t1_2" and "M11" in these spin-orbital
  * dimensions (M11: the paper's M_+ / M_- one-particle block).  adc_davidson and
  * adc_mp_energy are not available on these handles yet.
  * Errors: ADC_ERR_ARG, ADC_ERR_OOM, ADC_ERR_CUDA (message: adc_last_error(NULL)).
  */
 int adc_setup_unrestricted(const double* eps_a, const double* eps_b, const double* Ba, const double* Bb, int nocc_a,
-                           int nocc_b, int nmo, int naux, int order, int kind, adc_handle** out);
+                           int nocc_b, int nmo, int naux, int order, int kind, int aux_chunk, adc_handle** out);
 
 /* Length of the spin-adapted vector (see layout above). */
 int adc_dim(const adc_handle* h, long long* dim);
@@ -311,6 +321,29 @@ int adc_mlp_loss_grad(const float* weights, const double* d, const unsigned char
 int adc_mlp_train(float* weights, const double* d, const unsigned char* blk, const double* r, const double* t, long long n,
                   int steps, float lr, double* loss_hist);
 int adc_set_mlp(adc_handle* h, const float* weights);
+
+/*
+ * Training samples for the learned preconditioner from this handle's own plain
+ * Davidson (closed-shell handles).  The roots are first converged tightly (to
+ * exact_tol on the energies, S-norm residual 1e-6 or the handle's res_tol if
+ * smaller); then for each k = iters[0 .. n_iters) the solver is stopped after k
+ * iterations, and for each of the nroots iterates y (Ritz value w) the library
+ * forms on the device the residual r = sigma(y) - w y and the exact correction
+ * t = y_exact / <y_exact, y>_S - y, y_exact the converged root of largest
+ * S-overlap (S = diag(1, 2 - P), Appendix norm).  Each sample is one element x:
+ * d = D_x - w, blk = [x in the 1p/1h block], r_x, t_x; per (k, root) the samples
+ * are every 1p/1h element followed by min(per_vector, dim - n1) distinct
+ * 2p1h/2h1p elements drawn by a splitmix64 stream seeded by `seed`.
+ * Host outputs d, r, t (double) and blk (bytes) of length n >= adc_mlp_nsamples;
+ * the handle's solver options are restored on return.
+ * adc_mlp_nsamples returns that count (n_iters * nroots * (n1 + min(per_vector,
+ * dim - n1))), or -1 for invalid arguments.
+ * Errors: ADC_ERR_ARG, ADC_ERR_OOM, ADC_ERR_CUDA, ADC_ERR_NONFINITE.
+ */
+long long adc_mlp_nsamples(const adc_handle* h, int nroots, int n_iters, long long per_vector);
+int adc_mlp_samples(adc_handle* h, int nroots, const int* iters, int n_iters, long long per_vector,
+                    unsigned long long seed, double exact_tol, double* d, unsigned char* blk, double* r, double* t,
+                    long long n);
 
 /* Message of the last error on this handle (or of the last failed adc_setup
  * when h is NULL).  Never NULL. */

@@ -20,6 +20,8 @@ EXPORTED = [
     "adc_mlp_loss_grad",
     "adc_mlp_train",
     "adc_set_mlp",
+    "adc_mlp_nsamples",
+    "adc_mlp_samples",
     "adc_spectrum",
     "adc_setup_batch",
     "adc_davidson_batch",
@@ -51,6 +53,7 @@ class Options(ctypes.Structure):
         ("contractions", ctypes.c_int),
         ("refine", ctypes.c_int),
         ("transition_order", ctypes.c_int),
+        ("refine_res_tol", ctypes.c_double),
     ]
 
 
@@ -87,7 +90,7 @@ def load_library():
     lib.adc_davidson.argtypes = [P, I, D, P, P, P, P, P]
     lib.adc_get_tensor.argtypes = [P, ctypes.c_char_p, P, LL]
     lib.adc_mp_energy.argtypes = [P, P, ctypes.c_int]
-    lib.adc_setup_unrestricted.argtypes = [P, P, P, P, I, I, I, I, I, I, ctypes.POINTER(P)]
+    lib.adc_setup_unrestricted.argtypes = [P, P, P, P, I, I, I, I, I, I, I, ctypes.POINTER(P)]
     lib.adc_kernel_timing.argtypes = [P, I, P]
     lib.adc_ladder_noalloc.argtypes = [P, P, P, LL]
     lib.adc_spectrum.argtypes = [P, P, I, D, P, I, P]
@@ -95,6 +98,9 @@ def load_library():
     lib.adc_mlp_loss_grad.argtypes = [P, P, P, P, P, LL, P, P]
     lib.adc_mlp_train.argtypes = [P, P, P, P, P, LL, I, ctypes.c_float, P]
     lib.adc_set_mlp.argtypes = [P, P]
+    lib.adc_mlp_nsamples.argtypes = [P, I, I, LL]
+    lib.adc_mlp_nsamples.restype = LL
+    lib.adc_mlp_samples.argtypes = [P, I, P, I, LL, ctypes.c_ulonglong, D, P, P, P, P, LL]
     lib.adc_set_options.argtypes = [P, ctypes.POINTER(Options)]
     lib.adc_setup_batch.argtypes = [I, P, P, P, P, P, I, I, ctypes.POINTER(Options), I, P]
     lib.adc_davidson_batch.argtypes = [P, I, I, D, P, P, P, P]
@@ -140,7 +146,7 @@ class ADC:
 
     def __init__(self, eps, B, nocc, order=3, kind="ea", precision="fp64", max_space_per_root=8, max_iter=100,
                  nguess_extra=2, res_tol=0.0, aux_chunk=0, keep_per_root=2, contractions=-1, refine=1,
-                 transition_order=0):
+                 transition_order=0, refine_res_tol=0.0):
         lib = load_library()
         self._lib = lib
         opt = Options()
@@ -155,9 +161,10 @@ class ADC:
         opt.contractions = contractions
         opt.refine = refine
         opt.transition_order = transition_order
+        opt.refine_res_tol = refine_res_tol
         self._solver = dict(max_space_per_root=max_space_per_root, max_iter=max_iter, nguess_extra=nguess_extra,
                             res_tol=res_tol, keep_per_root=keep_per_root, refine=refine,
-                            transition_order=transition_order)
+                            transition_order=transition_order, refine_res_tol=refine_res_tol)
         if isinstance(eps, np.ndarray):
             eps = np.ascontiguousarray(eps, dtype=np.float64)
             B = np.ascontiguousarray(B, dtype=np.float64)
@@ -218,11 +225,11 @@ class ADC:
 
     def set_options(self, **kw):
         """Change solver options (max_space_per_root, max_iter, nguess_extra, res_tol, keep_per_root, refine,
-        transition_order)."""
+        transition_order, refine_res_tol)."""
         opt = Options()
         self._lib.adc_default_options(ctypes.byref(opt))
         for k in ("max_space_per_root", "max_iter", "nguess_extra", "res_tol", "keep_per_root", "refine",
-                  "transition_order"):
+                  "transition_order", "refine_res_tol"):
             setattr(opt, k, kw.pop(k, self._solver[k]))
         if kw:
             raise TypeError(f"not a solver option: {sorted(kw)}")
@@ -236,6 +243,18 @@ class ADC:
         else:
             w = np.ascontiguousarray(weights, dtype=np.float32)
             self._check(self._lib.adc_set_mlp(self._h, w.ctypes.data))
+
+    def mlp_samples(self, nroots, iters=(1, 2, 3, 4, 6, 8, 10, 14), per_vector=100_000, seed=0, exact_tol=1e-10):
+        """(d, blk, r, t) training samples of the learned preconditioner (adc_mlp_samples)."""
+        it = np.ascontiguousarray(iters, dtype=np.int32)
+        n = self._lib.adc_mlp_nsamples(self._h, nroots, it.size, per_vector)
+        if n < 0:
+            raise ADCError(ADC_ERR_ARG, "adc_mlp_nsamples: invalid argument")
+        d, r, t = np.zeros(n), np.zeros(n), np.zeros(n)
+        blk = np.zeros(n, dtype=np.uint8)
+        self._check(self._lib.adc_mlp_samples(self._h, nroots, it.ctypes.data, it.size, per_vector, seed, exact_tol,
+                                              d.ctypes.data, blk.ctypes.data, r.ctypes.data, t.ctypes.data, n))
+        return d, blk, r, t
 
     def mp_energy(self):
         """MP correlation energies (E(2),) for ADC(2) or (E(2), E(3)) for ADC(3), Eh."""
@@ -386,7 +405,7 @@ class ADCUnrestricted:
     beta, virtual alpha, virtual beta; EA [1p | (i, a<b)], IP [1h | (i<j, a)].
     """
 
-    def __init__(self, eps_a, eps_b, B_a, B_b, nocc_a, nocc_b, order=3, kind="ea"):
+    def __init__(self, eps_a, eps_b, B_a, B_b, nocc_a, nocc_b, order=3, kind="ea", aux_chunk=0):
         lib = load_library()
         self._lib = lib
         arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (eps_a, eps_b, B_a, B_b)]
@@ -394,7 +413,7 @@ class ADCUnrestricted:
         self.order, self.kind = order, kind
         h = ctypes.c_void_p()
         rc = lib.adc_setup_unrestricted(*[a.ctypes.data for a in arrs], nocc_a, nocc_b, nmo, naux, order,
-                                        ADC_EA if kind == "ea" else ADC_IP, ctypes.byref(h))
+                                        ADC_EA if kind == "ea" else ADC_IP, aux_chunk, ctypes.byref(h))
         if rc != ADC_OK:
             raise ADCError(rc, lib.adc_last_error(None).decode())
         self._h = h

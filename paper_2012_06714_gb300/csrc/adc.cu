@@ -21,6 +21,7 @@
 #include <vector>
 #include <atomic>
 #include <thread>
+#include <unordered_set>
 
 #include "../../include/adc.h"
 #include "common.cuh"
@@ -225,6 +226,21 @@ __global__ void k_precond(long long nr, long long dim, const double* __restrict_
 __global__ void k_units(int n, const long long* __restrict__ idx, long long dim, double* __restrict__ V) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n) V[(long long)k * dim + idx[k]] = 1.0;
+}
+
+// learned-preconditioner samples of one root: for each chosen element x = idx[k],
+// d = D_x - w, blk = [x in the 1p/1h block], r = sigma_x - w y_x, t = y_exact_x / ov - y_x
+__global__ void k_mlp_samples(long long m, const long long* __restrict__ idx, long long n1, const double* __restrict__ D,
+                              double w, const double* __restrict__ sig, const double* __restrict__ y,
+                              const double* __restrict__ yex, double inv_ov, double* __restrict__ od,
+                              unsigned char* __restrict__ ob, double* __restrict__ orr, double* __restrict__ ot) {
+    GRID_STRIDE(k, m) {
+        const long long x = idx[k];
+        od[k] = D[x] - w;
+        ob[k] = x < n1 ? 1 : 0;
+        orr[k] = sig[x] - w * y[x];
+        ot[k] = yex[x] * inv_ov - y[x];
+    }
 }
 
 void launch_check(Ctx& c) {
@@ -656,10 +672,17 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
         ADC_CUDA(cudaMemcpyAsync(h->M11, m0.data(), n1 * n1 * sizeof(double), cudaMemcpyHostToDevice, c.stream));
         ADC_CUDA(cudaStreamSynchronize(c.stream));
     }
-    if (h->kind == ADC_EA)
+    if (h->kind == ADC_EA) {
         setup_m11_ea(h);
-    else
+    } else {
+        // The 1h-1h block's contractions run in FP64 in every precision: on strongly correlated
+        // inputs its third-order terms cancel to a small fraction of their parts, and FP32-accurate
+        // contractions there moved the IP roots by ~1e-6 Eh.  Its costliest terms are o^3 v^3.
+        const int saved = c.gemm_mode;
+        c.gemm_mode = 0;
         setup_m11_ip(h);
+        c.gemm_mode = saved;
+    }
     h->Lt = nullptr;
     h->diag = h->dmalloc(h->dim());
     k_diag<<<grid_for(h->dim()), 256, 0, c.stream>>>(h->kind == ADC_EA, (int)o, (int)v, h->eps, h->M11, h->diag);
@@ -1063,6 +1086,34 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
     std::vector<int> stall(nroots, 0), diag_only(nroots, h->mlp_w ? 0 : 1);
     int it = 0, status = ADC_ERR_NOT_CONVERGED;
     int maxit = std::max(1, h->opt.max_iter);
+    // Refinement phase (mixed precision, refine >= 1 and refine_res_tol > 0): once the fast
+    // operator has converged, the Davidson continues from its Ritz vectors with the accurate
+    // one (lm_refine ladder; other contractions FP32-accurate for refine = 1, FP64 for
+    // refine = 2) until the residual is below refine_res_tol.  That converges the vectors,
+    // not just the energies, under the accurate operator (the spectroscopic factors are
+    // linear in the vector error).
+    const bool polish = h->opt.precision != ADC_PREC_FP64 && h->opt.refine > 0 && h->opt.refine_res_tol > 0;
+    bool polishing = false;
+    double rtol_cur = rtol;
+    std::vector<double> w_fast;
+    auto t_polish = std::chrono::steady_clock::now();
+    struct AccurateOperator {  // h->refining and the contraction mode for the refinement, restored on exit
+        adc_handle* h;
+        int saved = 0;
+        bool on = false;
+        void enter() {
+            saved = h->ctx.gemm_mode;
+            h->refining = true;
+            h->ctx.gemm_mode = h->opt.refine >= 2 ? 0 : std::min(h->cmode_sigma, 1);
+            on = true;
+        }
+        ~AccurateOperator() {
+            if (on) {
+                h->refining = false;
+                h->ctx.gemm_mode = saved;
+            }
+        }
+    } accurate{h};
     for (it = 1; it <= maxit; ++it) {
         int k = d.k;
         // G = V S W^T (symmetrised), kept up to date on the host as vectors are added
@@ -1090,7 +1141,7 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
         std::vector<int> todo;
         for (int r = 0; r < nroots; ++r) {
             rn[r] = std::sqrt(std::max(rr[r], 0.0));
-            bool cv = std::fabs(w[r] - wold[r]) <= tol && rn[r] <= rtol;
+            bool cv = std::fabs(w[r] - wold[r]) <= tol && rn[r] <= rtol_cur;
             if (!std::isfinite(w[r]) || !std::isfinite(rn[r]))
                 throw Error(ADC_ERR_NONFINITE, "davidson: non-finite Ritz value or residual (non-finite sigma)");
             if (!cv) {
@@ -1104,6 +1155,25 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
             } else if (++stall[r] >= 4) {
                 diag_only[r] = 1;
             }
+        }
+        if (all && polish && !polishing) {
+            // switch to the accurate operator: the subspace restarts from the converged Ritz vectors
+            polishing = true;
+            t_polish = std::chrono::steady_clock::now();
+            w_fast.assign(w.begin(), w.begin() + nroots);
+            accurate.enter();
+            ADC_CUDA(cudaMemcpyAsync(d.V, X, (size_t)nroots * dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+            d.metric(d.V, d.SV, nroots, 0);
+            d.k = nroots;
+            std::fill(d.G.begin(), d.G.end(), 0.0);
+            d.sigma(0, nroots);
+            d.update_G(0, nroots);
+            std::fill(wold.begin(), wold.end(), INFINITY);
+            std::fill(best_rn.begin(), best_rn.end(), INFINITY);
+            std::fill(stall.begin(), stall.end(), 0);
+            rtol_cur = h->opt.refine_res_tol;
+            maxit = it + std::max(1, h->opt.max_iter);
+            continue;
         }
         if (all) {
             status = ADC_OK;
@@ -1171,7 +1241,10 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
     // makes the vector error first order, its energy error second order, so
     // the refined energies carry the accurate operator's error only.
     double refine_shift = 0.0, refine_sec = 0.0;
-    if (h->opt.precision != ADC_PREC_FP64 && h->opt.refine) {
+    if (polishing) {
+        for (int r = 0; r < nroots; ++r) refine_shift = std::max(refine_shift, std::fabs(w[r] - w_fast[r]));
+        refine_sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_polish).count();
+    } else if (h->opt.precision != ADC_PREC_FP64 && h->opt.refine) {
         auto tr = std::chrono::steady_clock::now();
         const int saved = c.gemm_mode;
         h->refining = true;
@@ -1368,6 +1441,106 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
         stats[7] = fell;
     }
     return status;
+}
+
+// --------------------------------------------------------------------------
+// Training samples of the learned preconditioner from the handle's own plain
+// Davidson: the iterates y after k iterations (the solver stopped at max_iter =
+// k), their residuals r = sigma(y) - w y and the exact correction
+// t* = y_exact / <y_exact, y>_S - y, with y_exact the tightly converged root of
+// largest S-overlap.  Each sample is one vector element.
+// --------------------------------------------------------------------------
+static long long mlp_samples_per_vector(const adc_handle* h, long long per_vector) {
+    const long long n1 = h->n1(), rest = h->dim() - n1;
+    return n1 + std::min(std::max(per_vector, 0LL), rest);
+}
+
+static void mlp_samples(adc_handle* h, int nroots, const int* iters, int n_iters, long long per_vector,
+                        unsigned long long seed, double exact_tol, double* od, unsigned char* ob, double* orr, double* ot) {
+    Ctx& c = h->ctx;
+    const long long dim = h->dim(), n1 = h->n1(), per = mlp_samples_per_vector(h, per_vector);
+    const adc_options saved = h->opt;
+    struct Restore {
+        adc_handle* h;
+        adc_options o;
+        ~Restore() { h->opt = o; }
+    } restore{h, saved};
+    Scope sc(c.arena);
+    std::vector<double> e(nroots), hv((size_t)nroots * dim);
+    // exact roots
+    h->opt.max_iter = std::max(200, saved.max_iter);
+    h->opt.res_tol = saved.res_tol > 0 ? std::min(1e-6, saved.res_tol) : 1e-6;
+    h->opt.refine_res_tol = 0.0;
+    davidson(h, nroots, exact_tol, nullptr, e.data(), nullptr, hv.data(), nullptr);
+    double* Yex = c.arena.dalloc((size_t)nroots * dim);
+    double* SYex = c.arena.dalloc((size_t)nroots * dim);
+    double* Y = c.arena.dalloc((size_t)nroots * dim);
+    double* W = c.arena.dalloc((size_t)nroots * dim);
+    double* ov = c.arena.dalloc((size_t)nroots * nroots);
+    long long* di = (long long*)c.arena.alloc((size_t)per * sizeof(long long));
+    double* sd = c.arena.dalloc((size_t)per);
+    double* sr = c.arena.dalloc((size_t)per);
+    double* st = c.arena.dalloc((size_t)per);
+    unsigned char* sb = (unsigned char*)c.arena.alloc((size_t)per);
+    ADC_CUDA(cudaMemcpyAsync(Yex, hv.data(), hv.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    k_metric<<<grid_for((long long)nroots * dim), 256, 0, c.stream>>>(h->kind == ADC_EA, h->o, h->v, nroots, Yex, SYex, 0);
+    launch_check(c);
+    // element choice: every 1p/1h element, then per - n1 distinct 2p1h/2h1p elements (Floyd's
+    // sampling with a splitmix64 stream seeded by `seed`)
+    unsigned long long state = seed;
+    auto next = [&state]() {
+        unsigned long long z = (state += 0x9E3779B97F4A7C15ULL);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        return z ^ (z >> 31);
+    };
+    std::vector<long long> pick((size_t)per);
+    long long out = 0;
+    for (int ki = 0; ki < n_iters; ++ki) {
+        h->opt = saved;
+        h->opt.max_iter = std::max(1, iters[ki]);
+        h->opt.res_tol = 1e-12;
+        h->opt.refine_res_tol = 0.0;
+        davidson(h, nroots, 1e-14, nullptr, e.data(), nullptr, hv.data(), nullptr);  // NOT_CONVERGED by design
+        ADC_CUDA(cudaMemcpyAsync(Y, hv.data(), hv.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+        sigma_device(h, Y, W, nroots);
+        multidot(c, nroots, SYex, dim, nroots, Y, dim, dim, ov);  // ov[s][r] = <y_exact_s, y_r>_S
+        std::vector<double> hov((size_t)nroots * nroots);
+        ADC_CUDA(cudaMemcpyAsync(hov.data(), ov, hov.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        ADC_CUDA(cudaStreamSynchronize(c.stream));
+        for (int r = 0; r < nroots; ++r) {
+            int best = 0;
+            for (int s2 = 1; s2 < nroots; ++s2)
+                if (std::fabs(hov[(size_t)s2 * nroots + r]) > std::fabs(hov[(size_t)best * nroots + r])) best = s2;
+            const double ovr = hov[(size_t)best * nroots + r];
+            if (!(std::fabs(ovr) > 0)) throw Error(ADC_ERR_NONFINITE, "adc_mlp_samples: iterate orthogonal to every exact root");
+            for (long long x = 0; x < n1; ++x) pick[x] = x;
+            const long long rest = dim - n1, m = per - n1;
+            std::vector<long long> chosen;
+            chosen.reserve((size_t)m);
+            {
+                std::unordered_set<long long> used;
+                for (long long j = rest - m; j < rest; ++j) {
+                    long long q = (long long)(next() % (unsigned long long)(j + 1));
+                    if (used.count(q)) q = j;
+                    used.insert(q);
+                    chosen.push_back(q);
+                }
+            }
+            for (long long k = 0; k < m; ++k) pick[n1 + k] = n1 + chosen[k];
+            ADC_CUDA(cudaMemcpyAsync(di, pick.data(), per * sizeof(long long), cudaMemcpyHostToDevice, c.stream));
+            k_mlp_samples<<<grid_for(per), 256, 0, c.stream>>>(per, di, n1, h->diag, e[r], W + (long long)r * dim,
+                                                                Y + (long long)r * dim, Yex + (long long)best * dim, 1.0 / ovr,
+                                                                sd, sb, sr, st);
+            launch_check(c);
+            ADC_CUDA(cudaMemcpyAsync(od + out, sd, per * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+            ADC_CUDA(cudaMemcpyAsync(ob + out, sb, per, cudaMemcpyDeviceToHost, c.stream));
+            ADC_CUDA(cudaMemcpyAsync(orr + out, sr, per * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+            ADC_CUDA(cudaMemcpyAsync(ot + out, st, per * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+            ADC_CUDA(cudaStreamSynchronize(c.stream));
+            out += per;
+        }
+    }
 }
 
 // Internal accessor for the allocation-free ladder entry point (ladder_static.cu).
@@ -1636,9 +1809,17 @@ static void setup_unrestricted(adc_handle* h, const double* eps_so, const double
         h->m12 = h->dmalloc(o3v);
         perm4(c, h->g_ooov, {o, o, o, v}, {2, 0, 1, 3}, h->m12, 1.0, 0.0);
         if (third) {
-            double* G = c.arena.dalloc(Q * o3v);  // [Q,i,j,k,d] = sum_e B^Q_ie t_jk^de
-            einsum(c, "Qie,jkde->Qijkd", 1.0, Bov, T4, 0.0, G, {Q, o, o, o, v});
-            einsum(c, "Qijkd,Qad->ijka", -1.0, tn(G, {Q, o, o, o, v}), Bvv, 1.0, h->m12, {o, o, o, v});
+            // - sum_Q sum_d (sum_e B^Q_ie t_jk^de) B^Q_ad through G[Q,i,j,k,d], the auxiliary index in
+            // chunks (aux_chunk, else G of at most 2^27 elements = 1 GiB per chunk)
+            const long long qc = h->opt.aux_chunk > 0 ? std::min<long long>(Q, h->opt.aux_chunk)
+                                                      : std::max(1LL, std::min(Q, (1LL << 27) / std::max(o3v, 1LL)));
+            double* G = c.arena.dalloc(qc * o3v);
+            for (long long q0 = 0; q0 < Q; q0 += qc) {
+                const long long nq = std::min(qc, Q - q0);
+                einsum(c, "Qie,jkde->Qijkd", 1.0, tn(h->Bov + q0 * o * v, {nq, o, v}), T4, 0.0, G, {nq, o, o, o, v});
+                einsum(c, "Qijkd,Qad->ijka", -1.0, tn(G, {nq, o, o, o, v}), tn(h->Bvv + q0 * v * v, {nq, v, v}), 1.0,
+                       h->m12, {o, o, o, v});
+            }
             double* Xc = c.arena.dalloc(o3v);
             einsum(c, "ilkc,jlac->ijka", 1.0, tn(h->g_ooov, {o, o, o, v}), T4, 0.0, Xc, {o, o, o, v});
             axpby(c, o3v, -1.0, Xc, 1.0, h->m12);
@@ -1800,7 +1981,8 @@ int adc_mlp_train(float* weights, const double* d, const unsigned char* blk, con
 int adc_set_options(adc_handle* h, const adc_options* opt) {
     if (!h || !opt) return ADC_ERR_ARG;
     if (opt->max_space_per_root < 1 || opt->max_iter < 1 || opt->nguess_extra < 0 || opt->keep_per_root < 1 ||
-        opt->refine < 0 || opt->refine > 2 || (opt->transition_order != 0 && opt->transition_order != 2)) {
+        opt->refine < 0 || opt->refine > 2 || (opt->transition_order != 0 && opt->transition_order != 2) ||
+        !(opt->refine_res_tol >= 0.0)) {
         h->err = "adc_set_options: invalid option";
         return ADC_ERR_ARG;
     }
@@ -1812,6 +1994,7 @@ int adc_set_options(adc_handle* h, const adc_options* opt) {
     h->opt.keep_per_root = opt->keep_per_root;
     h->opt.refine = opt->refine;
     h->opt.transition_order = opt->transition_order;
+    h->opt.refine_res_tol = opt->refine_res_tol;
     return ADC_OK;
 }
 
@@ -1832,6 +2015,31 @@ int adc_set_mlp(adc_handle* h, const float* weights) {
     })
 }
 
+long long adc_mlp_nsamples(const adc_handle* h, int nroots, int n_iters, long long per_vector) {
+    if (!h || h->unrestricted || nroots < 1 || n_iters < 1 || per_vector < 0) return -1;
+    return (long long)n_iters * nroots * mlp_samples_per_vector(h, per_vector);
+}
+
+int adc_mlp_samples(adc_handle* h, int nroots, const int* iters, int n_iters, long long per_vector,
+                    unsigned long long seed, double exact_tol, double* d, unsigned char* blk, double* r, double* t,
+                    long long n) {
+    if (!h) return ADC_ERR_ARG;
+    if (h->unrestricted || nroots < 1 || nroots > h->dim() || !iters || n_iters < 1 || per_vector < 0 ||
+        !(exact_tol > 0) || !d || !blk || !r || !t || n < adc_mlp_nsamples(h, nroots, n_iters, per_vector)) {
+        h->err = "adc_mlp_samples: invalid argument (or output arrays shorter than adc_mlp_nsamples)";
+        return ADC_ERR_ARG;
+    }
+    for (int k = 0; k < n_iters; ++k)
+        if (iters[k] < 1) {
+            h->err = "adc_mlp_samples: iteration counts must be >= 1";
+            return ADC_ERR_ARG;
+        }
+    GUARD(h, {
+        mlp_samples(h, nroots, iters, n_iters, per_vector, seed, exact_tol, d, blk, r, t);
+        return ADC_OK;
+    })
+}
+
 int adc_default_options(adc_options* opt) {
     if (!opt) return ADC_ERR_ARG;
     opt->precision = ADC_PREC_FP64;
@@ -1844,6 +2052,7 @@ int adc_default_options(adc_options* opt) {
     opt->contractions = -1;
     opt->refine = 1;
     opt->transition_order = 0;
+    opt->refine_res_tol = 0.0;
     return ADC_OK;
 }
 
@@ -1863,8 +2072,9 @@ static int setup_one(const double* eps, const double* Bq, int nocc, int nvir, in
         msg = "adc_setup: unknown precision";
         return ADC_ERR_ARG;
     }
-    if (opt && (opt->contractions < -1 || opt->contractions > 2 || opt->refine < 0 || opt->refine > 2)) {
-        msg = "adc_setup: contractions must be -1..2 and refine 0..2";
+    if (opt && (opt->contractions < -1 || opt->contractions > 2 || opt->refine < 0 || opt->refine > 2 ||
+                !(opt->refine_res_tol >= 0.0))) {
+        msg = "adc_setup: contractions must be -1..2, refine 0..2 and refine_res_tol >= 0";
         return ADC_ERR_ARG;
     }
     if (opt && opt->transition_order != 0 && opt->transition_order != 2) {
@@ -1958,13 +2168,14 @@ int adc_setup_batch(int nmol, const double* const* eps, const double* const* Bq,
 }
 
 int adc_setup_unrestricted(const double* eps_a, const double* eps_b, const double* Ba, const double* Bb, int nocc_a,
-                           int nocc_b, int nmo, int naux, int order, int kind, adc_handle** out) {
+                           int nocc_b, int nmo, int naux, int order, int kind, int aux_chunk, adc_handle** out) {
     if (!out) return ADC_ERR_ARG;
     *out = nullptr;
     const int no = nocc_a + nocc_b, nso = 2 * nmo, nv = nso - no;
     const bool pairs_ok = kind == ADC_EA ? nv >= 2 : no >= 2;
     if (!eps_a || !eps_b || !Ba || !Bb || nmo < 1 || nocc_a < 0 || nocc_b < 0 || nocc_a > nmo || nocc_b > nmo || no < 1 ||
-        nv < 1 || naux < 1 || (order != 2 && order != 3) || (kind != ADC_EA && kind != ADC_IP) || !pairs_ok) {
+        nv < 1 || naux < 1 || (order != 2 && order != 3) || (kind != ADC_EA && kind != ADC_IP) || !pairs_ok ||
+        aux_chunk < 0) {
         g_setup_error = "adc_setup_unrestricted: invalid argument";
         return ADC_ERR_ARG;
     }
@@ -1992,6 +2203,7 @@ int adc_setup_unrestricted(const double* eps_a, const double* eps_b, const doubl
     h->kind = kind;
     h->unrestricted = true;
     adc_default_options(&h->opt);
+    h->opt.aux_chunk = aux_chunk;
     try {
         setup_unrestricted(h, eps_so.data(), Bso.data());
     } catch (const adc::Error& e) {

@@ -69,13 +69,14 @@ def test_roots_mixed_vs_fp64(kind, prec):
 
     o, v, naux, seed = 6, 40, 100, 2
     s = make_system(o, v, naux, seed=seed)
-    g64 = ADC(s.eps, s.B, o, order=3, kind=kind, precision="fp64", res_tol=1e-6)
-    gmx = ADC(s.eps, s.B, o, order=3, kind=kind, precision=prec, res_tol=1e-6)
+    g64 = ADC(s.eps, s.B, o, order=3, kind=kind, precision="fp64", res_tol=1e-7)
+    gmx = ADC(s.eps, s.B, o, order=3, kind=kind, precision=prec, res_tol=1e-5, refine_res_tol=1e-7)
     e64, p64, _, _ = g64.davidson(4, tol=1e-9)
     emx, pmx, _, st = gmx.davidson(4, tol=1e-9)
     assert st["status"] == 0
     assert np.abs(e64 - emx).max() < TOL_E[prec], np.abs(e64 - emx).max()
-    assert np.abs(p64 - pmx).max() < 1e-4
+    # vectors converged under the accurate operator: P within the target of 1e-6
+    assert np.abs(p64 - pmx).max() < 1e-6, np.abs(p64 - pmx).max()
     g64.close()
     gmx.close()
 

@@ -36,6 +36,53 @@ def test_loss_grad_vs_oracle():
     assert np.abs(gg - go).max() <= 1e-3 * np.abs(go).max()
 
 
+def _metric_ea(x, o, v):
+    """S x for the EA layout [Y_a | Y_iab] (S = diag(1, 2 - P), P swapping a and b)."""
+    y = x.copy()
+    Y2 = x[v:].reshape(o, v, v)
+    y[v:] = (2.0 * Y2 - Y2.transpose(0, 2, 1)).ravel()
+    return y
+
+
+def test_samples_follow_their_definition():
+    """adc_mlp_samples against its definition, formed here from the library's own
+    outputs: the tightly converged roots, the iterates of a Davidson stopped after
+    k iterations, and sigma of those iterates.  With per_vector >= dim every
+    element is sampled (in the generator's order), so each (k, root) block is
+    compared as a set of (d, blk, r, t) tuples."""
+    from paper_2012_06714_gb300 import ADC
+
+    o, v = 4, 16
+    s = make_system(o, v, 48, seed=3)
+    g = ADC(s.eps, s.B, o, order=3, kind="ea", precision="fp64")
+    dim, nroots = g.dim, 3
+    d, blk, r, t = g.mlp_samples(nroots, iters=(2, 3), per_vector=dim, seed=5)
+    assert d.size == 2 * nroots * dim
+    D = g.get("diag", (dim,))
+    g.set_options(max_iter=200, res_tol=1e-6)
+    _, _, Yex, _ = g.davidson(nroots, tol=1e-10, want_vectors=True)
+    SYex = np.array([_metric_ea(y, o, v) for y in Yex])
+    blocks = []
+    for k in (2, 3):
+        g.set_options(max_iter=k, res_tol=1e-12)
+        e, _, Y, st = g.davidson(nroots, tol=1e-14, want_vectors=True)
+        assert st["status"] == -4  # stopped by design
+        W = g.sigma(Y)
+        for q in range(nroots):
+            ov = SYex @ Y[q]
+            b = int(np.argmax(np.abs(ov)))
+            blocks.append(np.stack([D - e[q], (np.arange(dim) < v).astype(float), W[q] - e[q] * Y[q],
+                                    Yex[b] / ov[b] - Y[q]], axis=1))
+    g.close()
+    got = np.stack([d, blk.astype(float), r, t], axis=1).reshape(len(blocks), dim, 4)
+    for q, ref in enumerate(blocks):
+        # the 1p elements come first, in order
+        assert np.abs(got[q, :v] - ref[:v]).max() <= 1e-10 * np.abs(ref).max()
+        a = got[q, v:][np.lexsort(got[q, v:].T[::-1])]
+        b = ref[v:][np.lexsort(ref[v:].T[::-1])]
+        assert np.abs(a - b).max() <= 1e-10 * np.abs(ref).max()
+
+
 @pytest.fixture(scope="module")
 def trained():
     from paper_2012_06714_gb300 import ADC, mlp_loss_grad, mlp_train

@@ -41,6 +41,24 @@ def test_unrestricted_sigma_fp64(kind, order, case):
     assert np.abs(Sg - Sr).max() <= 1e-11 * np.abs(Sr).max()
 
 
+def test_unrestricted_ip3_coupling_in_auxiliary_chunks():
+    """The IP-UADC(3) coupling intermediate sum_e B^Q_ie t_jk^de (naux x o^3 x v)
+    is built in auxiliary chunks; 3 functions per chunk (14 chunks, the last
+    ragged) give the same sigma as the oracle."""
+    from oracle.unrestricted import UnrestrictedDFADC
+    from paper_2012_06714_gb300 import ADCUnrestricted
+
+    na, nb, nmo, naux = 5, 4, 23, 41
+    s = make_open_shell_system(na, nb, nmo, naux, seed=2)
+    ref = UnrestrictedDFADC(s, 3, "ip")
+    gpu = ADCUnrestricted(s.eps_a, s.eps_b, s.B_a, s.B_b, na, nb, order=3, kind="ip", aux_chunk=3)
+    X = np.random.default_rng(4).standard_normal((2, gpu.dim))
+    Sg = gpu.sigma(X)
+    Sr = ref.sigma(X)
+    gpu.close()
+    assert np.abs(Sg - Sr).max() <= 1e-11 * np.abs(Sr).max()
+
+
 def test_unrestricted_argument_errors():
     import ctypes
 
