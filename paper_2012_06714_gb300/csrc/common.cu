@@ -96,7 +96,250 @@ inline int grid_for(long long n) {
     return (int)std::min<long long>(std::max<long long>(g, 1), 152LL * 32);
 }
 
+// ---- own GEMM kernels for the small and skinny contractions of sigma ------------
+// Row-major A [M][K] (lda), B [K][N] (ldb).  F32: FP64 operands rounded to FP32 in
+// registers, FP32 products summed in FP32 over at most 64 terms, those partial sums
+// accumulated in FP64 (the FP32-accurate class); else FP64 throughout.  Each kernel
+// writes its K slice's partial result P[slice][m][n]; k_reduce_slices finishes
+// C = alpha sum_slices P + beta C.
+
+constexpr int SK_THREADS = 256;
+constexpr int SK_CHUNK = 64;  // FP32 partial-sum length
+
+// M <= MM rows of A (a few trial vectors): one thread per column n of B, the A values of
+// the current 256-deep K chunk in shared memory; reads B once, coalesced along n.
+template <int MM, bool F32>
+__global__ void __launch_bounds__(SK_THREADS) k_skinny_m(int M, long long N, long long K, long long kslice,
+                                                         const double* __restrict__ A, long long lda,
+                                                         const double* __restrict__ B, long long ldb,
+                                                         double* __restrict__ P) {
+    __shared__ double As[MM][SK_THREADS];
+    const long long n = blockIdx.x * (long long)SK_THREADS + threadIdx.x;
+    const long long k0 = blockIdx.y * kslice, k1 = min(K, k0 + kslice);
+    double acc[MM];
+#pragma unroll
+    for (int m = 0; m < MM; ++m) acc[m] = 0.0;
+    for (long long kc = k0; kc < k1; kc += SK_THREADS) {
+        const int kn = (int)min((long long)SK_THREADS, k1 - kc);
+        __syncthreads();
+        if (threadIdx.x < kn)
+#pragma unroll
+            for (int m = 0; m < MM; ++m) As[m][threadIdx.x] = m < M ? A[m * lda + kc + threadIdx.x] : 0.0;
+        __syncthreads();
+        if (n >= N) continue;
+        const double* b = B + kc * ldb + n;
+        if (F32) {
+            for (int k2 = 0; k2 < kn; k2 += SK_CHUNK) {
+                float part[MM];
+#pragma unroll
+                for (int m = 0; m < MM; ++m) part[m] = 0.f;
+                const int ke = min(kn, k2 + SK_CHUNK);
+                for (int kk = k2; kk < ke; ++kk) {
+                    const float bv = (float)b[kk * ldb];
+#pragma unroll
+                    for (int m = 0; m < MM; ++m) part[m] = fmaf((float)As[m][kk], bv, part[m]);
+                }
+#pragma unroll
+                for (int m = 0; m < MM; ++m) acc[m] += (double)part[m];
+            }
+        } else {
+            for (int kk = 0; kk < kn; ++kk) {
+                const double bv = b[kk * ldb];
+#pragma unroll
+                for (int m = 0; m < MM; ++m) acc[m] = fma(As[m][kk], bv, acc[m]);
+            }
+        }
+    }
+    if (n < N)
+#pragma unroll
+        for (int m = 0; m < MM; ++m)
+            if (m < M) P[((long long)blockIdx.y * M + m) * N + n] = acc[m];
+}
+
+// N <= NN columns of B: one block per row m of A and K slice; threads stride over k
+// (A read coalesced), then a warp-shuffle and shared-memory reduction of the NN sums.
+template <int NN, bool F32>
+__global__ void __launch_bounds__(SK_THREADS) k_skinny_n(long long M, int N, long long K, long long kslice,
+                                                         const double* __restrict__ A, long long lda,
+                                                         const double* __restrict__ B, long long ldb,
+                                                         double* __restrict__ P) {
+    __shared__ double red[SK_THREADS / 32][NN];
+    const long long m = blockIdx.x;
+    const long long k0 = blockIdx.y * kslice, k1 = min(K, k0 + kslice);
+    double acc[NN];
+#pragma unroll
+    for (int j = 0; j < NN; ++j) acc[j] = 0.0;
+    const double* a = A + m * lda;
+    if (F32) {
+        // each thread takes up to SK_CHUNK of its strided terms per FP32 partial sum
+        for (long long kb = k0; kb < k1; kb += (long long)SK_THREADS * SK_CHUNK) {
+            float part[NN];
+#pragma unroll
+            for (int j = 0; j < NN; ++j) part[j] = 0.f;
+            const long long ke = min(k1, kb + (long long)SK_THREADS * SK_CHUNK);
+            for (long long k = kb + threadIdx.x; k < ke; k += SK_THREADS) {
+                const float av = (float)a[k];
+#pragma unroll
+                for (int j = 0; j < NN; ++j)
+                    if (j < N) part[j] = fmaf(av, (float)B[k * ldb + j], part[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < NN; ++j) acc[j] += (double)part[j];
+        }
+    } else {
+        for (long long k = k0 + threadIdx.x; k < k1; k += SK_THREADS) {
+            const double av = a[k];
+#pragma unroll
+            for (int j = 0; j < NN; ++j)
+                if (j < N) acc[j] = fma(av, B[k * ldb + j], acc[j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NN; ++j) {
+        double x = acc[j];
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][j] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < N) {
+        double x = 0.0;
+        for (int w = 0; w < SK_THREADS / 32; ++w) x += red[w][threadIdx.x];
+        P[((long long)blockIdx.y * M + m) * N + threadIdx.x] = x;
+    }
+}
+
+// General small contraction in FP64: 64 x 64 output tiles, 16-deep K steps through
+// shared memory, 4 x 4 outputs per thread.
+__global__ void __launch_bounds__(256) k_tile_f64(long long M, long long N, long long K, const double* __restrict__ A,
+                                                  long long lda, const double* __restrict__ B, long long ldb,
+                                                  double* __restrict__ P) {
+    __shared__ double As[16][64 + 1];
+    __shared__ double Bs[16][64];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const long long m0 = blockIdx.y * 64LL, n0 = blockIdx.x * 64LL;
+    double acc[4][4] = {};
+    for (long long k0 = 0; k0 < K; k0 += 16) {
+        for (int e = threadIdx.x; e < 64 * 16; e += 256) {
+            const int r = e / 16, kk = e % 16;
+            const long long gm = m0 + r, gk = k0 + kk;
+            As[kk][r] = (gm < M && gk < K) ? A[gm * lda + gk] : 0.0;
+            const int kb = e / 64, cn = e % 64;
+            const long long gn = n0 + cn, gk2 = k0 + kb;
+            Bs[kb][cn] = (gn < N && gk2 < K) ? B[gk2 * ldb + gn] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const long long gm = m0 + ty * 4 + i, gn = n0 + tx * 4 + j;
+            if (gm < M && gn < N) P[gm * N + gn] = acc[i][j];
+        }
+}
+
+// C[m * ldc + n] = alpha sum_s P[s][m][n] + beta C[m * ldc + n]
+__global__ void k_reduce_slices(int S, long long M, long long N, const double* __restrict__ P, double alpha, double beta,
+                                double* __restrict__ C, long long ldc) {
+    const long long total = M * N;
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total; x += (long long)gridDim.x * blockDim.x) {
+        double a = 0.0;
+        for (int s2 = 0; s2 < S; ++s2) a += P[s2 * total + x];
+        const long long m = x / N, n = x - m * N;
+        double* cp = C + m * ldc + n;
+        *cp = beta == 0.0 ? alpha * a : alpha * a + beta * *cp;
+    }
+}
+
+template <int MM, bool F32>
+void launch_skinny_m(dim3 g, cudaStream_t st, int M, long long N, long long K, long long ks, const double* A, long long lda,
+                     const double* B, long long ldb, double* P) {
+    k_skinny_m<MM, F32><<<g, SK_THREADS, 0, st>>>(M, N, K, ks, A, lda, B, ldb, P);
+}
+template <int NN, bool F32>
+void launch_skinny_n(dim3 g, cudaStream_t st, long long M, int N, long long K, long long ks, const double* A, long long lda,
+                     const double* B, long long ldb, double* P) {
+    k_skinny_n<NN, F32><<<g, SK_THREADS, 0, st>>>(M, N, K, ks, A, lda, B, ldb, P);
+}
+
 }  // namespace
+
+void own_gemm(Ctx& c, long long M, long long N, long long K, double alpha, const double* A, long long lda, const double* B,
+              long long ldb, double beta, double* C, long long ldc, bool f32) {
+    if (M <= 0 || N <= 0) return;
+    if (K <= 0) {
+        for (long long m = 0; m < M; ++m) {
+            if (beta == 0.0)
+                fill(c, N, 0.0, C + m * ldc);
+            else if (beta != 1.0)
+                axpby(c, N, 0.0, C + m * ldc, beta, C + m * ldc);
+        }
+        return;
+    }
+    const long long target = 152LL * 8;  // blocks that fill the GPU several times over
+    Arena::Mark mk = c.arena.mark();
+    int S = 1;
+    double* P = nullptr;
+    if (M <= 8) {
+        const long long nbn = (N + SK_THREADS - 1) / SK_THREADS;
+        const long long kch = (K + SK_THREADS - 1) / SK_THREADS;
+        S = (int)std::max<long long>(1, std::min<long long>({kch, (target + nbn - 1) / nbn, 4096}));
+        const long long ks = (kch + S - 1) / S * SK_THREADS;
+        S = (int)((K + ks - 1) / ks);
+        P = c.arena.dalloc((size_t)S * M * N);
+        dim3 g((unsigned)nbn, (unsigned)S);
+        auto go = [&](auto f) { f(g, c.stream, (int)M, N, K, ks, A, lda, B, ldb, P); };
+        switch ((int)M) {
+#define SKM(X)                                                              \
+    case X:                                                                 \
+        if (f32) go(launch_skinny_m<X, true>); else go(launch_skinny_m<X, false>); \
+        break;
+            SKM(1) SKM(2) SKM(3) SKM(4) SKM(5) SKM(6) SKM(7) SKM(8)
+#undef SKM
+        }
+    } else if (N <= 8) {
+        const long long kch = (K + SK_THREADS - 1) / SK_THREADS;
+        S = (int)std::max<long long>(1, std::min<long long>({kch, (target + M - 1) / M, 65535}));
+        const long long ks = (kch + S - 1) / S * SK_THREADS;
+        S = (int)((K + ks - 1) / ks);
+        if (M > 0x7fffffffLL) throw Error(-1, "own_gemm: too many rows");
+        P = c.arena.dalloc((size_t)S * M * N);
+        dim3 g((unsigned)M, (unsigned)S);
+        auto go = [&](auto f) { f(g, c.stream, M, (int)N, K, ks, A, lda, B, ldb, P); };
+        switch ((int)N) {
+#define SKN(X)                                                              \
+    case X:                                                                 \
+        if (f32) go(launch_skinny_n<X, true>); else go(launch_skinny_n<X, false>); \
+        break;
+            SKN(1) SKN(2) SKN(3) SKN(4) SKN(5) SKN(6) SKN(7) SKN(8)
+#undef SKN
+        }
+    } else {
+        if ((M + 63) / 64 > 65535) throw Error(-1, "own_gemm: too many row tiles");
+        P = c.arena.dalloc((size_t)M * N);
+        dim3 g((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64));
+        k_tile_f64<<<g, 256, 0, c.stream>>>(M, N, K, A, lda, B, ldb, P);
+    }
+    ++c.kernels;
+    ADC_CUDA(cudaGetLastError());
+    k_reduce_slices<<<grid_for(M * N), 256, 0, c.stream>>>(S, M, N, P, alpha, beta, C, ldc);
+    ++c.kernels;
+    ADC_CUDA(cudaGetLastError());
+    c.arena.release(mk);
+}
 
 void permute(Ctx& c, const double* in, const Shape& s, const int* perm, double* out, double alpha, double beta) {
     PermArgs a;
@@ -429,8 +672,28 @@ void einsum(Ctx& c, const char* specstr, double alpha, const T& A, const T& B, d
     };
     long long nb = prod(batch), M = prod(fa), N = prod(fb), K = prod(con);
     Arena::Mark mk = c.arena.mark();
-    if (c.gemm_mode == 2 && nb == 1 && 2.0 * M * N * K >= c.fp32_min_flops && tc_gemm_worthwhile(M, N, K)) {
-        einsum_tc(c, sp.a, sp.b, sp.c, dim, fa, fb, con, alpha, A.p, B.p, beta, C, A.constant, B.constant);
+    if (c.gemm_mode == 2 && nb == 1) {
+        // the mixed sigma: tensor cores for the large contractions, own kernels for the rest
+        const bool big = 2.0 * M * N * K >= c.fp32_min_flops;
+        if (big && std::min(M, N) > 8 && tc_gemm_fits(M, N, K)) {
+            einsum_tc(c, sp.a, sp.b, sp.c, dim, fa, fb, con, alpha, A.p, B.p, beta, C, A.constant, B.constant);
+        } else {
+            const double* Ap = to_order(c, A.p, sp.a, dim, fa + con);
+            const double* Bp = to_order(c, B.p, sp.b, dim, con + fb);
+            const std::string tord = fa + fb;
+            if (tord == sp.c) {
+                own_gemm(c, M, N, K, alpha, Ap, K, Bp, N, beta, C, N, big);
+            } else {
+                double* Tm = c.arena.dalloc((size_t)(M * N));
+                own_gemm(c, M, N, K, 1.0, Ap, K, Bp, N, 0.0, Tm, N, big);
+                Shape sh;
+                sh.nd = (int)tord.size();
+                for (int j = 0; j < sh.nd; ++j) sh.d[j] = dim[tord[j]];
+                int perm[kMaxDim];
+                for (int j = 0; j < sh.nd; ++j) perm[j] = (int)tord.find(sp.c[j]);
+                permute(c, Tm, sh, perm, C, alpha, beta);
+            }
+        }
         c.arena.release(mk);
         return;
     }

@@ -114,10 +114,12 @@ struct Ctx {
     long long kernels = 0;  // own kernel launches issued (for reporting)
     // 0: every contraction in FP64 (DGEMM).  1: contractions of >= fp32_min_flops
     // run as FP32-accurate GEMMs (BF16x9 emulation on the tensor cores), with
-    // FP64 inputs rounded to FP32 and results accumulated into FP64.  2: as 1,
-    // but unbatched contractions that tile the GPU well run on the tcgen05
-    // split-BF16 GEMM (two planes, FP32 partial sums promoted every 16 K
-    // blocks, FP64 result).
+    // FP64 inputs rounded to FP32 and results accumulated into FP64.  2 (the
+    // mixed sigma): unbatched contractions of >= fp32_min_flops with both free
+    // dimensions above 8 run on the tcgen05 split-BF16 GEMM (two planes, FP32
+    // partial sums promoted every 16 K blocks, FP64 result); the others on the
+    // library's own kernels (own_gemm: FP32-accurate from fp32_min_flops, else
+    // FP64).
     int gemm_mode = 0;
     double fp32_min_flops = 1e8;
     int emulation_ok = -1;  // -1 unknown, 1 BF16x9 emulation available, 0 plain FP32
@@ -179,6 +181,14 @@ void einsum(Ctx& c, const char* spec, double alpha, const T& A, const T& B, doub
 // planes), written K-major as out[p][r * Kp + k] with zeros for K <= k < Kp.
 void split_planes(Ctx& c, const double* in, const Shape& s, const int* perm, long long rows, long long K, long long Kp,
                   void* const* out);
+
+// The library's own kernels for small and skinny contractions (row-major A [M][K],
+// B [K][N], C [M][N] with leading dimensions): C = alpha A B + beta C.  M <= 8 or
+// N <= 8 take bandwidth kernels that read the large operand once (K split over
+// blocks, deterministic slice reduction); others a 64 x 64 tiled FP64 kernel.
+// f32: FP32 products and partial sums of <= 64 terms, accumulated in FP64.
+void own_gemm(Ctx& c, long long M, long long N, long long K, double alpha, const double* A, long long lda, const double* B,
+              long long ldb, double beta, double* C, long long ldc, bool f32);
 
 // Row-major GEMM: C[MxN] = alpha op(A) op(B) + beta C, batched with strides.
 void gemm(Ctx& c, bool ta, bool tb, long long M, long long N, long long K, double alpha, const double* A, long long lda,

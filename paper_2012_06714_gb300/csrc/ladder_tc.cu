@@ -1302,12 +1302,9 @@ bool ladder_tc_apply_scratch(LadderTC& L, Ctx& c, const double* X, long long nma
 }
 
 // ---- generic split-BF16 contraction (gemm_mode 2) --------------------------
-bool tc_gemm_worthwhile(long long M, long long N, long long K) {
-    // enough 256 x 256 tiles to occupy the CTA pairs -- directly, or (few tiles, long K) as
-    // up to 16 concurrent K slices -- and 32-bit tile coordinates
-    const long long tiles = ((M + 255) / 256) * ((N + 255) / 256);
-    if (M >= (1LL << 30) || N >= (1LL << 30) || K >= (1LL << 30)) return false;
-    return (tiles >= 64 && K >= 256) || (tiles >= 4 && K >= 4096);
+
+bool tc_gemm_fits(long long M, long long N, long long K) {
+    return M < (1LL << 30) && N < (1LL << 30) && K < (1LL << 30) && K >= 64;
 }
 
 void tc_gemm(Ctx& c, const void* const* A, const void* const* B, long long M, long long N, long long Kp, double algo_flops,
