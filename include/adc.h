@@ -88,7 +88,8 @@ typedef struct {
                              /* collapsed (thick restart, default 2)                  */
     int contractions;        /* non-ladder contractions: -1 follow precision (default:*/
                              /* FP64 -> 0; BF16X3 -> 2 in sigma, 1 in setup and      */
-                             /* refinement), 0 FP64 DGEMM, 1 FP32-accurate emulated   */
+                             /* refinement for EA, 0 in setup and refinement for IP), */
+                             /* 0 FP64 DGEMM, 1 FP32-accurate emulated                */
                              /* GEMM, 2 as 1 but unbatched contractions that tile the */
                              /* GPU run on the tensor-core split-BF16 GEMM of the     */
                              /* ladder (setup and refinement use 1)                   */
@@ -107,6 +108,12 @@ typedef struct {
                              /* below this value (vectors and spectroscopic factors   */
                              /* converged under that operator); 0 (default): one      */
                              /* Rayleigh-Ritz step in the span of the converged roots */
+    int m11_on_the_fly;      /* 1: the 1p-1p (EA) / 1h-1h (IP) block is not precomputed */
+                             /* (step 3 skipped); every sigma applies it from small    */
+                             /* intermediates (Sec. III A, the alternative to step 3;  */
+                             /* EA keeps the ladder of t, o^2 v^2); the preconditioner */
+                             /* then uses zeroth-order one-particle energies and      */
+                             /* adc_get_tensor("M11") is unavailable.  0 (default)     */
 } adc_options;
 
 /* Fill *opt with the defaults listed above.  Returns ADC_OK or ADC_ERR_ARG (NULL). */

@@ -58,10 +58,13 @@ struct adc_handle {
     // setup and refinement: every K block, drift ~4e-7)
     LadderMode lm_sigma{2, 0, 16}, lm_setup{2, 1, 1}, lm_refine{2, 1, 1};
     bool refining = false;  // sigma evaluates with lm_refine
-    int cmode_setup = 0, cmode_sigma = 0;  // Ctx::gemm_mode in setup / in sigma
+    int cmode_setup = 0, cmode_sigma = 0, cmode_refine = 0;  // Ctx::gemm_mode in setup / sigma / refinement
     std::vector<double> X_last;             // spectroscopic amplitudes [nroots][nmo] of the last adc_davidson
     float* mlp_w = nullptr;                 // learned preconditioner weights (device), NULL: diagonal
-    double* Lt = nullptr;    // setup only: sum_cd (ac|bd) t_kl^cd, shared by t2(2) and the EA 1p-1p block
+    double* Lt = nullptr;    // sum_cd (ac|bd) t_kl^cd, shared by t2(2) and the EA 1p-1p block (setup only,
+                             // unless the 1p-1p block is applied on the fly)
+    // 1p-1p / 1h-1h block applied on the fly (m11_on_the_fly): small intermediates of step 2
+    double *otf_g = nullptr, *otf_Hq = nullptr, *otf_gz = nullptr, *otf_Zm = nullptr, *otf_U = nullptr;
     std::vector<void*> owned;
     cudaStream_t own_stream = nullptr;  // created by adc_setup_batch, destroyed with the handle
     std::string err;
@@ -195,10 +198,15 @@ __global__ void k_diag(int ea, int o, int v, const double* __restrict__ eps, con
     long long n = n1 + blk;
     GRID_STRIDE(x, n) {
         if (x < n1)
-            D[x] = M11[x * n1 + x];
+            D[x] = M11 ? M11[x * n1 + x] : (ea ? eps[o + x] : -eps[x]);  // no M11: zeroth order
         else
             D[x] = ea ? d22(1, o, v, eps, x - n1) : -d22(0, o, v, eps, x - n1);
     }
+}
+// s[n][p] = e[p] y[n][p]: the zeroth-order one-particle block applied to nvec vectors
+__global__ void k_eps_apply(long long nvec, long long n1, const double* __restrict__ e, const double* __restrict__ y,
+                            double* __restrict__ out) {
+    GRID_STRIDE(x, nvec * n1) { out[x] = e[x % n1] * y[x]; }
 }
 // copy strided blocks: out[n][r] = in[n*ldin + off + r]
 __global__ void k_gather(long long nvec, long long len, const double* __restrict__ in, long long ldin, long long off,
@@ -257,6 +265,7 @@ struct Scope {
 };
 
 T tn(const double* p, std::initializer_list<long long> d) { return T{p, std::vector<long long>(d), false}; }
+T tn(const double* p, const std::vector<long long>& d) { return T{p, d, false}; }
 // handle-owned tensor that never changes after setup (its FP32 operand copy may be cached)
 T tc(const double* p, std::initializer_list<long long> d) { return T{p, std::vector<long long>(d), true}; }
 
@@ -427,6 +436,238 @@ static void setup_m11_ip(adc_handle* h) {
 }
 
 // --------------------------------------------------------------------------
+// The 1p-1p (EA) / 1h-1h (IP) block applied on the fly (Sec. III A: instead of
+// precomputing the block in step 3, its contribution sum_b M_ab Y_b / sum_j
+// M_ij Y_j is recomputed in every sigma from intermediates).  Each term of
+// setup_m11_ea / setup_m11_ip is contracted with the vector first: a term
+// X_ab = sum A_..a.. C_..b.. enters through (X + X^T) y = X y + X^T y, and
+// every integral or amplitude of the term meets y before the other factor.
+// Step-2 intermediates kept for it: the ladder of t (EA), and the small
+// g_Q = sum_kc B^Q_kc t_k^c(2), Hq_Qka = sum_c t_k^c(2) B^Q_ac, Zm_cd =
+// sum t t (v x v), gz_Q = sum_cd B^Q_cd Zm_cd and U_kl = sum t t (o x o).
+// --------------------------------------------------------------------------
+static void setup_m11_otf(adc_handle* h) {
+    Ctx& c = h->ctx;
+    const long long o = h->o, v = h->v, Q = h->naux;
+    if (h->order < 3) return;
+    const T T4 = tn(h->t, {o, o, v, v});
+    h->otf_Zm = h->dmalloc(v * v);
+    einsum(c, "klce,klde->cd", 2.0, T4, T4, 0.0, h->otf_Zm, {v, v});
+    einsum(c, "klce,kled->cd", -1.0, T4, T4, 1.0, h->otf_Zm, {v, v});
+    h->otf_U = h->dmalloc(o * o);
+    einsum(c, "kmcd,lmcd->kl", 2.0, T4, T4, 0.0, h->otf_U, {o, o});
+    einsum(c, "kmcd,lmdc->kl", -1.0, T4, T4, 1.0, h->otf_U, {o, o});
+    if (h->kind != ADC_EA) return;
+    h->otf_g = h->dmalloc(Q);
+    einsum(c, "Qkc,kc->Q", 1.0, tn(h->Bov, {Q, o, v}), tn(h->t1_2, {o, v}), 0.0, h->otf_g, {Q});
+    h->otf_Hq = h->dmalloc(Q * o * v);
+    einsum(c, "kc,Qac->Qka", 1.0, tn(h->t1_2, {o, v}), tn(h->Bvv, {Q, v, v}), 0.0, h->otf_Hq, {Q, o, v});
+    h->otf_gz = h->dmalloc(Q);
+    einsum(c, "Qcd,cd->Q", 1.0, tn(h->Bvv, {Q, v, v}), tn(h->otf_Zm, {v, v}), 0.0, h->otf_gz, {Q});
+}
+
+// s1 = M_+11 y1 (EA, n vectors of length v), terms as in setup_m11_ea
+static void m11_apply_otf_ea(adc_handle* h, const double* y1, double* s1, long long n) {
+    Ctx& c = h->ctx;
+    const long long o = h->o, v = h->v, Q = h->naux;
+    Scope sc(c.arena);
+    k_eps_apply<<<grid_for(n * v), 256, 0, c.stream>>>(n, v, h->eps + o, y1, s1);  // zeroth order
+    launch_check(c);
+    const T Y = tn(y1, {n, v});
+    const T ovov = tc(h->ovov, {o, v, o, v}), oovv = tc(h->oovv, {o, o, v, v});
+    const std::vector<long long> d4{n, o, o, v};
+    double* W = c.arena.dalloc(n * o * o * v);
+    double* Z = c.arena.dalloc(n * o * o * v);
+    // X_ab = -sum t_kl^ac [(kb|lc) - 1/2 (kc|lb)] for t = t2(1) and (ADC(3)) t2(2)
+    auto second = [&](const double* tt) {
+        const T T4 = tc(tt, {o, o, v, v});
+        einsum(c, "kblc,nb->nklc", -1.0, ovov, Y, 0.0, W, d4);
+        einsum(c, "kclb,nb->nklc", 0.5, ovov, Y, 1.0, W, d4);
+        einsum(c, "klac,nklc->na", 1.0, T4, tn(W, {n, o, o, v}), 1.0, s1, {n, v});
+        einsum(c, "klbc,nb->nklc", 1.0, T4, Y, 0.0, Z, d4);  // Z_klc = sum_b t_kl^bc y_b
+        einsum(c, "nklc,kalc->na", -1.0, tn(Z, {n, o, o, v}), ovov, 1.0, s1, {n, v});
+        einsum(c, "nklc,kcla->na", 0.5, tn(Z, {n, o, o, v}), ovov, 1.0, s1, {n, v});
+    };
+    second(h->t);
+    if (h->order < 3) return;
+    second(h->t_2);
+    const T T4 = tc(h->t, {o, o, v, v}), Bvv = tc(h->Bvv, {Q, v, v}), Bov = tc(h->Bov, {Q, o, v});
+    // t1(2): X_ab = 2 sum_Q g_Q B^Q_ab - sum_Qk B^Q_kb Hq_Qka
+    double* hq = c.arena.dalloc(n * Q * v);  // hq_Qa = sum_b B^Q_ab y_b
+    einsum(c, "Qab,nb->nQa", 1.0, Bvv, Y, 0.0, hq, {n, Q, v});
+    const T HQ = tn(hq, {n, Q, v});
+    double* p = c.arena.dalloc(n * Q * o);
+    einsum(c, "Q,nQa->na", 4.0, tc(h->otf_g, {Q}), HQ, 1.0, s1, {n, v});  // X y and X^T y
+    einsum(c, "Qkb,nb->nQk", 1.0, Bov, Y, 0.0, p, {n, Q, o});
+    einsum(c, "Qka,nQk->na", -1.0, tc(h->otf_Hq, {Q, o, v}), tn(p, {n, Q, o}), 1.0, s1, {n, v});
+    einsum(c, "Qkb,nb->nQk", 1.0, tc(h->otf_Hq, {Q, o, v}), Y, 0.0, p, {n, Q, o});
+    einsum(c, "Qka,nQk->na", -1.0, Bov, tn(p, {n, Q, o}), 1.0, s1, {n, v});
+    // ladder of t: X_ab = -sum t_kl^ac [L_kl^bc - 1/2 L_kl^cb]
+    const T L = tc(h->Lt, {o, o, v, v});
+    einsum(c, "klbc,nb->nklc", -1.0, L, Y, 0.0, W, d4);
+    einsum(c, "klcb,nb->nklc", 0.5, L, Y, 1.0, W, d4);
+    einsum(c, "klac,nklc->na", 1.0, T4, tn(W, {n, o, o, v}), 1.0, s1, {n, v});
+    einsum(c, "klbc,nb->nklc", 1.0, T4, Y, 0.0, Z, d4);  // Z_klc = sum_b t_kl^bc y_b (also the ring's Zt1)
+    const T ZT = tn(Z, {n, o, o, v});
+    einsum(c, "nklc,klac->na", -1.0, ZT, L, 1.0, s1, {n, v});
+    einsum(c, "nklc,klca->na", 0.5, ZT, L, 1.0, s1, {n, v});
+    // ring: X_ab = sum t_km^ac G_kmcb + t_km^ca GB_kmcb with G = (kl|db) u1 + (kb|ld) u2,
+    // GB = (kb|ld) u1 + (kl|db) u3; u1 = -t/2 + t^T, u2 = t - 2 t^T, u3 = t - t^T/2
+    double* A1 = c.arena.dalloc(n * o * o * v);  // sum_b (kl|db) y_b
+    double* A2 = c.arena.dalloc(n * o * o * v);  // sum_b (kb|ld) y_b
+    einsum(c, "kldb,nb->nkld", 1.0, oovv, Y, 0.0, A1, d4);
+    einsum(c, "kbld,nb->nkld", 1.0, ovov, Y, 0.0, A2, d4);
+    const T A1T = tn(A1, {n, o, o, v}), A2T = tn(A2, {n, o, o, v});
+    // W <- G y, Z2 <- GB y (u contracted as a t + b t^T)
+    double* Z2 = c.arena.dalloc(n * o * o * v);
+    einsum(c, "nkld,lmcd->nkmc", -0.5, A1T, T4, 0.0, W, d4);
+    einsum(c, "nkld,lmdc->nkmc", 1.0, A1T, T4, 1.0, W, d4);
+    einsum(c, "nkld,lmcd->nkmc", 1.0, A2T, T4, 1.0, W, d4);
+    einsum(c, "nkld,lmdc->nkmc", -2.0, A2T, T4, 1.0, W, d4);
+    einsum(c, "nkld,lmcd->nkmc", -0.5, A2T, T4, 0.0, Z2, d4);
+    einsum(c, "nkld,lmdc->nkmc", 1.0, A2T, T4, 1.0, Z2, d4);
+    einsum(c, "nkld,lmcd->nkmc", 1.0, A1T, T4, 1.0, Z2, d4);
+    einsum(c, "nkld,lmdc->nkmc", -0.5, A1T, T4, 1.0, Z2, d4);
+    einsum(c, "kmac,nkmc->na", 1.0, T4, tn(W, {n, o, o, v}), 1.0, s1, {n, v});
+    einsum(c, "kmca,nkmc->na", 1.0, T4, tn(Z2, {n, o, o, v}), 1.0, s1, {n, v});
+    // X^T y through Zt1 = Z and Zt2_kmc = sum_b t_km^cb y_b: sum (kl|da) Ra_kld + (ka|ld) Rb_kld,
+    // Ra = R(Zt1, u1) + R(Zt2, u3), Rb = R(Zt1, u2) + R(Zt2, u1), R(Z, u)_kld = sum_mc Z_kmc u_lm^cd
+    double* Zt2 = c.arena.dalloc(n * o * o * v);
+    einsum(c, "kmcb,nb->nkmc", 1.0, T4, Y, 0.0, Zt2, d4);
+    const T Z2T = tn(Zt2, {n, o, o, v});
+    double* Ra = W;
+    double* Rb = Z2;
+    einsum(c, "nkmc,lmcd->nkld", -0.5, ZT, T4, 0.0, Ra, d4);
+    einsum(c, "nkmc,lmdc->nkld", 1.0, ZT, T4, 1.0, Ra, d4);
+    einsum(c, "nkmc,lmcd->nkld", 1.0, Z2T, T4, 1.0, Ra, d4);
+    einsum(c, "nkmc,lmdc->nkld", -0.5, Z2T, T4, 1.0, Ra, d4);
+    einsum(c, "nkmc,lmcd->nkld", 1.0, ZT, T4, 0.0, Rb, d4);
+    einsum(c, "nkmc,lmdc->nkld", -2.0, ZT, T4, 1.0, Rb, d4);
+    einsum(c, "nkmc,lmcd->nkld", -0.5, Z2T, T4, 1.0, Rb, d4);
+    einsum(c, "nkmc,lmdc->nkld", 1.0, Z2T, T4, 1.0, Rb, d4);
+    einsum(c, "klda,nkld->na", 1.0, oovv, tn(Ra, {n, o, o, v}), 1.0, s1, {n, v});
+    einsum(c, "kald,nkld->na", 1.0, ovov, tn(Rb, {n, o, o, v}), 1.0, s1, {n, v});
+    // both lines on the integral: M_ab += 2 sum_Q gz_Q B^Q_ab - sum_Q (B^Q Zm^T B^Q)_ab
+    einsum(c, "Q,nQa->na", 2.0, tc(h->otf_gz, {Q}), HQ, 1.0, s1, {n, v});
+    double* w = c.arena.dalloc(n * Q * v);
+    einsum(c, "nQc,cd->nQd", 1.0, HQ, tc(h->otf_Zm, {v, v}), 0.0, w, {n, Q, v});
+    einsum(c, "Qad,nQd->na", -1.0, Bvv, tn(w, {n, Q, v}), 1.0, s1, {n, v});
+    // M_ab += -2 sum_kl (kl|ab) U_kl + sum_kl (kb|la) U_kl   (A1, A2 hold the y-contracted integrals)
+    einsum(c, "kl,nkla->na", -2.0, tc(h->otf_U, {o, o}), A1T, 1.0, s1, {n, v});
+    einsum(c, "kl,nkla->na", 1.0, tc(h->otf_U, {o, o}), A2T, 1.0, s1, {n, v});
+}
+
+// s1 += M_-11 y1 (the paper's IP block, before the library's sign flip; n vectors of
+// length o), terms as in setup_m11_ip
+static void m11_apply_otf_ip(adc_handle* h, const double* y1, double* s1, long long n) {
+    Ctx& c = h->ctx;
+    const long long o = h->o, v = h->v;
+    Scope sc(c.arena);
+    double* s0 = c.arena.dalloc(n * o);
+    k_eps_apply<<<grid_for(n * o), 256, 0, c.stream>>>(n, o, h->eps, y1, s0);  // zeroth order
+    launch_check(c);
+    axpby(c, n * o, 1.0, s0, 1.0, s1);
+    const T Y = tn(y1, {n, o});
+    const T ovov = tc(h->ovov, {o, v, o, v}), oovv = tc(h->oovv, {o, o, v, v}), oooo = tc(h->oooo, {o, o, o, o}),
+            ooov = tc(h->ooov, {o, o, o, v});
+    const std::vector<long long> d4{n, o, v, v};
+    double* W = c.arena.dalloc(n * o * v * v);
+    double* Z = c.arena.dalloc(n * o * v * v);
+    // X_ij = sum t_il^cd [(jc|ld) - 1/2 (jd|lc)]
+    {
+        const T T4 = tc(h->t, {o, o, v, v});
+        einsum(c, "jcld,nj->nlcd", 1.0, ovov, Y, 0.0, W, d4);
+        einsum(c, "jdlc,nj->nlcd", -0.5, ovov, Y, 1.0, W, d4);
+        einsum(c, "ilcd,nlcd->ni", 1.0, T4, tn(W, d4), 1.0, s1, {n, o});
+        einsum(c, "jlcd,nj->nlcd", 1.0, T4, Y, 0.0, Z, d4);
+        einsum(c, "icld,nlcd->ni", 1.0, ovov, tn(Z, d4), 1.0, s1, {n, o});
+        einsum(c, "idlc,nlcd->ni", -0.5, ovov, tn(Z, d4), 1.0, s1, {n, o});
+    }
+    if (h->order < 3) return;
+    const T T4 = tc(h->t, {o, o, v, v}), T2 = tc(h->t_2, {o, o, v, v}), T1 = tc(h->t1_2, {o, v});
+    // t1(2): X_ij = 2 sum_kc t_k^c (ij|kc) - sum_kc t_k^c (ik|jc)
+    {
+        double* e = c.arena.dalloc(n * o * o * v);
+        const T E = tn(e, {n, o, o, v});
+        einsum(c, "ijkc,nj->nikc", 2.0, ooov, Y, 0.0, e, {n, o, o, v});
+        einsum(c, "ikjc,nj->nikc", -1.0, ooov, Y, 1.0, e, {n, o, o, v});
+        einsum(c, "kc,nikc->ni", 1.0, T1, E, 1.0, s1, {n, o});
+        einsum(c, "jikc,nj->nikc", 2.0, ooov, Y, 0.0, e, {n, o, o, v});
+        einsum(c, "jkic,nj->nikc", -1.0, ooov, Y, 1.0, e, {n, o, o, v});
+        einsum(c, "kc,nikc->ni", 1.0, T1, E, 1.0, s1, {n, o});
+    }
+    // t2(2): X_ij = sum t2_ik^cd [(jc|kd) - 1/2 (kc|jd)]
+    einsum(c, "jckd,nj->nkcd", 1.0, ovov, Y, 0.0, W, d4);
+    einsum(c, "kcjd,nj->nkcd", -0.5, ovov, Y, 1.0, W, d4);
+    einsum(c, "ikcd,nkcd->ni", 1.0, T2, tn(W, d4), 1.0, s1, {n, o});
+    einsum(c, "jkcd,nj->nkcd", 1.0, T2, Y, 0.0, Z, d4);
+    einsum(c, "ickd,nkcd->ni", 1.0, ovov, tn(Z, d4), 1.0, s1, {n, o});
+    einsum(c, "kcid,nkcd->ni", -0.5, ovov, tn(Z, d4), 1.0, s1, {n, o});
+    // oooo, one open line: X_ij = sum t_ik^cd G_jkcd, G_jkcd = sum_lm (jl|km) u_lm^cd, u = t - t^T/2
+    {
+        double* O4 = c.arena.dalloc(n * o * o * o);
+        const T O4T = tn(O4, {n, o, o, o});
+        einsum(c, "jlkm,nj->nlkm", 1.0, oooo, Y, 0.0, O4, {n, o, o, o});
+        einsum(c, "nlkm,lmcd->nkcd", 1.0, O4T, T4, 0.0, W, d4);
+        einsum(c, "nlkm,lmdc->nkcd", -0.5, O4T, T4, 1.0, W, d4);
+        einsum(c, "ikcd,nkcd->ni", 1.0, T4, tn(W, d4), 1.0, s1, {n, o});
+        einsum(c, "jkcd,nj->nkcd", 1.0, T4, Y, 0.0, Z, d4);  // Zt_kcd = sum_j t_jk^cd y_j
+        einsum(c, "nkcd,lmcd->nklm", 1.0, tn(Z, d4), T4, 0.0, O4, {n, o, o, o});
+        einsum(c, "nkcd,lmdc->nklm", -0.5, tn(Z, d4), T4, 1.0, O4, {n, o, o, o});
+        einsum(c, "ilkm,nklm->ni", 1.0, oooo, O4T, 1.0, s1, {n, o});
+    }
+    // ring: X_ij = sum t_ik^ce G_kecj + t_ik^ec GB_kecj with G = (lj|cd) w1 + (jc|ld) w2,
+    // GB = (jc|ld) w1 + (lj|cd) w3 (sums over l, d; w_kl^de); w1 = t/2 - t^T, w2 = -t + 2 t^T,
+    // w3 = -t + t^T/2
+    {
+        double* B1 = c.arena.dalloc(n * o * v * v);  // sum_j (lj|cd) y_j  [n][l][c][d]
+        double* B2 = c.arena.dalloc(n * o * v * v);  // sum_j (jc|ld) y_j
+        einsum(c, "ljcd,nj->nlcd", 1.0, oovv, Y, 0.0, B1, d4);
+        einsum(c, "jcld,nj->nlcd", 1.0, ovov, Y, 0.0, B2, d4);
+        const T B1T = tn(B1, d4), B2T = tn(B2, d4);
+        // W <- G y [n][k][e][c], Z <- GB y
+        einsum(c, "nlcd,klde->nkec", 0.5, B1T, T4, 0.0, W, d4);
+        einsum(c, "nlcd,kled->nkec", -1.0, B1T, T4, 1.0, W, d4);
+        einsum(c, "nlcd,klde->nkec", -1.0, B2T, T4, 1.0, W, d4);
+        einsum(c, "nlcd,kled->nkec", 2.0, B2T, T4, 1.0, W, d4);
+        einsum(c, "nlcd,klde->nkec", 0.5, B2T, T4, 0.0, Z, d4);
+        einsum(c, "nlcd,kled->nkec", -1.0, B2T, T4, 1.0, Z, d4);
+        einsum(c, "nlcd,klde->nkec", -1.0, B1T, T4, 1.0, Z, d4);
+        einsum(c, "nlcd,kled->nkec", 0.5, B1T, T4, 1.0, Z, d4);
+        einsum(c, "ikce,nkec->ni", 1.0, T4, tn(W, d4), 1.0, s1, {n, o});
+        einsum(c, "ikec,nkec->ni", 1.0, T4, tn(Z, d4), 1.0, s1, {n, o});
+        // X^T y: Zr1_kce = sum_j t_jk^ce y_j, Zr2_kce = sum_j t_jk^ec y_j;
+        // sum (li|cd) Ra_lcd + (ic|ld) Rb_lcd with Ra = R(Zr1, w1) + R(Zr2, w3), Rb = R(Zr1, w2) + R(Zr2, w1),
+        // R(Z, w)_lcd = sum_ke Z_kce w_kl^de
+        double* Zr1 = B1;
+        double* Zr2 = B2;
+        einsum(c, "jkce,nj->nkce", 1.0, T4, Y, 0.0, Zr1, d4);
+        einsum(c, "jkec,nj->nkce", 1.0, T4, Y, 0.0, Zr2, d4);
+        einsum(c, "nkce,klde->nlcd", 0.5, B1T, T4, 0.0, W, d4);
+        einsum(c, "nkce,kled->nlcd", -1.0, B1T, T4, 1.0, W, d4);
+        einsum(c, "nkce,klde->nlcd", -1.0, B2T, T4, 1.0, W, d4);
+        einsum(c, "nkce,kled->nlcd", 0.5, B2T, T4, 1.0, W, d4);
+        einsum(c, "nkce,klde->nlcd", -1.0, B1T, T4, 0.0, Z, d4);
+        einsum(c, "nkce,kled->nlcd", 2.0, B1T, T4, 1.0, Z, d4);
+        einsum(c, "nkce,klde->nlcd", 0.5, B2T, T4, 1.0, Z, d4);
+        einsum(c, "nkce,kled->nlcd", -1.0, B2T, T4, 1.0, Z, d4);
+        einsum(c, "licd,nlcd->ni", 1.0, oovv, tn(W, d4), 1.0, s1, {n, o});
+        einsum(c, "icld,nlcd->ni", 1.0, ovov, tn(Z, d4), 1.0, s1, {n, o});
+    }
+    // both lines on the integral: M_ij += -2 sum_kl (ij|kl) U_kl + sum_kl (il|kj) U_kl
+    //                                   + 2 sum_cd (ij|cd) Zm_cd - sum_cd (jc|id) Zm_cd
+    {
+        double* e = c.arena.dalloc(n * o * o * o);
+        einsum(c, "ijkl,nj->nikl", -2.0, oooo, Y, 0.0, e, {n, o, o, o});
+        einsum(c, "ilkj,nj->nikl", 1.0, oooo, Y, 1.0, e, {n, o, o, o});
+        einsum(c, "kl,nikl->ni", 1.0, tc(h->otf_U, {o, o}), tn(e, {n, o, o, o}), 1.0, s1, {n, o});
+        einsum(c, "ijcd,nj->nicd", 2.0, oovv, Y, 0.0, W, d4);
+        einsum(c, "jcid,nj->nicd", -1.0, ovov, Y, 1.0, W, d4);
+        einsum(c, "cd,nicd->ni", 1.0, tc(h->otf_Zm, {v, v}), tn(W, d4), 1.0, s1, {n, o});
+    }
+}
+
+// --------------------------------------------------------------------------
 // Third-order singles t_i^a(3) (Eq. t_singles at k = 3), spin-integrated.
 // They enter only the ADC(3) transition moments, so they are made on first
 // use, in the setup's contraction arithmetic.  With tau = 2t - t(ab swap):
@@ -559,6 +800,15 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
     const int cm = h->opt.contractions >= 0 ? h->opt.contractions : (h->opt.precision != ADC_PREC_FP64 ? 2 : 0);
     h->cmode_sigma = cm;
     h->cmode_setup = cm > 1 ? 1 : cm;
+    h->cmode_refine = cm > 1 ? 1 : cm;
+    if (h->kind == ADC_IP && h->opt.contractions < 0) {
+        // IP: the sigma has no ladder and is cheap (o^3 v^2), and setup beyond its ladder is
+        // o^3 v^3; on strongly correlated inputs the IP spectroscopic factors need these in
+        // FP64 (FP32-accurate setup contractions moved them by ~1.5e-6 at o=20, v=180).  The
+        // ladder of t2(2) stays on the tensor cores; the fast sigma keeps mode 2.
+        h->cmode_setup = 0;
+        h->cmode_refine = 0;
+    }
     c.gemm_mode = h->cmode_setup;
     const long long o = h->o, v = h->v, Q = h->naux, nmo = o + v;
     h->eps = h->dmalloc(nmo);
@@ -605,9 +855,22 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
     Scope setup_scope(c.arena);
     if (h->order >= 3) {
         const double* t = h->t;
-        h->Lt = c.arena.dalloc(o * o * v * v);
+        // the ladder of t outlives setup when the EA 1p-1p block is applied on the fly
+        h->Lt = (h->opt.m11_on_the_fly && h->kind == ADC_EA) ? h->dmalloc(o * o * v * v) : c.arena.dalloc(o * o * v * v);
         fill(c, o * o * v * v, 0.0, h->Lt);
         ladder(h, t, o * o, h->Lt, h->lm_setup);  // sum_cd (ac|bd) t_ij^cd (it feeds M_11 directly)
+        if (h->opt.precision != ADC_PREC_FP64 && h->tc) {
+            // The tensor core's truncating FP32 accumulation biases each promoted partial sum toward
+            // zero, about linearly in the accumulation length.  With L(E) the ladder accumulated in
+            // epochs of E K blocks, 2 L(1) - L(2) removes the linear part of that bias (Richardson
+            // extrapolation in E): measured on t2(2), bias -1.8e-7 -> -6e-8 relative.
+            Scope rs(c.arena);
+            double* L2 = c.arena.dalloc(o * o * v * v);
+            fill(c, o * o * v * v, 0.0, L2);
+            const LadderMode twice{h->lm_setup.planes, 2 * h->lm_setup.epoch1, 2 * h->lm_setup.epoch2};
+            ladder(h, t, o * o, L2, twice);
+            axpby(c, o * o * v * v, -1.0, L2, 2.0, h->Lt);
+        }
         Scope sc(c.arena);
         h->t_2 = h->dmalloc(o * o * v * v);
         double* N = h->t_2;
@@ -661,6 +924,16 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
         c.gemm_mode = saved;
     }
     const long long n1 = h->n1();
+    if (h->opt.m11_on_the_fly) {
+        // step 3 skipped: sigma applies the block from intermediates (the diagonal preconditioner
+        // then takes the zeroth-order one-particle energies)
+        setup_m11_otf(h);
+        h->diag = h->dmalloc(h->dim());
+        k_diag<<<grid_for(h->dim()), 256, 0, c.stream>>>(h->kind == ADC_EA, (int)o, (int)v, h->eps, nullptr, h->diag);
+        launch_check(c);
+        ADC_CUDA(cudaStreamSynchronize(c.stream));
+        return;
+    }
     h->M11 = h->dmalloc(n1 * n1);
     {
         // zeroth order: diag(eps)
@@ -709,8 +982,11 @@ static void sigma_ea(adc_handle* h, const double* Xin, double* Sout, long long n
     double* Yt = c.arena.dalloc(n * blk);
     k_two_minus_swap<<<grid_for(n * blk), 256, 0, c.stream>>>(1, (int)o, (int)v, n, Y2, Yt);
     launch_check(c);
-    // 1p row: M_ab Y_b
-    einsum(c, "nb,ab->na", 1.0, tn(y1, {n, v}), tn(h->M11, {v, v}), 0.0, s1, {n, v});
+    // 1p row: M_ab Y_b (precomputed block, or on the fly)
+    if (h->M11)
+        einsum(c, "nb,ab->na", 1.0, tn(y1, {n, v}), tn(h->M11, {v, v}), 0.0, s1, {n, v});
+    else
+        m11_apply_otf_ea(h, y1, s1, n);
     // coupling row, first order: sum (ad|jc) Y~_jcd.  W^Q_d collects every coupling-row
     // term of the form sum_Qd W^Q_d (Q|da); it is contracted with B^Q_vv once, below.
     double* Wq = c.arena.dalloc(n * Q * v);
@@ -834,8 +1110,13 @@ static void sigma_ip(adc_handle* h, const double* Xin, double* Sout, long long n
         einsum(c, "iakb,njkb->nija", 1.0, tc(h->ovov, {o, v, o, v}), tn(Y2, {n, o, o, v}), 1.0, S2, {n, o, o, v});
         einsum(c, "kjab,nikb->nija", 1.0, tc(h->oovv, {o, o, v, v}), tn(Y2, {n, o, o, v}), 1.0, S2, {n, o, o, v});
     }
-    // negate (M_IP = -M_-) and add the 1h-1h block (already negated)
-    einsum(c, "nj,ij->ni", 1.0, tn(y1, {n, o}), tn(h->M11, {o, o}), -1.0, s1, {n, o});
+    // negate (M_IP = -M_-) and add the 1h-1h block (already negated), or apply it on the fly and negate
+    if (h->M11) {
+        einsum(c, "nj,ij->ni", 1.0, tn(y1, {n, o}), tn(h->M11, {o, o}), -1.0, s1, {n, o});
+    } else {
+        m11_apply_otf_ip(h, y1, s1, n);
+        axpby(c, n * o, 0.0, s1, -1.0, s1);
+    }
     k_gather<<<grid_for(n * o), 256, 0, c.stream>>>(n, o, s1, o, 0, Sout, dim, 0, 0.0);
     launch_check(c);
     axpby(c, n * blk, 0.0, S2, -1.0, S2);
@@ -1104,7 +1385,7 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
         void enter() {
             saved = h->ctx.gemm_mode;
             h->refining = true;
-            h->ctx.gemm_mode = h->opt.refine >= 2 ? 0 : std::min(h->cmode_sigma, 1);
+            h->ctx.gemm_mode = h->opt.refine >= 2 ? 0 : h->cmode_refine;
             on = true;
         }
         ~AccurateOperator() {
@@ -1249,7 +1530,7 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
         const int saved = c.gemm_mode;
         h->refining = true;
         // other contractions FP32-accurate (refine = 1) or FP64 (refine = 2)
-        c.gemm_mode = h->opt.refine >= 2 ? 0 : std::min(h->cmode_sigma, 1);
+        c.gemm_mode = h->opt.refine >= 2 ? 0 : h->cmode_refine;
         try {
             sigma_device(h, X, AX, nroots);
         } catch (...) {
@@ -1729,6 +2010,16 @@ static void setup_unrestricted(adc_handle* h, const double* eps_so, const double
     }
     // one-particle block (EA: M_ab; IP: the paper's M_ij, negated when applied)
     const long long n1 = h->n1();
+    if (h->opt.m11_on_the_fly) {
+        // step 3 skipped: sigma applies the block from intermediates (the diagonal preconditioner
+        // then takes the zeroth-order one-particle energies)
+        setup_m11_otf(h);
+        h->diag = h->dmalloc(h->dim());
+        k_diag<<<grid_for(h->dim()), 256, 0, c.stream>>>(h->kind == ADC_EA, (int)o, (int)v, h->eps, nullptr, h->diag);
+        launch_check(c);
+        ADC_CUDA(cudaStreamSynchronize(c.stream));
+        return;
+    }
     h->M11 = h->dmalloc(n1 * n1);
     {
         std::vector<double> e0((size_t)n1 * n1, 0.0), eh(nso);
@@ -1995,6 +2286,7 @@ int adc_set_options(adc_handle* h, const adc_options* opt) {
     h->opt.refine = opt->refine;
     h->opt.transition_order = opt->transition_order;
     h->opt.refine_res_tol = opt->refine_res_tol;
+    // m11_on_the_fly is fixed at setup
     return ADC_OK;
 }
 
@@ -2053,6 +2345,7 @@ int adc_default_options(adc_options* opt) {
     opt->refine = 1;
     opt->transition_order = 0;
     opt->refine_res_tol = 0.0;
+    opt->m11_on_the_fly = 0;
     return ADC_OK;
 }
 

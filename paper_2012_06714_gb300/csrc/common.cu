@@ -251,6 +251,25 @@ __global__ void __launch_bounds__(256) k_tile_f64(long long M, long long N, long
         }
 }
 
+// As k_reduce_slices for many slices: one warp per output element, lanes over slices,
+// then a shuffle reduction.
+__global__ void k_reduce_slices_warp(int S, long long M, long long N, const double* __restrict__ P, double alpha,
+                                     double beta, double* __restrict__ C, long long ldc) {
+    const long long total = M * N;
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * blockDim.x / 32;
+    for (long long x = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32; x < total; x += warps) {
+        double a = 0.0;
+        for (int s2 = lane; s2 < S; s2 += 32) a += P[s2 * total + x];
+        for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+        if (lane == 0) {
+            const long long m = x / N, n = x - m * N;
+            double* cp = C + m * ldc + n;
+            *cp = beta == 0.0 ? alpha * a : alpha * a + beta * *cp;
+        }
+    }
+}
+
 // C[m * ldc + n] = alpha sum_s P[s][m][n] + beta C[m * ldc + n]
 __global__ void k_reduce_slices(int S, long long M, long long N, const double* __restrict__ P, double alpha, double beta,
                                 double* __restrict__ C, long long ldc) {
@@ -296,7 +315,7 @@ void own_gemm(Ctx& c, long long M, long long N, long long K, double alpha, const
     if (M <= 8) {
         const long long nbn = (N + SK_THREADS - 1) / SK_THREADS;
         const long long kch = (K + SK_THREADS - 1) / SK_THREADS;
-        S = (int)std::max<long long>(1, std::min<long long>({kch, (target + nbn - 1) / nbn, 4096}));
+        S = (int)std::max<long long>(1, std::min<long long>({kch, (target + nbn - 1) / nbn, 512}));
         const long long ks = (kch + S - 1) / S * SK_THREADS;
         S = (int)((K + ks - 1) / ks);
         P = c.arena.dalloc((size_t)S * M * N);
@@ -312,7 +331,7 @@ void own_gemm(Ctx& c, long long M, long long N, long long K, double alpha, const
         }
     } else if (N <= 8) {
         const long long kch = (K + SK_THREADS - 1) / SK_THREADS;
-        S = (int)std::max<long long>(1, std::min<long long>({kch, (target + M - 1) / M, 65535}));
+        S = (int)std::max<long long>(1, std::min<long long>({kch, (target + M - 1) / M, 512}));
         const long long ks = (kch + S - 1) / S * SK_THREADS;
         S = (int)((K + ks - 1) / ks);
         if (M > 0x7fffffffLL) throw Error(-1, "own_gemm: too many rows");
@@ -335,7 +354,10 @@ void own_gemm(Ctx& c, long long M, long long N, long long K, double alpha, const
     }
     ++c.kernels;
     ADC_CUDA(cudaGetLastError());
-    k_reduce_slices<<<grid_for(M * N), 256, 0, c.stream>>>(S, M, N, P, alpha, beta, C, ldc);
+    if (S >= 16)
+        k_reduce_slices_warp<<<grid_for(32 * M * N), 256, 0, c.stream>>>(S, M, N, P, alpha, beta, C, ldc);
+    else
+        k_reduce_slices<<<grid_for(M * N), 256, 0, c.stream>>>(S, M, N, P, alpha, beta, C, ldc);
     ++c.kernels;
     ADC_CUDA(cudaGetLastError());
     c.arena.release(mk);
