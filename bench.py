@@ -262,6 +262,62 @@ def run_davidson_case(args):
     return 0
 
 
+def run_fp64_plain(args):
+    """The plain FP64 comparator at the bench workload (EA-ADC(3), nocc=40 nvir=400 naux=1400,
+    4 roots): the mixed-precision solve to 4 roots is run and timed in full (setup + Davidson +
+    refinement + spectroscopic factors); the FP64 path's setup is timed in full and its sigma
+    on a bounded sample (2 calls of 2 vectors), and its time to 4 roots is extrapolated as
+    setup + (sigma vectors of the mixed solve) x (FP64 seconds per sigma vector) + the mixed
+    solve's non-sigma Davidson time (the same FP64 subspace work on both paths)."""
+    import torch
+
+    from adc_inputs import make_system
+    from paper_2012_06714_gb300 import ADC
+
+    torch.cuda.set_device(0)
+    w = WORKLOAD
+    o, v, naux = w["nocc"], w["nvir"], w["naux"]
+    s = make_system(o, v, naux, seed=0)
+    out = {"workload": f"EA-ADC(3) nocc={o} nvir={v} naux={naux}, 4 roots, |dE| <= 1e-6 Eh, residual 1e-4"}
+    eps, B = torch.from_numpy(s.eps).cuda(), torch.from_numpy(s.B).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = ADC(eps, B, o, order=3, kind="ea", precision="bf16x3", res_tol=1e-4, max_space_per_root=16, keep_per_root=4)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    e, p, _, st = g.davidson(4, tol=1e-6)
+    t2 = time.perf_counter()
+    g.close()
+    mixed = {"setup_s": t1 - t0, "davidson_s": t2 - t1, "total_s": t2 - t0, "sigma_vectors": st["sigma_vectors"],
+             "sigma_s": st["sigma_seconds"], "iterations": st["iterations"], "energies_eh": [float(x) for x in e],
+             "spectroscopic_factors": [float(x) for x in p]}
+    out["mixed"] = mixed
+    t0 = time.perf_counter()
+    g = ADC(eps, B, o, order=3, kind="ea", precision="fp64", res_tol=1e-4)
+    torch.cuda.synchronize()
+    setup64 = time.perf_counter() - t0
+    X = torch.randn((2, g.dim), device="cuda", dtype=torch.float64) / np.sqrt(g.dim)
+    S = torch.empty_like(X)
+    g.sigma(X, out=S)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.sigma(X, out=S)
+    torch.cuda.synchronize()
+    per_vec = (time.perf_counter() - t0) / 2
+    g.close()
+    other = mixed["davidson_s"] - mixed["sigma_s"]
+    est = setup64 + mixed["sigma_vectors"] * per_vec + other
+    out["fp64"] = {"setup_s": setup64, "sigma_s_per_vector": per_vec,
+                   "sigma_tflops": 4.0 * naux * o * v ** 3 / per_vec / 1e12,
+                   "time_to_roots_s_extrapolated": est,
+                   "note": "setup measured; sigma measured on 2 calls of 2 vectors; time to roots = setup + "
+                           "mixed sigma-vector count x FP64 sigma seconds per vector + the mixed run's non-sigma "
+                           "Davidson seconds"}
+    out["speedup_mixed_vs_fp64"] = est / mixed["total_s"]
+    print(json.dumps(out))
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -443,9 +499,13 @@ def main():
     ap.add_argument("--no-roots", action="store_true")
     ap.add_argument("--ladder-case", action="store_true", help="small ladder profiling case (for ncu)")
     ap.add_argument("--davidson-case", action="store_true", help="small Davidson profiling case (for ncu)")
+    ap.add_argument("--fp64-plain", action="store_true",
+                    help="FP64 comparator at the bench workload (setup timed, time to roots extrapolated)")
     args = ap.parse_args()
     if args.davidson_case:
         return run_davidson_case(args)
+    if args.fp64_plain:
+        return run_fp64_plain(args)
     if args.ladder_case:
         return run_ladder_case(args)
     if args.impl == "reference":

@@ -114,6 +114,13 @@ typedef struct {
                              /* EA keeps the ladder of t, o^2 v^2); the preconditioner */
                              /* then uses zeroth-order one-particle energies and      */
                              /* adc_get_tensor("M11") is unavailable.  0 (default)     */
+    const char* tune_cache;  /* NULL (default): tile widths from the cost model; else a */
+                             /* text file of measured tile choices: a tensor-core     */
+                             /* problem not yet in it (ladder GEMM2 tile width and    */
+                             /* auxiliary chunk, generic contraction tile width) is   */
+                             /* timed once on the device with each candidate, and the */
+                             /* fastest is kept (file rewritten; read at setup; one   */
+                             /* table per path, shared by the process's handles)      */
 } adc_options;
 
 /* Fill *opt with the defaults listed above.  Returns ADC_OK or ADC_ERR_ARG (NULL). */

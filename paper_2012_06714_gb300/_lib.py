@@ -55,6 +55,7 @@ class Options(ctypes.Structure):
         ("transition_order", ctypes.c_int),
         ("refine_res_tol", ctypes.c_double),
         ("m11_on_the_fly", ctypes.c_int),
+        ("tune_cache", ctypes.c_char_p),
     ]
 
 
@@ -147,7 +148,7 @@ class ADC:
 
     def __init__(self, eps, B, nocc, order=3, kind="ea", precision="fp64", max_space_per_root=8, max_iter=100,
                  nguess_extra=2, res_tol=0.0, aux_chunk=0, keep_per_root=2, contractions=-1, refine=1,
-                 transition_order=0, refine_res_tol=0.0, m11_on_the_fly=0):
+                 transition_order=0, refine_res_tol=0.0, m11_on_the_fly=0, tune_cache=None):
         lib = load_library()
         self._lib = lib
         opt = Options()
@@ -164,6 +165,7 @@ class ADC:
         opt.transition_order = transition_order
         opt.refine_res_tol = refine_res_tol
         opt.m11_on_the_fly = m11_on_the_fly
+        opt.tune_cache = None if tune_cache is None else os.fsencode(tune_cache)
         self._solver = dict(max_space_per_root=max_space_per_root, max_iter=max_iter, nguess_extra=nguess_extra,
                             res_tol=res_tol, keep_per_root=keep_per_root, refine=refine,
                             transition_order=transition_order, refine_res_tol=refine_res_tol)

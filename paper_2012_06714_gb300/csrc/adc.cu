@@ -828,6 +828,8 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
                                        c.stream));
         }
     }
+    if (h->opt.tune_cache && h->opt.tune_cache[0]) c.tuner = tune_cache_open(h->opt.tune_cache);
+    h->opt.tune_cache = nullptr;  // the caller's string is not kept
     if (h->opt.precision != ADC_PREC_FP64) {
         h->tc = ladder_tc_create(c, h->Bvv, (int)Q, (int)v, h->opt.aux_chunk);
         noalloc_prepare();  // the allocation-free ladder's scratch address on this device, resolved up front
@@ -2346,6 +2348,7 @@ int adc_default_options(adc_options* opt) {
     opt->transition_order = 0;
     opt->refine_res_tol = 0.0;
     opt->m11_on_the_fly = 0;
+    opt->tune_cache = nullptr;
     return ADC_OK;
 }
 

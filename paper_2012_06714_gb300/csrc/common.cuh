@@ -135,6 +135,7 @@ struct Ctx {
     // split BF16 planes (K-major GEMM operand order) of operands marked constant
     std::map<std::pair<const void*, std::string>, void*> bf16cache;
     int* d_err = nullptr;  // device flag raised by a bounded wait that gave up (tensor-core GEMMs)
+    void* tuner = nullptr;  // TuneCache of the tile autotuner (ladder_tc.cuh), or NULL: cost-model tiles
     // side streams for concurrent K slices of a contraction, with their fork / join events
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> side_join;

@@ -23,7 +23,13 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstdlib>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
 #include <mutex>
+#include <string>
+#include <vector>
 
 #include "ladder_tc.cuh"
 
@@ -1115,7 +1121,7 @@ struct LadderTC {
     const double* Bvv = nullptr;        // FP64 source (owned by the caller, outlives this object)
     int nplanes = 0;                    // BF16 planes held (2; 3 once a three-plane ladder was asked for)
     __nv_bfloat16 *Bs[3] = {}, *Bp[3] = {};  // BF16 planes of B^Q in the GEMM1-A and GEMM2-B layouts
-    CUtensorMap mBs[3], mBp2[3], mBp3[3];     // GEMM2-B maps exist for both tile widths
+    CUtensorMap mBs[3];                       // GEMM1-A maps
     int* d_err = nullptr;
     ~LadderTC() {
         for (int p = 0; p < 3; ++p) {
@@ -1148,8 +1154,6 @@ void split_B(LadderTC& L, Ctx& c, int planes) {
     for (int p = 0; p < planes; ++p) {
         L.mBs[p] = make_map(L.Bs[p], (long long)L.naux * L.vp, L.vp, BM);
         // GEMM2-B boxes: one CTA's half of the tile in pair mode
-        L.mBp2[p] = make_map(L.Bp[p], L.v, (long long)L.naux * L.vp, L.pair2 ? L.bn2[2] / 2 : L.bn2[2]);
-        L.mBp3[p] = make_map(L.Bp[p], L.v, (long long)L.naux * L.vp, L.pair2 ? L.bn2[3] / 2 : L.bn2[3]);
     }
     L.nplanes = planes;
 }
@@ -1182,9 +1186,11 @@ namespace {
 // The chunk loop shared by both entry points: groups of mg matrices, chunks of
 // qc auxiliary functions; scratch xt (split X^T planes of one group) and zt (Z planes).
 void run_ladder(LadderTC& L, Ctx& c, const double* X, long long nmat, double* out, const LadderMode& md, Planes xt,
-                Planes zt, long long mg, int qc) {
+                Planes zt, long long mg, int qc, int bn2) {
     const int v = L.v, vp = L.vp, naux = L.naux, planes = md.planes;
-    const int bn1 = BN1[planes], bn2 = L.bn2[planes];
+    const int bn1 = BN1[planes];
+    CUtensorMap mBp[3];  // GEMM2-B maps: one CTA's half of the tile in pair mode
+    for (int p = 0; p < planes; ++p) mBp[p] = make_map(L.Bp[p], L.v, (long long)L.naux * L.vp, L.pair2 ? bn2 / 2 : bn2);
     for (long long m0 = 0; m0 < nmat; m0 += mg) {
         const long long nm = std::min(mg, nmat - m0);
         k_split_XT<<<grid_for(nm * vp * vp), 256, 0, c.stream>>>(X + m0 * v * v, nm, v, vp, planes, xt);
@@ -1212,7 +1218,7 @@ void run_ladder(LadderTC& L, Ctx& c, const double* X, long long nmat, double* ou
             Maps m2;
             for (int p = 0; p < planes; ++p) {
                 m2.a[p] = make_map(zt.p[p], nm * v, (long long)qn * vp, BM);
-                m2.b[p] = planes == 3 ? L.mBp3[p] : L.mBp2[p];
+                m2.b[p] = mBp[p];
             }
             Epi e2{};
             e2.mode = 1;
@@ -1236,6 +1242,90 @@ void check_err(LadderTC& L, Ctx& c) {
 
 }  // namespace
 
+// ---- tile autotuner ------------------------------------------------------------
+// Tile choices measured on the device and kept in a text file shared by every handle
+// of the process that names it (one line per problem: key, then the chosen values).
+struct TuneCache {
+    std::mutex mu;
+    std::string path;
+    std::map<std::string, std::vector<int>> table;
+};
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::string, std::unique_ptr<TuneCache>> g_tune;
+
+bool tune_get(TuneCache* t, const std::string& key, std::vector<int>& v) {
+    std::lock_guard<std::mutex> lk(t->mu);
+    auto it = t->table.find(key);
+    if (it == t->table.end()) return false;
+    v = it->second;
+    return true;
+}
+
+void tune_put(TuneCache* t, const std::string& key, const std::vector<int>& v) {
+    std::lock_guard<std::mutex> lk(t->mu);
+    t->table[key] = v;
+    FILE* f = std::fopen(t->path.c_str(), "w");
+    if (!f) return;  // the choices still hold for this process
+    for (auto& kv : t->table) {
+        std::fprintf(f, "%s", kv.first.c_str());
+        for (int x : kv.second) std::fprintf(f, " %d", x);
+        std::fprintf(f, "\n");
+    }
+    std::fclose(f);
+}
+
+// milliseconds of one run of f on c.stream (CUDA events; synchronises)
+template <class F>
+float time_on_stream(Ctx& c, F f) {
+    cudaEvent_t e0, e1;
+    ADC_CUDA(cudaEventCreate(&e0));
+    ADC_CUDA(cudaEventCreate(&e1));
+    ADC_CUDA(cudaEventRecord(e0, c.stream));
+    f();
+    ADC_CUDA(cudaEventRecord(e1, c.stream));
+    ADC_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    ADC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms;
+}
+
+// distinct multiples of 16 in [16, maxbn], the cost model's choice first
+std::vector<int> bn_candidates(int n, int maxbn, std::initializer_list<int> extra) {
+    std::vector<int> c{pick_bn(n, maxbn)};
+    for (int b : extra)
+        if (b >= 16 && b <= maxbn && b % 16 == 0 && std::find(c.begin(), c.end(), b) == c.end()) c.push_back(b);
+    return c;
+}
+}  // namespace
+
+TuneCache* tune_cache_open(const char* path) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto& slot = g_tune[path];
+    if (!slot) {
+        slot.reset(new TuneCache());
+        slot->path = path;
+        if (FILE* f = std::fopen(path, "r")) {
+            char line[512];
+            while (std::fgets(line, sizeof line, f)) {
+                // key: the first token; values: the integers after it
+                char* save = nullptr;
+                char* tok = strtok_r(line, " \t\n", &save);
+                if (!tok) continue;
+                std::string key = tok;
+                std::vector<int> vals;
+                while ((tok = strtok_r(nullptr, " \t\n", &save))) vals.push_back(std::atoi(tok));
+                if (!vals.empty()) slot->table[key] = vals;
+            }
+            std::fclose(f);
+        }
+    }
+    return slot.get();
+}
+
 void ladder_tc_apply(LadderTC& L, Ctx& c, const double* X, long long nmat, double* out, const LadderMode& md) {
     const int v = L.v, vp = L.vp, naux = L.naux, planes = md.planes;
     if (nmat <= 0) return;
@@ -1255,13 +1345,52 @@ void ladder_tc_apply(LadderTC& L, Ctx& c, const double* X, long long nmat, doubl
     mg = std::min(mg, nmat);
     int qc = L.chunk > 0 ? std::min(L.chunk, qmax) : (int)std::max<long long>(1, budget / (per_mq * mg));
     qc = std::max(1, std::min(qc, qmax));
+    int bn2 = L.bn2[planes];
     Arena::Mark mk = c.arena.mark();
-    Planes xt{}, zt{};
-    for (int p = 0; p < planes; ++p) {
-        xt.p[p] = (__nv_bfloat16*)c.arena.alloc(mg * vp * vp * 2);
-        zt.p[p] = (__nv_bfloat16*)c.arena.alloc(mg * v * (long long)qc * vp * 2);
+    auto scratch = [&](int q) {
+        Planes xt{}, zt{};
+        for (int p = 0; p < planes; ++p) {
+            xt.p[p] = (__nv_bfloat16*)c.arena.alloc(mg * vp * vp * 2);
+            zt.p[p] = (__nv_bfloat16*)c.arena.alloc(mg * v * (long long)q * vp * 2);
+        }
+        return std::make_pair(xt, zt);
+    };
+    if (c.tuner && !c.timing && L.chunk <= 0) {
+        // GEMM2 tile width and auxiliary chunk: measured once per problem, cached
+        TuneCache* tc = (TuneCache*)c.tuner;
+        const std::string key = "ladder:sm" + std::to_string(dev_info().num_sms) + ":v" + std::to_string(v) + ":naux" +
+                                std::to_string(naux) + ":nmat" + std::to_string(nmat) + ":p" + std::to_string(planes) +
+                                ":e" + std::to_string(md.epoch1) + "," + std::to_string(md.epoch2);
+        std::vector<int> got;
+        if (tune_get(tc, key, got) && got.size() == 2) {
+            bn2 = got[0];
+            qc = std::max(1, std::min(got[1], qmax));
+        } else {
+            const int maxbn = planes == 3 ? 128 : 256;
+            std::vector<int> qcs{qc};
+            if (qc / 2 >= 1) qcs.push_back(qc / 2);
+            if (2 * qc <= qmax) qcs.push_back(2 * qc);
+            double* tmp = c.arena.dalloc((size_t)nmat * v * v);  // timing runs accumulate here
+            ADC_CUDA(cudaMemsetAsync(tmp, 0, (size_t)nmat * v * v * sizeof(double), c.stream));
+            float best = 1e30f;
+            int bb = bn2, bq = qc;
+            for (int q : qcs) {
+                Arena::Mark m2 = c.arena.mark();
+                auto sc = scratch(q);
+                for (int b : bn_candidates(v, maxbn, {256, 224, 208, 192, 160, 128})) {
+                    const float ms = time_on_stream(c, [&] { run_ladder(L, c, X, nmat, tmp, md, sc.first, sc.second, mg, q, b); });
+                    if (ms < best) best = ms, bb = b, bq = q;
+                }
+                c.arena.release(m2);
+            }
+            check_err(L, c);
+            bn2 = bb;
+            qc = bq;
+            tune_put(tc, key, {bn2, qc});
+        }
     }
-    run_ladder(L, c, X, nmat, out, md, xt, zt, mg, qc);
+    auto sc = scratch(qc);
+    run_ladder(L, c, X, nmat, out, md, sc.first, sc.second, mg, qc, bn2);
     check_err(L, c);
     c.arena.release(mk);
 }
@@ -1296,7 +1425,7 @@ bool ladder_tc_apply_scratch(LadderTC& L, Ctx& c, const double* X, long long nma
     zt.p[1] = zt.p[0] + mg * v * (long long)qc * vp;
     ADC_CUDA(cudaMemsetAsync(L.d_err, 0, sizeof(int), c.stream));  // clear a timeout of an earlier call
     ADC_CUDA(cudaMemsetAsync(out, 0, (size_t)nmat * v * v * sizeof(double), c.stream));
-    run_ladder(L, c, X, nmat, out, md, xt, zt, mg, qc);
+    run_ladder(L, c, X, nmat, out, md, xt, zt, mg, qc, L.bn2[planes]);
     check_err(L, c);
     return true;
 }
@@ -1307,10 +1436,40 @@ bool tc_gemm_fits(long long M, long long N, long long K) {
     return M < (1LL << 30) && N < (1LL << 30) && K < (1LL << 30) && K >= 64;
 }
 
+static void tc_gemm_bn(Ctx& c, const void* const* A, const void* const* B, long long M, long long N, long long Kp,
+                       double algo_flops, double* C, int BN);
+
 void tc_gemm(Ctx& c, const void* const* A, const void* const* B, long long M, long long N, long long Kp, double algo_flops,
              double* C) {
     if (!c.d_err) throw Error(-1, "tc_gemm: no device error flag");
-    const int BN = pick_bn((int)std::min<long long>(N, 1 << 20), 256);
+    const int n = (int)std::min<long long>(N, 1 << 20);
+    int BN = pick_bn(n, 256);
+    if (c.tuner && !c.timing) {
+        // tile width measured once per shape (every run overwrites C, so the runs are interchangeable)
+        TuneCache* tc = (TuneCache*)c.tuner;
+        const std::string key = "gemm:sm" + std::to_string(dev_info().num_sms) + ":M" + std::to_string(M) + ":N" +
+                                std::to_string(N) + ":K" + std::to_string(Kp);
+        std::vector<int> got;
+        if (tune_get(tc, key, got) && got.size() == 1) {
+            BN = got[0];
+        } else {
+            float best = 1e30f;
+            int bb = BN, last = BN;
+            for (int b : bn_candidates(n, 256, {256, 192, 128, 64})) {
+                const float ms = time_on_stream(c, [&] { tc_gemm_bn(c, A, B, M, N, Kp, algo_flops, C, b); });
+                last = b;
+                if (ms < best) best = ms, bb = b;
+            }
+            tune_put(tc, key, {bb});
+            if (bb == last) return;  // C already holds the result of the chosen tile width
+            BN = bb;
+        }
+    }
+    tc_gemm_bn(c, A, B, M, N, Kp, algo_flops, C, BN);
+}
+
+static void tc_gemm_bn(Ctx& c, const void* const* A, const void* const* B, long long M, long long N, long long Kp,
+                       double algo_flops, double* C, int BN) {
     const bool pair = true;
     const long long tiles = ((M + 255) / 256) * ((N + BN - 1) / BN);
     // K slices, each its own launch on a side stream (the launches of few tiles run side by side)

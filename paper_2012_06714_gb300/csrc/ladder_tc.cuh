@@ -32,6 +32,12 @@ bool ladder_tc_apply_scratch(LadderTC& L, Ctx& c, const double* X, long long nma
 // [M][Kp], B[p] [N][Kp] (Kp a multiple of 8, zeros beyond K), FP32 partial
 // sums promoted every 16 K blocks (64 deep).  A bounded device wait that gives
 // up raises c.d_err.
+// Tile autotuner: measured tile choices (GEMM2 tile width and auxiliary chunk of the
+// ladder, tile width of the generic contractions) kept per problem in a text file;
+// one instance per path, shared by the process's handles (Ctx::tuner).
+struct TuneCache;
+TuneCache* tune_cache_open(const char* path);
+
 // the shape fits the kernel's 32-bit tile coordinates and K >= 64 (one K block)
 bool tc_gemm_fits(long long M, long long N, long long K);
 void tc_gemm(Ctx& c, const void* const* A, const void* const* B, long long M, long long N, long long Kp, double algo_flops,
