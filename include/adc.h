@@ -174,9 +174,13 @@ int adc_set_options(adc_handle* h, const adc_options* opt);
  * aux_chunk: auxiliary functions per chunk of the IP third-order coupling
  * intermediate sum_e B^Q_ie t_jk^de (naux x o^3 x v); 0 = automatic (chunks of
  * at most 2^27 elements).
- * adc_get_tensor returns "t2", "t2_2", "t1_2" and "M11" in these spin-orbital
- * dimensions (M11: the paper's M_+ / M_- one-particle block).  adc_davidson and
- * adc_mp_energy are not available on these handles yet.
+ * adc_get_tensor returns "t2", "t2_2", "t1_2", "t1_3" (third-order singles, made
+ * on first use) and "M11" in these spin-orbital dimensions (M11: the paper's
+ * M_+ / M_- one-particle block).  adc_davidson runs with metric S = 1 (the
+ * antisymmetric pair basis is orthonormal) and a preconditioner of diag(M11)
+ * and the zeroth-order pair energies; its spectroscopic factors are those of
+ * one spin-orbital component, P = sum_p X_p^2 with T through order n (a
+ * Koopmans state has P = 1).  adc_mp_energy is not available on these handles.
  * Errors: ADC_ERR_ARG, ADC_ERR_OOM, ADC_ERR_CUDA (message: adc_last_error(NULL)).
  */
 int adc_setup_unrestricted(const double* eps_a, const double* eps_b, const double* Ba, const double* Bb, int nocc_a,

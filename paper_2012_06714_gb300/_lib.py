@@ -429,6 +429,23 @@ class ADCUnrestricted:
         if rc != ADC_OK:
             raise ADCError(rc, self._lib.adc_last_error(self._h).decode())
 
+    def davidson(self, nroots, tol=1e-8, want_vectors=False, res_tol=0.0, max_iter=100, max_space_per_root=8):
+        """(energies, spectroscopic factors (one spin-orbital component), vectors or None, stats dict)."""
+        opt = Options()
+        self._lib.adc_default_options(ctypes.byref(opt))
+        opt.res_tol, opt.max_iter, opt.max_space_per_root = res_tol, max_iter, max_space_per_root
+        self._check(self._lib.adc_set_options(self._h, ctypes.byref(opt)))
+        e = np.zeros(nroots)
+        p = np.zeros(nroots)
+        vec = np.zeros((nroots, self.dim)) if want_vectors else None
+        st = np.zeros(8)
+        rc = self._lib.adc_davidson(self._h, nroots, tol, None, e.ctypes.data, p.ctypes.data,
+                                    None if vec is None else vec.ctypes.data, st.ctypes.data)
+        stats = dict(iterations=int(st[0]), sigma_vectors=int(st[1]), seconds=st[2], max_residual=st[3], status=rc)
+        if rc not in (ADC_OK, ADC_ERR_NOT_CONVERGED):
+            self._check(rc)
+        return e, p, vec, stats
+
     def sigma(self, X):
         """sigma = M X (EA) or -M_- X (IP) for host X [nvec, dim]."""
         X = np.ascontiguousarray(np.atleast_2d(X), dtype=np.float64)

@@ -1223,6 +1223,11 @@ struct Davidson {
     std::vector<double> G;  // host [ldg][ldg]: G_ij = (SV_i . W_j + SV_j . W_i) / 2 for i, j < k
 
     void metric(const double* in, double* out, long long nvec, int inverse) {
+        if (h->unrestricted) {  // the antisymmetric pair basis of an open-shell reference: S = 1
+            if (out != in)
+                ADC_CUDA(cudaMemcpyAsync(out, in, (size_t)nvec * dim * sizeof(double), cudaMemcpyDeviceToDevice, h->ctx.stream));
+            return;
+        }
         k_metric<<<grid_for(nvec * dim), 256, 0, h->ctx.stream>>>(h->kind == ADC_EA, h->o, h->v, nvec, in, out, inverse);
         launch_check(h->ctx);
     }
@@ -1309,6 +1314,8 @@ struct Davidson {
         return kept;
     }
 };
+
+static void specfac_unrestricted(adc_handle* h, const double* Y, int nroots, double* specfac);
 
 static int davidson(adc_handle* h, int nroots, double tol, const double* guess, double* energies, double* specfac,
                     double* vectors, double* stats) {
@@ -1600,7 +1607,9 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
     // outputs
     for (int r = 0; r < nroots; ++r) energies[r] = w[r];
     if (vectors) ADC_CUDA(cudaMemcpyAsync(vectors, X, (size_t)nroots * dim * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
-    if (specfac) {
+    if (specfac && h->unrestricted) {
+        specfac_unrestricted(h, X, nroots, specfac);
+    } else if (specfac) {
         // X_p = sum_nu T_{p,nu} (S Y~)_nu, P = 2 sum_p X_p^2  (Appendix); Ritz vectors are S-normalised
         const long long o = h->o, v = h->v, nmo = o + v;
         double* SX = SR;
@@ -1874,6 +1883,21 @@ __global__ void k_pairs_to_full(int ea, long long n, long long np, int o, int v,
     }
 }
 
+// preconditioner diagonal of an unrestricted handle: [diag of the applied 1p/1h block,
+// zeroth-order pair energies] (EA: e_a + e_b - e_i; IP: -(e_i + e_j - e_a))
+__global__ void k_diag_pairs(int ea, long long n1, long long np, int o, const int* __restrict__ idx,
+                             const double* __restrict__ eps, const double* __restrict__ M11, double* __restrict__ D) {
+    GRID_STRIDE(x, n1 + np) {
+        if (x < n1) {
+            D[x] = ea ? M11[x * n1 + x] : -M11[x * n1 + x];
+        } else {
+            const long long q = x - n1;
+            const int p0 = idx[q], p1 = idx[np + q], p2 = idx[2 * np + q];
+            D[x] = ea ? eps[o + p1] + eps[o + p2] - eps[p0] : -(eps[p0] + eps[p1] - eps[o + p2]);
+        }
+    }
+}
+
 // S[r][off + q] = alpha * F[r][pair q]
 __global__ void k_full_to_pairs(int ea, long long n, long long np, int o, int v, const int* __restrict__ idx,
                                 const double* __restrict__ F, double alpha, double* __restrict__ S, long long lds, long long off) {
@@ -2012,16 +2036,6 @@ static void setup_unrestricted(adc_handle* h, const double* eps_so, const double
     }
     // one-particle block (EA: M_ab; IP: the paper's M_ij, negated when applied)
     const long long n1 = h->n1();
-    if (h->opt.m11_on_the_fly) {
-        // step 3 skipped: sigma applies the block from intermediates (the diagonal preconditioner
-        // then takes the zeroth-order one-particle energies)
-        setup_m11_otf(h);
-        h->diag = h->dmalloc(h->dim());
-        k_diag<<<grid_for(h->dim()), 256, 0, c.stream>>>(h->kind == ADC_EA, (int)o, (int)v, h->eps, nullptr, h->diag);
-        launch_check(c);
-        ADC_CUDA(cudaStreamSynchronize(c.stream));
-        return;
-    }
     h->M11 = h->dmalloc(n1 * n1);
     {
         std::vector<double> e0((size_t)n1 * n1, 0.0), eh(nso);
@@ -2119,7 +2133,193 @@ static void setup_unrestricted(adc_handle* h, const double* eps_so, const double
             perm4(c, Xc, {o, o, o, v}, {0, 2, 1, 3}, h->m12, 1.0, 1.0);
         }
     }
+    // Davidson preconditioner diagonal (S = 1 in the antisymmetric pair basis)
+    h->diag = h->dmalloc(h->dim());
+    k_diag_pairs<<<grid_for(h->dim()), 256, 0, c.stream>>>(h->kind == ADC_EA, n1, h->npairs(), (int)o, h->pair_idx, h->eps,
+                                                            h->M11, h->diag);
+    launch_check(c);
     ADC_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+// Third-order singles of an open-shell reference (Eq. t_singles at k = 3, the
+// spin-orbital form: t antisymmetric, <pq||rs>), FP64, made on first use:
+//   D t(3) = A + (2 E1 + E2 + 4 E3 + 2 E4)/4 - (2 F1 + 4 F2 + F3 + 2 F4)/4,  t(3) += 1/2 sum t_ij^ab t_j^b(2)
+// A: the t1(2)-, t2(2)- and singles-shaped terms; E1..E4 / F1..F4: the connected
+// triples-shaped term by particle / hole half.  Every integral with three virtual
+// indices goes through B^Q (Eq. 19); E2 runs in auxiliary chunks.
+static void make_t1_third_order_u(adc_handle* h) {
+    if (h->t1_3 || h->order < 3) return;
+    Ctx& c = h->ctx;
+    const long long o = h->o, v = h->v, Q = h->naux, o2v2 = o * o * v * v;
+    double* out = h->dmalloc(o * v);
+    Scope sc(c.arena);
+    const T T4 = tn(h->t, {o, o, v, v}), T2 = tn(h->t_2, {o, o, v, v}), t1 = tn(h->t1_2, {o, v});
+    const T Bov = tn(h->Bov, {Q, o, v}), Bvv = tn(h->Bvv, {Q, v, v});
+    double* num = c.arena.dalloc(o * v);
+    double* G = c.arena.dalloc(Q * std::max(o * v, o * o));
+    // A = sum (ia|jb) t_j^b - sum (ji|ab) t_j^b + singles(t2(2)),
+    // singles(x) = -sum_Q sum_kcd B^Q_kc B^Q_ad x_ik^cd - 1/2 sum <kl||ic> x_kl^ac
+    einsum(c, "iajb,jb->ia", 1.0, tn(h->ovov, {o, v, o, v}), t1, 0.0, num, {o, v});
+    einsum(c, "jiab,jb->ia", -1.0, tn(h->oovv, {o, o, v, v}), t1, 1.0, num, {o, v});
+    einsum(c, "Qkc,ikcd->Qid", 1.0, Bov, T2, 0.0, G, {Q, o, v});
+    einsum(c, "Qid,Qad->ia", -1.0, tn(G, {Q, o, v}), Bvv, 1.0, num, {o, v});
+    einsum(c, "klic,klac->ia", -0.5, tn(h->g_ooov, {o, o, o, v}), T2, 1.0, num, {o, v});
+    // E1/2 = sum t_ij^ad Y_jd, Y_jd = 2 sum_Q sum_b B^Q_bd (sum_kc B^Q_kc t_jk^bc)
+    double* Y = c.arena.dalloc(o * v);
+    einsum(c, "Qkc,jkbc->Qjb", 1.0, Bov, T4, 0.0, G, {Q, o, v});
+    einsum(c, "Qjb,Qbd->jd", 2.0, tn(G, {Q, o, v}), Bvv, 0.0, Y, {o, v});
+    einsum(c, "ijad,jd->ia", 0.5, T4, tn(Y, {o, v}), 1.0, num, {o, v});
+    {
+        // E2/4 = 1/2 sum t_jk^ad V_jkdi, V_jkdi = sum_Q sum_b B^Q_bd sum_c t_jk^bc B^Q_ic
+        Scope s2(c.arena);
+        const long long per = o * o * v * o;
+        double* V = c.arena.dalloc(per);
+        const long long qc = h->opt.aux_chunk > 0 ? std::min<long long>(Q, h->opt.aux_chunk)
+                                                  : std::max(1LL, std::min(Q, (1LL << 27) / std::max(per, 1LL)));
+        double* W = c.arena.dalloc(qc * per);  // [Q][j][k][b][i]
+        for (long long q0 = 0; q0 < Q; q0 += qc) {
+            const long long nq = std::min(qc, Q - q0);
+            einsum(c, "jkbc,Qic->Qjkbi", 1.0, T4, tn(h->Bov + q0 * o * v, {nq, o, v}), 0.0, W, {nq, o, o, v, o});
+            einsum(c, "Qjkbi,Qbd->jkdi", 1.0, tn(W, {nq, o, o, v, o}), tn(h->Bvv + q0 * v * v, {nq, v, v}),
+                   q0 == 0 ? 0.0 : 1.0, V, {o, o, v, o});
+        }
+        einsum(c, "jkad,jkdi->ia", 0.5, T4, tn(V, {o, o, v, o}), 1.0, num, {o, v});
+    }
+    {
+        // E3 = -(sum_Q B^Q_ad B^Q_kc R_ikcd - sum_Q B^Q_ka B^Q_cd R_ikcd), R_ikcd = sum_jb t_ij^bd t_jk^bc
+        Scope s2(c.arena);
+        double* R = c.arena.dalloc(o2v2);
+        einsum(c, "ijbd,jkbc->ikcd", 1.0, T4, T4, 0.0, R, {o, o, v, v});
+        einsum(c, "Qkc,ikcd->Qid", 1.0, Bov, tn(R, {o, o, v, v}), 0.0, G, {Q, o, v});
+        einsum(c, "Qid,Qad->ia", -1.0, tn(G, {Q, o, v}), Bvv, 1.0, num, {o, v});
+        einsum(c, "Qcd,ikcd->Qik", 1.0, Bvv, tn(R, {o, o, v, v}), 0.0, G, {Q, o, o});
+        einsum(c, "Qik,Qka->ia", 1.0, tn(G, {Q, o, o}), Bov, 1.0, num, {o, v});
+    }
+    {
+        // E4/2 = -1/2 (sum_Q B^Q_ad B^Q_ic rho_cd - sum_Q B^Q_ia B^Q_cd rho_cd), rho_cd = sum t_jk^bc t_jk^bd
+        double* rho = c.arena.dalloc(v * v);
+        double* r = c.arena.dalloc(Q);
+        einsum(c, "jkbc,jkbd->cd", 1.0, T4, T4, 0.0, rho, {v, v});
+        einsum(c, "Qic,cd->Qid", 1.0, Bov, tn(rho, {v, v}), 0.0, G, {Q, o, v});
+        einsum(c, "Qid,Qad->ia", -0.5, tn(G, {Q, o, v}), Bvv, 1.0, num, {o, v});
+        einsum(c, "Qcd,cd->Q", 1.0, Bvv, tn(rho, {v, v}), 0.0, r, {Q});
+        einsum(c, "Qia,Q->ia", 0.5, Bov, tn(r, {Q}), 1.0, num, {o, v});
+    }
+    {
+        // F terms with <ia||jk> = (ij|ak) - (ik|aj), stored gov[i][a][j][k]
+        Scope s2(c.arena);
+        double* gov = c.arena.dalloc(o * v * o * o);
+        perm4(c, h->ooov, {o, o, o, v}, {0, 3, 1, 2}, gov, 1.0, 0.0);
+        perm4(c, h->ooov, {o, o, o, v}, {0, 3, 2, 1}, gov, -1.0, 1.0);
+        const T GOV = tn(gov, {o, v, o, o});
+        // -F1/2: F1 = sum t_il^ab U1_lb, U1_lb = sum t_jk^bc <lc||jk>
+        double* U1 = c.arena.dalloc(o * v);
+        einsum(c, "jkbc,lcjk->lb", 1.0, T4, GOV, 0.0, U1, {o, v});
+        einsum(c, "ilab,lb->ia", -0.5, T4, tn(U1, {o, v}), 1.0, num, {o, v});
+        // -F2: F2 = -sum <lc||ik> t_jk^bc t_jl^ab
+        double* U2 = c.arena.dalloc(o * o * o * v);  // [l][i][j][b]
+        einsum(c, "lcik,jkbc->lijb", 1.0, GOV, T4, 0.0, U2, {o, o, o, v});
+        einsum(c, "lijb,jlab->ia", 1.0, tn(U2, {o, o, o, v}), T4, 1.0, num, {o, v});
+        // -F3/4: F3 = sum <la||jk> t_jk^bc t_il^bc
+        double* U3 = c.arena.dalloc(o * o * o * o);  // [j][k][i][l]
+        einsum(c, "jkbc,ilbc->jkil", 1.0, T4, T4, 0.0, U3, {o, o, o, o});
+        einsum(c, "lajk,jkil->ia", -0.25, GOV, tn(U3, {o, o, o, o}), 1.0, num, {o, v});
+        // -F4/2: F4 = -sum <la||ik> t_jk^bc t_jl^bc
+        double* U4 = c.arena.dalloc(o * o);
+        einsum(c, "jkbc,jlbc->kl", 1.0, T4, T4, 0.0, U4, {o, o});
+        einsum(c, "laik,kl->ia", 0.5, GOV, tn(U4, {o, o}), 1.0, num, {o, v});
+    }
+    k_div_D1<<<grid_for(o * v), 256, 0, c.stream>>>((int)o, (int)v, h->eps, num);
+    launch_check(c);
+    ADC_CUDA(cudaMemcpyAsync(out, num, o * v * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    einsum(c, "ijab,jb->ia", 0.5, T4, t1, 1.0, out, {o, v});
+    h->t1_3 = out;
+}
+
+// Spectroscopic factors of an open-shell reference (Eq. spec_factors with T from
+// Eqs. T_ea, T_ip through order n, spin-orbital form): X_p = sum_nu T_p,nu Y_nu for
+// Y normalised (S = 1), P = sum_p X_p^2 (one spin-orbital component: a Koopmans
+// state has P = 1).  Pair columns act through the full antisymmetric tensor F
+// (sum over i, a<b of T y = 1/2 sum over i, a, b of T F).
+static void specfac_unrestricted(adc_handle* h, const double* Y, int nroots, double* specfac) {
+    Ctx& c = h->ctx;
+    Scope sc(c.arena);
+    const long long o = h->o, v = h->v, nso = o + v, n1 = h->n1(), np = h->npairs(), dim = h->dim(), n = nroots;
+    const bool ea = h->kind == ADC_EA;
+    const bool third = h->order >= 3 && h->opt.transition_order != 2;
+    if (third) make_t1_third_order_u(h);
+    const long long blk = ea ? o * v * v : o * o * v;
+    double* y1 = c.arena.dalloc(n * n1);
+    double* F = c.arena.dalloc(n * blk);
+    k_gather<<<grid_for(n * n1), 256, 0, c.stream>>>(n, n1, Y, dim, 0, y1, n1, 0, 0.0);
+    launch_check(c);
+    fill(c, n * blk, 0.0, F);
+    k_pairs_to_full<<<grid_for(n * np), 256, 0, c.stream>>>(ea, n, np, (int)o, (int)v, h->pair_idx, Y, dim, n1, F);
+    launch_check(c);
+    const T T4 = tn(h->t, {o, o, v, v}), Y1 = tn(y1, {n, n1});
+    double* tt = c.arena.dalloc(o * o * v * v);  // t2(1) [+ t2(2)]
+    ADC_CUDA(cudaMemcpyAsync(tt, h->t, o * o * v * v * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    if (third) axpby(c, o * o * v * v, 1.0, h->t_2, 1.0, tt);
+    double* t1x = c.arena.dalloc(o * v);  // t1(2) [+ t1(3) + 1/2 sum t t1(2)]
+    if (h->t1_2) {
+        ADC_CUDA(cudaMemcpyAsync(t1x, h->t1_2, o * v * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    } else {
+        // ADC(2): second-order singles of the spin-orbital form, -(kc|ad) t_ik^cd - 1/2 <kl||ic> t_kl^ac
+        const long long Q = h->naux;
+        double* G = c.arena.dalloc(Q * o * v);
+        einsum(c, "Qkc,ikcd->Qid", 1.0, tn(h->Bov, {Q, o, v}), T4, 0.0, G, {Q, o, v});
+        einsum(c, "Qid,Qad->ia", -1.0, tn(G, {Q, o, v}), tn(h->Bvv, {Q, v, v}), 0.0, t1x, {o, v});
+        einsum(c, "klic,klac->ia", -0.5, tn(h->g_ooov, {o, o, o, v}), T4, 1.0, t1x, {o, v});
+        k_div_D1<<<grid_for(o * v), 256, 0, c.stream>>>((int)o, (int)v, h->eps, t1x);
+        launch_check(c);
+    }
+    if (third) {
+        axpby(c, o * v, 1.0, h->t1_3, 1.0, t1x);
+        einsum(c, ea ? "klbc,lc->kb" : "jlcd,ld->jc", 0.5, T4, tn(h->t1_2, {o, v}), 1.0, t1x, {o, v});
+    }
+    double* Xp = c.arena.dalloc(n * nso);
+    double* xo = c.arena.dalloc(n * o);
+    double* xv = c.arena.dalloc(n * v);
+    if (ea) {
+        // virtual rows: T_cb = d_cb - 1/4 sum t_kl^cd t_kl^bd [- 1/4 (t t2 + t2 t)]
+        double* Tvv = c.arena.dalloc(v * v);
+        einsum(c, "klcd,klbd->cb", -0.25, T4, T4, 0.0, Tvv, {v, v});
+        if (third) {
+            einsum(c, "klcd,klbd->cb", -0.25, T4, tn(h->t_2, {o, o, v, v}), 1.0, Tvv, {v, v});
+            einsum(c, "klcd,klbd->cb", -0.25, tn(h->t_2, {o, o, v, v}), T4, 1.0, Tvv, {v, v});
+        }
+        ADC_CUDA(cudaMemcpyAsync(xv, y1, n * v * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+        einsum(c, "rb,cb->rc", 1.0, Y1, tn(Tvv, {v, v}), 1.0, xv, {n, v});
+        // occupied rows: T_kb = -t1x_kb; T_k,iab = t_ki^ab [+ t2_ki^ab]
+        einsum(c, "rb,kb->rk", -1.0, Y1, tn(t1x, {o, v}), 0.0, xo, {n, o});
+        einsum(c, "riab,kiab->rk", 0.5, tn(F, {n, o, v, v}), tn(tt, {o, o, v, v}), 1.0, xo, {n, o});
+    } else {
+        // occupied rows: T_kj = d_kj - 1/4 sum t_kl^cd t_jl^cd [- 1/4 (t t2 + t2 t)]
+        double* Too = c.arena.dalloc(o * o);
+        einsum(c, "klcd,jlcd->kj", -0.25, T4, T4, 0.0, Too, {o, o});
+        if (third) {
+            einsum(c, "klcd,jlcd->kj", -0.25, T4, tn(h->t_2, {o, o, v, v}), 1.0, Too, {o, o});
+            einsum(c, "klcd,jlcd->kj", -0.25, tn(h->t_2, {o, o, v, v}), T4, 1.0, Too, {o, o});
+        }
+        ADC_CUDA(cudaMemcpyAsync(xo, y1, n * o * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+        einsum(c, "rj,kj->rk", 1.0, Y1, tn(Too, {o, o}), 1.0, xo, {n, o});
+        // virtual rows: T_cj = t1x_jc; T_c,ija = t_ij^ca [+ t2_ij^ca]
+        einsum(c, "rj,jc->rc", 1.0, Y1, tn(t1x, {o, v}), 0.0, xv, {n, v});
+        einsum(c, "rija,ijca->rc", 0.5, tn(F, {n, o, o, v}), tn(tt, {o, o, v, v}), 1.0, xv, {n, v});
+    }
+    k_gather<<<grid_for(n * o), 256, 0, c.stream>>>(n, o, xo, o, 0, Xp, nso, 0, 0.0);
+    launch_check(c);
+    k_gather<<<grid_for(n * v), 256, 0, c.stream>>>(n, v, xv, v, 0, Xp, nso, o, 0.0);
+    launch_check(c);
+    std::vector<double> xh((size_t)n * nso);
+    ADC_CUDA(cudaMemcpyAsync(xh.data(), Xp, xh.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    ADC_CUDA(cudaStreamSynchronize(c.stream));
+    h->X_last = xh;
+    for (int r = 0; r < nroots; ++r) {
+        double s2 = 0.0;
+        for (long long p = 0; p < nso; ++p) s2 += xh[(size_t)r * nso + p] * xh[(size_t)r * nso + p];
+        specfac[r] = s2;
+    }
 }
 
 static void sigma_unrestricted(adc_handle* h, const double* Xin, double* Sout, long long n) {
@@ -2566,10 +2766,6 @@ int adc_sigma(adc_handle* h, const double* X, double* S, int nvec, int on_device
 int adc_davidson(adc_handle* h, int nroots, double tol, const double* guess, double* energies, double* specfac,
                  double* vectors, double* stats) {
     if (!h) return ADC_ERR_ARG;
-    if (h->unrestricted) {
-        h->err = "adc_davidson: handles of unrestricted references support adc_sigma only";
-        return ADC_ERR_ARG;
-    }
     if (nroots < 1 || !energies || !(tol > 0) || nroots > h->dim()) {
         h->err = "adc_davidson: invalid argument";
         return ADC_ERR_ARG;
@@ -2616,8 +2812,11 @@ int adc_get_tensor(adc_handle* h, const char* name, double* out, long long n) {
         } else if (s == "t1_2") {
             src = h->t1_2;
             cnt = o * v;
-        } else if (s == "t1_3" && !h->unrestricted) {
-            make_t1_third_order(h);
+        } else if (s == "t1_3") {
+            if (h->unrestricted)
+                make_t1_third_order_u(h);
+            else
+                make_t1_third_order(h);
             src = h->t1_3;
             cnt = o * v;
         } else if (s == "diag") {

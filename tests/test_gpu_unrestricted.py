@@ -59,6 +59,50 @@ def test_unrestricted_ip3_coupling_in_auxiliary_chunks():
     assert np.abs(Sg - Sr).max() <= 1e-11 * np.abs(Sr).max()
 
 
+def _group_sums(w, p, tol=1e-6):
+    """spectroscopic factors summed over groups of degenerate roots (the vectors of a
+    degenerate group are fixed only up to a rotation within it)"""
+    out, k = [], 0
+    while k < len(w):
+        j = k + 1
+        while j < len(w) and w[j] - w[j - 1] < tol:
+            j += 1
+        out.append(p[k:j].sum())
+        k = j
+    return np.array(out)
+
+
+@pytest.mark.parametrize("case", [CASES[0], (4, 3, 11, 30, 2, 1.0)], ids=lambda c: f"a{c[0]}b{c[1]}n{c[2]}")
+@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("kind", ["ea", "ip"])
+def test_unrestricted_roots_and_factors(kind, order, case):
+    """UADC Davidson (S = 1) against dense diagonalisation of the oracle's matrix: the
+    lowest roots to 1e-8 Eh and their spectroscopic factors (T through order n,
+    third-order singles included for ADC(3)) to 1e-6."""
+    from oracle.unrestricted import UnrestrictedDFADC
+    from paper_2012_06714_gb300 import ADCUnrestricted
+
+    na, nb, nmo, naux, seed, scale = case
+    s = make_open_shell_system(na, nb, nmo, naux, seed=seed)
+    s.B_a *= scale
+    s.B_b *= scale
+    ref = UnrestrictedDFADC(s, order, kind)
+    w, V = np.linalg.eigh(ref.dense())
+    nroots = 3
+    if w[nroots] - w[nroots - 1] < 1e-6:  # keep a degenerate group whole
+        nroots += 1
+    pref = ref.spectroscopic_factors(V[:, :nroots].T)
+    gpu = ADCUnrestricted(s.eps_a, s.eps_b, s.B_a, s.B_b, na, nb, order=order, kind=kind)
+    if order == 3:
+        o, v = ref.no, ref.nv
+        assert np.abs(gpu.get("t1_3", (o, v)) - ref.t1_3).max() < 1e-12
+    e, p, _, st = gpu.davidson(nroots, tol=1e-10, res_tol=1e-7)
+    gpu.close()
+    assert st["status"] == 0
+    assert np.abs(e - w[:nroots]).max() < 1e-8, (e, w[:nroots])
+    assert np.abs(_group_sums(w[:nroots], p) - _group_sums(w[:nroots], pref)).max() < 1e-6, (p, pref)
+
+
 def test_unrestricted_argument_errors():
     import ctypes
 
@@ -71,6 +115,6 @@ def test_unrestricted_argument_errors():
     g = ADCUnrestricted(s.eps_a, s.eps_b, s.B_a, s.B_b, 1, 0, order=2, kind="ea")
     L = load_library()
     e = np.zeros(2)
-    assert L.adc_davidson(g._h, 1, 1e-6, None, e.ctypes.data, None, None, None) != 0
+    assert L.adc_davidson(g._h, 0, 1e-6, None, e.ctypes.data, None, None, None) != 0  # nroots < 1
     assert L.adc_mp_energy(g._h, e.ctypes.data, 2) != 0
     g.close()
