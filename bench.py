@@ -377,7 +377,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     cold_start_s = time.perf_counter() - t0
     t0 = time.perf_counter()
-    gpu = ADC(eps_d, B_d, o, order=3, kind="ea", precision="bf16x3", res_tol=1e-4)
+    gpu = ADC(eps_d, B_d, o, order=3, kind="ea", precision="bf16x3", res_tol=1e-4, tune_cache=args.tune_cache)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     del B_d
@@ -499,6 +499,8 @@ def main():
     ap.add_argument("--no-roots", action="store_true")
     ap.add_argument("--ladder-case", action="store_true", help="small ladder profiling case (for ncu)")
     ap.add_argument("--davidson-case", action="store_true", help="small Davidson profiling case (for ncu)")
+    ap.add_argument("--tune-cache", default=None,
+                    help="tile autotuner cache file (tiles measured in the first warm-up step)")
     ap.add_argument("--fp64-plain", action="store_true",
                     help="FP64 comparator at the bench workload (setup timed, time to roots extrapolated)")
     args = ap.parse_args()

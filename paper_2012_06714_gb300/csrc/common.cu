@@ -128,25 +128,37 @@ __global__ void __launch_bounds__(SK_THREADS) k_skinny_m(int M, long long N, lon
         __syncthreads();
         if (n >= N) continue;
         const double* b = B + kc * ldb + n;
+        // U independent loads in flight per thread before their FMAs (the loop is bound by
+        // memory latency otherwise)
+        constexpr int U = 8;
         if (F32) {
             for (int k2 = 0; k2 < kn; k2 += SK_CHUNK) {
                 float part[MM];
 #pragma unroll
                 for (int m = 0; m < MM; ++m) part[m] = 0.f;
                 const int ke = min(kn, k2 + SK_CHUNK);
-                for (int kk = k2; kk < ke; ++kk) {
-                    const float bv = (float)b[kk * ldb];
+                for (int kk = k2; kk < ke; kk += U) {
+                    double bv[U];
 #pragma unroll
-                    for (int m = 0; m < MM; ++m) part[m] = fmaf((float)As[m][kk], bv, part[m]);
+                    for (int u = 0; u < U; ++u) bv[u] = kk + u < ke ? b[(long long)(kk + u) * ldb] : 0.0;
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+#pragma unroll
+                        for (int m = 0; m < MM; ++m)
+                            part[m] = fmaf(kk + u < ke ? (float)As[m][kk + u] : 0.f, (float)bv[u], part[m]);
                 }
 #pragma unroll
                 for (int m = 0; m < MM; ++m) acc[m] += (double)part[m];
             }
         } else {
-            for (int kk = 0; kk < kn; ++kk) {
-                const double bv = b[kk * ldb];
+            for (int kk = 0; kk < kn; kk += U) {
+                double bv[U];
 #pragma unroll
-                for (int m = 0; m < MM; ++m) acc[m] = fma(As[m][kk], bv, acc[m]);
+                for (int u = 0; u < U; ++u) bv[u] = kk + u < kn ? b[(long long)(kk + u) * ldb] : 0.0;
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int m = 0; m < MM; ++m) acc[m] = fma(kk + u < kn ? As[m][kk + u] : 0.0, bv[u], acc[m]);
             }
         }
     }
@@ -177,21 +189,37 @@ __global__ void __launch_bounds__(SK_THREADS) k_skinny_n(long long M, int N, lon
 #pragma unroll
             for (int j = 0; j < NN; ++j) part[j] = 0.f;
             const long long ke = min(k1, kb + (long long)SK_THREADS * SK_CHUNK);
-            for (long long k = kb + threadIdx.x; k < ke; k += SK_THREADS) {
-                const float av = (float)a[k];
+            constexpr int U = 4;
+            for (long long k = kb + threadIdx.x; k < ke; k += (long long)U * SK_THREADS) {
+                double av[U];
 #pragma unroll
-                for (int j = 0; j < NN; ++j)
-                    if (j < N) part[j] = fmaf(av, (float)B[k * ldb + j], part[j]);
+                for (int u = 0; u < U; ++u) av[u] = k + u * SK_THREADS < ke ? a[k + u * SK_THREADS] : 0.0;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const long long ku = k + u * SK_THREADS;
+                    if (ku < ke)
+#pragma unroll
+                        for (int j = 0; j < NN; ++j)
+                            if (j < N) part[j] = fmaf((float)av[u], (float)B[ku * ldb + j], part[j]);
+                }
             }
 #pragma unroll
             for (int j = 0; j < NN; ++j) acc[j] += (double)part[j];
         }
     } else {
-        for (long long k = k0 + threadIdx.x; k < k1; k += SK_THREADS) {
-            const double av = a[k];
+        constexpr int U = 4;
+        for (long long k = k0 + threadIdx.x; k < k1; k += (long long)U * SK_THREADS) {
+            double av[U];
 #pragma unroll
-            for (int j = 0; j < NN; ++j)
-                if (j < N) acc[j] = fma(av, B[k * ldb + j], acc[j]);
+            for (int u = 0; u < U; ++u) av[u] = k + u * SK_THREADS < k1 ? a[k + u * SK_THREADS] : 0.0;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const long long ku = k + u * SK_THREADS;
+                if (ku < k1)
+#pragma unroll
+                    for (int j = 0; j < NN; ++j)
+                        if (j < N) acc[j] = fma(av[u], B[ku * ldb + j], acc[j]);
+            }
         }
     }
 #pragma unroll
