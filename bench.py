@@ -160,7 +160,8 @@ def time_to_roots_medium(dev):
     from paper_2012_06714_gb300 import ADC
 
     s = make_system(20, 180, 600, seed=0)
-    out = {"workload": "EA-ADC(3) nocc=20 nvir=180 naux=600, 4 roots, tol 1e-6 Eh, residual 1e-4"}
+    out = {"workload": "EA- and IP-ADC(3) nocc=20 nvir=180 naux=600, 4 roots, tol 1e-6 Eh, residual 1e-4"}
+    out["ip"] = time_to_roots_ip(dev, s)
     res = {}
     for name, prec, refine in (("fp64", "fp64", 0), ("mixed", "bf16x3", 1), ("mixed_refine_fp64", "bf16x3", 2),
                                ("mixed_unrefined", "bf16x3", 0)):
@@ -183,6 +184,46 @@ def time_to_roots_medium(dev):
         out[name]["abs_dE_eh_vs_fp64"] = [float(x) for x in np.abs(res["fp64"][0] - res[name][0])]
         out[name]["max_abs_dP_vs_fp64"] = float(np.abs(res["fp64"][1] - res[name][1]).max())
         out[name]["speedup_vs_fp64"] = out["fp64"]["total_seconds"] / out[name]["total_seconds"]
+    return out
+
+
+def time_to_roots_ip(dev, s):
+    """IP-ADC(3) at nocc=20 nvir=180 naux=600, 4 roots: FP64 plain vs mixed precision (setup +
+    Davidson; the mixed run continues with the accurate operator to residual 1e-6), each root's
+    |dE| and |dP| against the FP64 run, and the IP sigma throughput of both (4 vectors)."""
+    import torch
+
+    from paper_2012_06714_gb300 import ADC
+
+    o, v, naux = 20, 180, 600
+    res, out = {}, {}
+    for name, prec, kw in (("fp64", "fp64", dict(res_tol=1e-6)),
+                           ("mixed", "bf16x3", dict(res_tol=1e-4, refine_res_tol=1e-6))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = ADC(torch.from_numpy(s.eps).to(dev), torch.from_numpy(s.B).to(dev), o, order=3, kind="ip", precision=prec,
+                **kw)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        e, p, _, st = g.davidson(4, tol=1e-8)
+        t2 = time.perf_counter()
+        X = torch.randn((4, g.dim), device=dev, dtype=torch.float64)
+        S = torch.empty_like(X)
+        g.sigma(X, out=S)
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        for _ in range(5):
+            g.sigma(X, out=S)
+        torch.cuda.synchronize()
+        sig_ms = (time.perf_counter() - t3) / 5 * 1e3
+        g.close()
+        res[name] = (e, p)
+        out[name] = {"setup_s": t1 - t0, "davidson_s": t2 - t1, "total_s": t2 - t0, "iterations": st["iterations"],
+                     "sigma_vectors": st["sigma_vectors"], "status": st["status"], "max_residual": st["max_residual"],
+                     "sigma_ms_4_vectors": sig_ms, "energies_eh": [float(x) for x in e]}
+    out["mixed"]["abs_dE_eh_vs_fp64"] = [float(x) for x in np.abs(res["fp64"][0] - res["mixed"][0])]
+    out["mixed"]["max_abs_dP_vs_fp64"] = float(np.abs(res["fp64"][1] - res["mixed"][1]).max())
+    out["mixed"]["speedup_vs_fp64"] = out["fp64"]["total_s"] / out["mixed"]["total_s"]
     return out
 
 
@@ -318,6 +359,55 @@ def run_fp64_plain(args):
     return 0
 
 
+def run_batched(args):
+    """The batched IP-ADC(3) workload: 64 synthetic molecules (nocc ~ U{8..30}, nvir ~ U{60..250},
+    naux = 3.5 nmo, seeds 0..63), mixed precision, 6 roots each, set up and solved as one batch
+    (adc_setup_batch / adc_davidson_batch: each system on its own stream and host thread) and one
+    at a time on the same GPU; wall times of both, and the largest root difference between them."""
+    import torch
+
+    from adc_inputs import batched_ip_molecules, make_system
+    from paper_2012_06714_gb300 import ADC, ADCBatch
+
+    torch.cuda.set_device(0)
+    mols = batched_ip_molecules(args.nmol)
+    systems = []
+    for m in mols:
+        s = make_system(m["nocc"], m["nvir"], m["naux"], seed=m["seed"])
+        systems.append((s.eps, s.B, m["nocc"]))
+    opts = dict(res_tol=1e-4, max_iter=300, max_space_per_root=24, keep_per_root=4)
+    # library first use (handles, module loading) outside the timed regions
+    ADC(systems[0][0], systems[0][1], systems[0][2], order=3, kind="ip", precision="bf16x3").close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b = ADCBatch(systems, order=3, kind="ip", precision="bf16x3", **opts)
+    t1 = time.perf_counter()
+    e, p, st, status = b.davidson(6, tol=1e-6)
+    t2 = time.perf_counter()
+    b.close()
+    seq_setup = seq_solve = 0.0
+    dmax = 0.0
+    for k, (eps, B, o) in enumerate(systems):
+        t3 = time.perf_counter()
+        g = ADC(eps, B, o, order=3, kind="ip", precision="bf16x3", **opts)
+        t4 = time.perf_counter()
+        e1, _, _, _ = g.davidson(6, tol=1e-6)
+        t5 = time.perf_counter()
+        g.close()
+        seq_setup += t4 - t3
+        seq_solve += t5 - t4
+        dmax = max(dmax, float(np.abs(e[k] - e1).max()))
+    out = {"workload": f"batched IP-ADC(3), {len(systems)} molecules, nocc 8..30, nvir 60..250, naux 3.5 nmo, "
+                       "6 roots, bf16x3, |dE| <= 1e-6 Eh, residual 1e-4",
+           "batched": {"setup_s": t1 - t0, "solve_s": t2 - t1, "total_s": t2 - t0,
+                       "converged": int((status == 0).sum()), "sigma_vectors": int(st[:, 1].sum())},
+           "one_at_a_time": {"setup_s": seq_setup, "solve_s": seq_solve, "total_s": seq_setup + seq_solve},
+           "max_abs_dE_batched_vs_one_at_a_time_eh": dmax}
+    out["speedup"] = out["one_at_a_time"]["total_s"] / out["batched"]["total_s"]
+    print(json.dumps(out))
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -377,7 +467,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     cold_start_s = time.perf_counter() - t0
     t0 = time.perf_counter()
-    gpu = ADC(eps_d, B_d, o, order=3, kind="ea", precision="bf16x3", res_tol=1e-4, tune_cache=args.tune_cache)
+    # tile autotuner: a fresh cache unless one is given, so the tiles are measured in the first warm-up step
+    tune_cache = args.tune_cache or os.path.join(tempfile.mkdtemp(prefix="adc_tiles_"), "tiles.txt")
+    gpu = ADC(eps_d, B_d, o, order=3, kind="ea", precision="bf16x3", res_tol=1e-4, tune_cache=tune_cache)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     del B_d
@@ -476,7 +568,8 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
             "config": {"workload": "EA-ADC(3) sigma build, nocc=40 nvir=400 naux=1400, 4 trial vectors",
                        "nocc": o, "nvir": v, "naux": naux, "order": 3, "kind": "ea", "nvec": nvec, "dim": gpu.dim,
-                       "l2": "inputs larger than L2 (B^Q > 2 GB)", "parallelism": "replicas" if world > 1 else "1 GPU"},
+                       "l2": "inputs larger than L2 (B^Q > 2 GB)", "parallelism": "replicas" if world > 1 else "1 GPU",
+                       "tiles": "autotuned in the first warm-up step (adc_options.tune_cache)"},
             "e2e": e2e, "roofline": roof, "gpu_launches": int(round(launches_per_step)), "clocks": clk,
             "time_to_roots": roots}
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -499,6 +592,8 @@ def main():
     ap.add_argument("--no-roots", action="store_true")
     ap.add_argument("--ladder-case", action="store_true", help="small ladder profiling case (for ncu)")
     ap.add_argument("--davidson-case", action="store_true", help="small Davidson profiling case (for ncu)")
+    ap.add_argument("--batched", action="store_true", help="batched IP-ADC(3) workload (64 molecules)")
+    ap.add_argument("--nmol", type=int, default=64)
     ap.add_argument("--tune-cache", default=None,
                     help="tile autotuner cache file (tiles measured in the first warm-up step)")
     ap.add_argument("--fp64-plain", action="store_true",
@@ -508,6 +603,8 @@ def main():
         return run_davidson_case(args)
     if args.fp64_plain:
         return run_fp64_plain(args)
+    if args.batched:
+        return run_batched(args)
     if args.ladder_case:
         return run_ladder_case(args)
     if args.impl == "reference":

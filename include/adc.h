@@ -171,9 +171,13 @@ int adc_set_options(adc_handle* h, const adc_options* opt);
  * (p_s q_s | r_t s_t) = sum_Q B^Q_{s,pq} B^Q_{t,rs} (Eq. 19 per spin pair).
  *   eps_a, eps_b  host [nmo] alpha / beta orbital energies, occupied first
  *   Ba, Bb        host [naux][nmo][nmo] alpha / beta DF factors, symmetric in pq
- * aux_chunk: auxiliary functions per chunk of the IP third-order coupling
- * intermediate sum_e B^Q_ie t_jk^de (naux x o^3 x v); 0 = automatic (chunks of
- * at most 2^27 elements).
+ * opt: NULL for defaults.  precision ADC_PREC_FP64 or ADC_PREC_BF16X3 (setup and
+ * the refinement of converged roots in FP64; the sigma's ladder on the tensor
+ * cores per spin block -- alpha-alpha, beta-beta and alpha-beta, the beta-alpha
+ * block by antisymmetry -- and its other contractions as in the closed-shell
+ * mixed sigma); aux_chunk also sets the chunks of the IP third-order coupling
+ * intermediate sum_e B^Q_ie t_jk^de (naux x o^3 x v; 0 = at most 2^27 elements);
+ * the solver options as for adc_setup; m11_on_the_fly is not available here.
  * adc_get_tensor returns "t2", "t2_2", "t1_2", "t1_3" (third-order singles, made
  * on first use) and "M11" in these spin-orbital dimensions (M11: the paper's
  * M_+ / M_- one-particle block).  adc_davidson runs with metric S = 1 (the
@@ -184,7 +188,7 @@ int adc_set_options(adc_handle* h, const adc_options* opt);
  * Errors: ADC_ERR_ARG, ADC_ERR_OOM, ADC_ERR_CUDA (message: adc_last_error(NULL)).
  */
 int adc_setup_unrestricted(const double* eps_a, const double* eps_b, const double* Ba, const double* Bb, int nocc_a,
-                           int nocc_b, int nmo, int naux, int order, int kind, int aux_chunk, adc_handle** out);
+                           int nocc_b, int nmo, int naux, int order, int kind, const adc_options* opt, adc_handle** out);
 
 /* Length of the spin-adapted vector (see layout above). */
 int adc_dim(const adc_handle* h, long long* dim);

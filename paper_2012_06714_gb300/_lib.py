@@ -92,7 +92,7 @@ def load_library():
     lib.adc_davidson.argtypes = [P, I, D, P, P, P, P, P]
     lib.adc_get_tensor.argtypes = [P, ctypes.c_char_p, P, LL]
     lib.adc_mp_energy.argtypes = [P, P, ctypes.c_int]
-    lib.adc_setup_unrestricted.argtypes = [P, P, P, P, I, I, I, I, I, I, I, ctypes.POINTER(P)]
+    lib.adc_setup_unrestricted.argtypes = [P, P, P, P, I, I, I, I, I, I, ctypes.POINTER(Options), ctypes.POINTER(P)]
     lib.adc_kernel_timing.argtypes = [P, I, P]
     lib.adc_ladder_noalloc.argtypes = [P, P, P, LL]
     lib.adc_spectrum.argtypes = [P, P, I, D, P, I, P]
@@ -409,15 +409,20 @@ class ADCUnrestricted:
     beta, virtual alpha, virtual beta; EA [1p | (i, a<b)], IP [1h | (i<j, a)].
     """
 
-    def __init__(self, eps_a, eps_b, B_a, B_b, nocc_a, nocc_b, order=3, kind="ea", aux_chunk=0):
+    def __init__(self, eps_a, eps_b, B_a, B_b, nocc_a, nocc_b, order=3, kind="ea", aux_chunk=0, precision="fp64",
+                 refine=1, refine_res_tol=0.0):
         lib = load_library()
         self._lib = lib
         arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (eps_a, eps_b, B_a, B_b)]
         naux, nmo = arrs[2].shape[0], arrs[2].shape[1]
         self.order, self.kind = order, kind
+        opt = Options()
+        lib.adc_default_options(ctypes.byref(opt))
+        opt.precision, opt.aux_chunk, opt.refine, opt.refine_res_tol = PRECISIONS[precision], aux_chunk, refine, refine_res_tol
+        self._solver = dict(refine=refine, refine_res_tol=refine_res_tol)
         h = ctypes.c_void_p()
         rc = lib.adc_setup_unrestricted(*[a.ctypes.data for a in arrs], nocc_a, nocc_b, nmo, naux, order,
-                                        ADC_EA if kind == "ea" else ADC_IP, aux_chunk, ctypes.byref(h))
+                                        ADC_EA if kind == "ea" else ADC_IP, ctypes.byref(opt), ctypes.byref(h))
         if rc != ADC_OK:
             raise ADCError(rc, lib.adc_last_error(None).decode())
         self._h = h
@@ -434,6 +439,7 @@ class ADCUnrestricted:
         opt = Options()
         self._lib.adc_default_options(ctypes.byref(opt))
         opt.res_tol, opt.max_iter, opt.max_space_per_root = res_tol, max_iter, max_space_per_root
+        opt.refine, opt.refine_res_tol = self._solver["refine"], self._solver["refine_res_tol"]
         self._check(self._lib.adc_set_options(self._h, ctypes.byref(opt)))
         e = np.zeros(nroots)
         p = np.zeros(nroots)

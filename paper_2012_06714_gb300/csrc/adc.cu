@@ -51,7 +51,9 @@ struct adc_handle {
     double *g_oovv = nullptr, *g_oooo = nullptr, *g_ooov = nullptr, *g_ovov = nullptr, *g_vovo = nullptr,
            *g_vooo = nullptr, *m12 = nullptr;
     int* pair_idx = nullptr;  // [3][npairs] (i, a, b) for EA, (i, j, a) for IP
-    LadderTC* tc = nullptr;  // tensor-core ladder state (BF16x3 operands of B^Q_vv)
+    LadderTC* tc = nullptr;  // tensor-core ladder state (BF16x3 operands of B^Q_vv; open shells: the alpha block)
+    LadderTC* tc_b = nullptr;  // open shells: the beta virtual block's ladder state
+    int nva = 0;               // open shells: alpha virtual spin orbitals (the first nva of the v)
     // tensor-core ladder arithmetic: Davidson sigma, the setup ladder of t, and
     // the final refinement of converged roots
     // (sigma: partial sums promoted every 16 K blocks, drift <= ~3e-6 relative;
@@ -84,6 +86,7 @@ struct adc_handle {
     ~adc_handle() {
         if (ctx.stream) cudaStreamSynchronize(ctx.stream);
         ladder_tc_destroy(tc);
+        ladder_tc_destroy(tc_b);
         for (void* p : owned) cudaFree(p);
         if (ctx.blas) cublasDestroy(ctx.blas);
         if (own_stream) cudaStreamDestroy(own_stream);
@@ -275,9 +278,15 @@ T tc(const double* p, std::initializer_list<long long> d) { return T{p, std::vec
 // DF ladder: out[n] += sum_Q B^Q_vv X_n B^Q_vv for nmat v x v matrices
 //   (sum_cd (ac|bd) X_n[c,d]; the vvvv integral is never formed)
 // --------------------------------------------------------------------------
+static void ladder_open_shell(adc_handle* h, const double* F, long long nmat, double* out, const LadderMode& md);
+
 static void ladder(adc_handle* h, const double* X, long long nmat, double* out, const LadderMode& md) {
     Ctx& c = h->ctx;
     const long long v = h->v;
+    if (h->unrestricted && h->tc) {
+        ladder_open_shell(h, X, nmat, out, md);
+        return;
+    }
     if (h->opt.precision != ADC_PREC_FP64 && h->tc) {
         ladder_tc_apply(*h->tc, c, X, nmat, out, md);
         return;
@@ -1130,14 +1139,12 @@ static void sigma_unrestricted(adc_handle* h, const double* Xin, double* Sout, l
 
 static void sigma_device(adc_handle* h, const double* X, double* S, long long nvec) {
     Ctx& c = h->ctx;
-    if (h->unrestricted) {
-        sigma_unrestricted(h, X, S, nvec);
-        return;
-    }
     if (!h->refining) c.gemm_mode = h->cmode_sigma;
     // a timeout of an earlier call left the flag raised; every call starts clean
     if (c.d_err) ADC_CUDA(cudaMemsetAsync(c.d_err, 0, sizeof(int), c.stream));
-    if (h->kind == ADC_EA)
+    if (h->unrestricted)
+        sigma_unrestricted(h, X, S, nvec);
+    else if (h->kind == ADC_EA)
         sigma_ea(h, X, S, nvec);
     else
         sigma_ip(h, X, S, nvec);
@@ -1883,6 +1890,31 @@ __global__ void k_pairs_to_full(int ea, long long n, long long np, int o, int v,
     }
 }
 
+// out[m][r][c] = F[m][r0 + r][c0 + c] for the nr x nc block of nmat v x v matrices
+__global__ void k_block_get(long long nmat, int v, int r0, int nr, int c0, int nc, const double* __restrict__ F,
+                            double* __restrict__ out) {
+    GRID_STRIDE(x, nmat * nr * nc) {
+        const int cc = x % nc;
+        const long long t = x / nc;
+        const int r = t % nr;
+        const long long m = t / nr;
+        out[x] = F[(m * v + r0 + r) * v + c0 + cc];
+    }
+}
+// S[m][r0 + r][c0 + c] += sgn * (trans ? O[m][c][r] : O[m][r][c]), O of nmat matrices of nr x nc
+// (trans: of nc x nr)
+__global__ void k_block_add(long long nmat, int v, int r0, int nr, int c0, int nc, int trans, double sgn,
+                            const double* __restrict__ O, double* __restrict__ S) {
+    GRID_STRIDE(x, nmat * nr * nc) {
+        const int cc = x % nc;
+        const long long t = x / nc;
+        const int r = t % nr;
+        const long long m = t / nr;
+        const double val = trans ? O[(m * nc + cc) * nr + r] : O[x];
+        S[(m * v + r0 + r) * v + c0 + cc] += sgn * val;
+    }
+}
+
 // preconditioner diagonal of an unrestricted handle: [diag of the applied 1p/1h block,
 // zeroth-order pair energies] (EA: e_a + e_b - e_i; IP: -(e_i + e_j - e_a))
 __global__ void k_diag_pairs(int ea, long long n1, long long np, int o, const int* __restrict__ idx,
@@ -1927,13 +1959,49 @@ void perm4(Ctx& c, const double* in, std::initializer_list<long long> d, std::in
 // M += alpha (X + X^T) for an n x n X
 static void sym_add_n(adc_handle* h, const double* X, double* M, long long n, double alpha) { sym_add(h, X, M, (int)n, alpha); }
 
+// The ladder of an open-shell reference on the tensor cores, per spin block (Eq. 19 per
+// spin pair): B^Q of the virtual spin orbitals is block diagonal (alpha, beta), so for the
+// antisymmetric F_n (v x v, alpha virtuals first)
+//   out_aa += sum_Q Ba F_aa Ba,  out_bb += sum_Q Bb F_bb Bb,  out_ab += sum_Q Ba F_ab Bb,
+// and out_ba = -out_ab^T (the ladder keeps the antisymmetry).  Three tensor-core ladders
+// instead of one over the spin-orbital factor, half of which is zeros.
+static void ladder_open_shell(adc_handle* h, const double* F, long long nmat, double* out, const LadderMode& md) {
+    Ctx& c = h->ctx;
+    const int v = h->v, va = h->nva, vb = h->v - h->nva;
+    Scope sc(c.arena);
+    double* X = c.arena.dalloc((size_t)nmat * std::max(va, vb) * std::max(va, vb));
+    double* O = c.arena.dalloc((size_t)nmat * std::max(va, vb) * std::max(va, vb));
+    auto block = [&](LadderTC* l, LadderTC* r, int r0, int nr, int c0, int nc, bool both) {
+        if (nr <= 0 || nc <= 0) return;
+        k_block_get<<<grid_for(nmat * nr * nc), 256, 0, c.stream>>>(nmat, v, r0, nr, c0, nc, F, X);
+        launch_check(c);
+        fill(c, nmat * nr * nc, 0.0, O);
+        ladder_tc_apply_pair(*l, *r, c, X, nmat, O, md);
+        k_block_add<<<grid_for(nmat * nr * nc), 256, 0, c.stream>>>(nmat, v, r0, nr, c0, nc, 0, 1.0, O, out);
+        launch_check(c);
+        if (both) {  // the transposed block by antisymmetry
+            k_block_add<<<grid_for(nmat * nr * nc), 256, 0, c.stream>>>(nmat, v, c0, nc, r0, nr, 1, -1.0, O, out);
+            launch_check(c);
+        }
+    };
+    block(h->tc, h->tc, 0, va, 0, va, false);
+    block(h->tc_b, h->tc_b, va, vb, va, vb, false);
+    block(h->tc, h->tc_b, 0, va, va, vb, true);
+}
+
 static void setup_unrestricted(adc_handle* h, const double* eps_so, const double* Bso) {
     Ctx& c = h->ctx;
     ADC_BLAS(cublasCreate(&c.blas));
     ADC_BLAS(cublasSetStream(c.blas, c.stream));
     ADC_BLAS(cublasSetMathMode(c.blas, CUBLAS_DEFAULT_MATH));
+    // setup (and the refinement of converged roots) in FP64; mixed precision: the sigma's
+    // contractions on the tensor cores / own kernels and its ladder per spin block on the
+    // tensor cores (the split B^Q are made at the end of setup, so the setup ladders are FP64)
     c.gemm_mode = 0;
-    h->cmode_setup = h->cmode_sigma = 0;
+    h->cmode_setup = h->cmode_refine = 0;
+    h->cmode_sigma = h->opt.precision != ADC_PREC_FP64 ? (h->opt.contractions >= 0 ? h->opt.contractions : 2) : 0;
+    if (h->opt.tune_cache && h->opt.tune_cache[0]) c.tuner = tune_cache_open(h->opt.tune_cache);
+    h->opt.tune_cache = nullptr;
     const long long o = h->o, v = h->v, Q = h->naux, nso = o + v;
     const long long o2v2 = o * o * v * v;
     h->eps = h->dmalloc(nso);
@@ -2133,6 +2201,18 @@ static void setup_unrestricted(adc_handle* h, const double* eps_so, const double
             perm4(c, Xc, {o, o, o, v}, {0, 2, 1, 3}, h->m12, 1.0, 1.0);
         }
     }
+    if (h->opt.precision != ADC_PREC_FP64) {
+        // per-spin virtual blocks of B^Q for the tensor-core ladders of sigma
+        const int va = h->nva, vb = (int)v - h->nva;
+        double* Ba = h->dmalloc(Q * va * va);
+        double* Bb = h->dmalloc(Q * vb * vb);
+        k_block_get<<<grid_for(Q * va * va), 256, 0, c.stream>>>(Q, (int)v, 0, va, 0, va, h->Bvv, Ba);
+        launch_check(c);
+        k_block_get<<<grid_for(Q * vb * vb), 256, 0, c.stream>>>(Q, (int)v, va, vb, va, vb, h->Bvv, Bb);
+        launch_check(c);
+        h->tc = ladder_tc_create(c, Ba, (int)Q, va, h->opt.aux_chunk);
+        h->tc_b = ladder_tc_create(c, Bb, (int)Q, vb, h->opt.aux_chunk);
+    }
     // Davidson preconditioner diagonal (S = 1 in the antisymmetric pair basis)
     h->diag = h->dmalloc(h->dim());
     k_diag_pairs<<<grid_for(h->dim()), 256, 0, c.stream>>>(h->kind == ADC_EA, n1, h->npairs(), (int)o, h->pair_idx, h->eps,
@@ -2324,7 +2404,7 @@ static void specfac_unrestricted(adc_handle* h, const double* Y, int nroots, dou
 
 static void sigma_unrestricted(adc_handle* h, const double* Xin, double* Sout, long long n) {
     Ctx& c = h->ctx;
-    c.gemm_mode = 0;
+    if (!h->refining) c.gemm_mode = h->cmode_sigma;
     const long long o = h->o, v = h->v, Q = h->naux, dim = h->dim(), np = h->npairs(), n1 = h->n1();
     const int ea = h->kind == ADC_EA;
     const long long blk = ea ? o * v * v : o * o * v;
@@ -2380,7 +2460,7 @@ static void sigma_unrestricted(adc_handle* h, const double* Xin, double* Sout, l
         k_diag22<<<grid_for(n * blk), 256, 0, c.stream>>>(1, (int)o, (int)v, n, h->eps, F, S2);
         launch_check(c);
         if (third) {
-            ladder(h, F, n * o, S2, h->lm_setup);
+            ladder(h, F, n * o, S2, h->refining ? h->lm_refine : h->lm_sigma);
             double* R = c.arena.dalloc(n * blk);
             einsum(c, "ajci,njcb->niab", 1.0, tn(h->g_vovo, {v, o, v, o}), F4, 0.0, R, {n, o, v, v});
             axpby(c, n * blk, -1.0, R, 1.0, S2);
@@ -2664,15 +2744,20 @@ int adc_setup_batch(int nmol, const double* const* eps, const double* const* Bq,
 }
 
 int adc_setup_unrestricted(const double* eps_a, const double* eps_b, const double* Ba, const double* Bb, int nocc_a,
-                           int nocc_b, int nmo, int naux, int order, int kind, int aux_chunk, adc_handle** out) {
+                           int nocc_b, int nmo, int naux, int order, int kind, const adc_options* opt, adc_handle** out) {
     if (!out) return ADC_ERR_ARG;
     *out = nullptr;
     const int no = nocc_a + nocc_b, nso = 2 * nmo, nv = nso - no;
     const bool pairs_ok = kind == ADC_EA ? nv >= 2 : no >= 2;
     if (!eps_a || !eps_b || !Ba || !Bb || nmo < 1 || nocc_a < 0 || nocc_b < 0 || nocc_a > nmo || nocc_b > nmo || no < 1 ||
         nv < 1 || naux < 1 || (order != 2 && order != 3) || (kind != ADC_EA && kind != ADC_IP) || !pairs_ok ||
-        aux_chunk < 0) {
-        g_setup_error = "adc_setup_unrestricted: invalid argument";
+        (opt && (opt->aux_chunk < 0 || (opt->precision != ADC_PREC_FP64 && opt->precision != ADC_PREC_BF16X3) ||
+                 opt->m11_on_the_fly || opt->refine < 0 || opt->refine > 2 || !(opt->refine_res_tol >= 0.0)))) {
+        g_setup_error = "adc_setup_unrestricted: invalid argument (or an option these handles do not take)";
+        return ADC_ERR_ARG;
+    }
+    if (opt && opt->precision != ADC_PREC_FP64 && (nmo - nocc_a < 1 || nmo - nocc_b < 1)) {
+        g_setup_error = "adc_setup_unrestricted: the mixed-precision ladder needs virtual orbitals of both spins";
         return ADC_ERR_ARG;
     }
     // spin orbitals: occupied alpha, occupied beta, virtual alpha, virtual beta
@@ -2698,8 +2783,9 @@ int adc_setup_unrestricted(const double* eps_a, const double* eps_b, const doubl
     h->order = order;
     h->kind = kind;
     h->unrestricted = true;
+    h->nva = nmo - nocc_a;
     adc_default_options(&h->opt);
-    h->opt.aux_chunk = aux_chunk;
+    if (opt) h->opt = *opt;
     try {
         setup_unrestricted(h, eps_so.data(), Bso.data());
     } catch (const adc::Error& e) {

@@ -894,15 +894,17 @@ __global__ void k_split_Bp(const double* __restrict__ B, int naux, int v, int vp
         splitp(val, planes, o.p[0] + x, o.p[1] + x, o.p[2] + x);
     }
 }
-// XT[(m,d)][cp] = X_m[c][d] (c, d < v), zero pad; m < nmat
-__global__ void k_split_XT(const double* __restrict__ X, long long nmat, int v, int vp, int planes, Planes o) {
-    long long n = nmat * vp * vp;
+// XT[(m,d)][cp] = X_m[c][d] for X_m of va x vb (c < va, d < vb; rows d padded to vpb,
+// columns c to vpa), zero pad; m < nmat
+__global__ void k_split_XT(const double* __restrict__ X, long long nmat, int va, int vb, int vpa, int vpb, int planes,
+                           Planes o) {
+    long long n = nmat * vpb * vpa;
     GRID_STRIDE(x, n) {
-        int cp = x % vp;
-        long long r = x / vp;
-        int d = r % vp;
-        long long m = r / vp;
-        double val = (cp < v && d < v) ? X[(m * v + cp) * v + d] : 0.0;
+        int cp = x % vpa;
+        long long r = x / vpa;
+        int d = r % vpb;
+        long long m = r / vpb;
+        double val = (cp < va && d < vb) ? X[(m * va + cp) * vb + d] : 0.0;
         splitp(val, planes, o.p[0] + x, o.p[1] + x, o.p[2] + x);
     }
 }
@@ -1185,50 +1187,54 @@ namespace {
 
 // The chunk loop shared by both entry points: groups of mg matrices, chunks of
 // qc auxiliary functions; scratch xt (split X^T planes of one group) and zt (Z planes).
-void run_ladder(LadderTC& L, Ctx& c, const double* X, long long nmat, double* out, const LadderMode& md, Planes xt,
-                Planes zt, long long mg, int qc, int bn2) {
-    const int v = L.v, vp = L.vp, naux = L.naux, planes = md.planes;
+// out_n[a,b] += sum_Q (B_l^Q X_n B_r^Q)[a,b] for X_n of va x vb: B_l (va x va) from Ll
+// (GEMM1's A operand), B_r (vb x vb) from Lr (GEMM2's B operand); Ll == Lr for the
+// square ladder of one B^Q.
+void run_ladder(LadderTC& Ll, LadderTC& Lr, Ctx& c, const double* X, long long nmat, double* out, const LadderMode& md,
+                Planes xt, Planes zt, long long mg, int qc, int bn2) {
+    const int va = Ll.v, vpa = Ll.vp, vb = Lr.v, vpb = Lr.vp, naux = Ll.naux, planes = md.planes;
     const int bn1 = BN1[planes];
     CUtensorMap mBp[3];  // GEMM2-B maps: one CTA's half of the tile in pair mode
-    for (int p = 0; p < planes; ++p) mBp[p] = make_map(L.Bp[p], L.v, (long long)L.naux * L.vp, L.pair2 ? bn2 / 2 : bn2);
+    for (int p = 0; p < planes; ++p) mBp[p] = make_map(Lr.Bp[p], vb, (long long)naux * vpb, Lr.pair2 ? bn2 / 2 : bn2);
     for (long long m0 = 0; m0 < nmat; m0 += mg) {
         const long long nm = std::min(mg, nmat - m0);
-        k_split_XT<<<grid_for(nm * vp * vp), 256, 0, c.stream>>>(X + m0 * v * v, nm, v, vp, planes, xt);
+        k_split_XT<<<grid_for(nm * vpb * vpa), 256, 0, c.stream>>>(X + m0 * va * vb, nm, va, vb, vpa, vpb, planes, xt);
         ++c.kernels;
         ADC_CUDA(cudaGetLastError());
         Maps m1;
         for (int p = 0; p < planes; ++p) {
-            m1.a[p] = L.mBs[p];
-            m1.b[p] = make_map(xt.p[p], nm * vp, vp, L.pair1 ? bn1 / 2 : bn1);
+            m1.a[p] = Ll.mBs[p];
+            m1.b[p] = make_map(xt.p[p], nm * vpb, vpa, Ll.pair1 ? bn1 / 2 : bn1);
         }
         for (int q0 = 0; q0 < naux; q0 += qc) {
             const int qn = std::min(qc, naux - q0);
-            const double algo = 2.0 * (double)qn * v * (double)nm * v * v;  // unpadded B^q X_n products
-            // GEMM1: Z[(q,a),(n,d)] = sum_c B^q[a,c] X_n[c,d]  (rows q*vp + a, a padded to vp)
+            // GEMM1: Z[(q,a),(n,d)] = sum_c B_l^q[a,c] X_n[c,d]  (rows q*vpa + a, a padded to vpa; d to vpb)
             Epi e1{};
             e1.mode = 0;
-            e1.M = qn * vp;
-            e1.N = (int)(nm * vp);
-            e1.vpa = vp;
-            e1.vp = vp;
-            e1.err = L.d_err;
-            for (int p = 0; p < planes; ++p) m1.z[p] = make_map_z(zt.p[p], vp, qn, v, nm);
-            launch_gemm(c, m1, planes, q0 * vp, 0, e1.M, e1.N, vp, bn1, 1, md.epoch1, L.pair1, e1, algo);
-            // GEMM2: out[(n,a),b] += sum_(q,d) Z_n[a,(q,d)] B^q[d,b]
+            e1.M = qn * vpa;
+            e1.N = (int)(nm * vpb);
+            e1.vpa = vpa;
+            e1.vp = vpb;
+            e1.err = Ll.d_err;
+            for (int p = 0; p < planes; ++p) m1.z[p] = make_map_z(zt.p[p], vpb, qn, va, nm);
+            launch_gemm(c, m1, planes, q0 * vpa, 0, e1.M, e1.N, vpa, bn1, 1, md.epoch1, Ll.pair1, e1,
+                        2.0 * (double)qn * va * (double)nm * vb * va);  // unpadded products
+            // GEMM2: out[(n,a),b] += sum_(q,d) Z_n[a,(q,d)] B_r^q[d,b]
             Maps m2;
             for (int p = 0; p < planes; ++p) {
-                m2.a[p] = make_map(zt.p[p], nm * v, (long long)qn * vp, BM);
+                m2.a[p] = make_map(zt.p[p], nm * va, (long long)qn * vpb, BM);
                 m2.b[p] = mBp[p];
             }
             Epi e2{};
             e2.mode = 1;
-            e2.M = (int)(nm * v);
-            e2.N = v;
-            e2.out = out + m0 * v * v;
-            e2.ldc = v;
-            e2.vec = ((uintptr_t)e2.out % 16 == 0) && (v % 2 == 0);
-            e2.err = L.d_err;
-            launch_gemm(c, m2, planes, 0, q0 * vp, e2.M, e2.N, qn * vp, bn2, 0, md.epoch2, L.pair2, e2, algo);
+            e2.M = (int)(nm * va);
+            e2.N = vb;
+            e2.out = out + m0 * va * vb;
+            e2.ldc = vb;
+            e2.vec = ((uintptr_t)e2.out % 16 == 0) && (vb % 2 == 0);
+            e2.err = Ll.d_err;
+            launch_gemm(c, m2, planes, 0, q0 * vpb, e2.M, e2.N, qn * vpb, bn2, 0, md.epoch2, Lr.pair2, e2,
+                        2.0 * (double)nm * va * (double)vb * qn * vb);
         }
     }
 }
@@ -1327,11 +1333,19 @@ TuneCache* tune_cache_open(const char* path) {
 }
 
 void ladder_tc_apply(LadderTC& L, Ctx& c, const double* X, long long nmat, double* out, const LadderMode& md) {
-    const int v = L.v, vp = L.vp, naux = L.naux, planes = md.planes;
+    ladder_tc_apply_pair(L, L, c, X, nmat, out, md);
+}
+
+void ladder_tc_apply_pair(LadderTC& Ll, LadderTC& Lr, Ctx& c, const double* X, long long nmat, double* out,
+                          const LadderMode& md) {
+    LadderTC& L = Ll;
+    const int v = Ll.v, vp = Lr.vp, vpl = Ll.vp, vr = Lr.v, naux = Ll.naux, planes = md.planes;
     if (nmat <= 0) return;
+    if (Lr.naux != naux) throw Error(-1, "ladder: the two B^Q factors differ in naux");
     if (planes != 2 && planes != 3) throw Error(-1, "ladder: planes must be 2 or 3");
     if (md.epoch1 < 0 || md.epoch2 < 0) throw Error(-1, "ladder: negative epoch length");
-    if (planes > L.nplanes) split_B(L, c, planes);  // the third plane only when first asked for
+    if (planes > Ll.nplanes) split_B(Ll, c, planes);  // the third plane only when first asked for
+    if (planes > Lr.nplanes) split_B(Lr, c, planes);
     ADC_CUDA(cudaMemsetAsync(L.d_err, 0, sizeof(int), c.stream));  // clear a timeout of an earlier call
     // Scratch budget for Z (all planes): ~4 GiB.  Matrices are processed in
     // groups small enough that a chunk holds >= 8 auxiliary functions (long K
@@ -1345,12 +1359,12 @@ void ladder_tc_apply(LadderTC& L, Ctx& c, const double* X, long long nmat, doubl
     mg = std::min(mg, nmat);
     int qc = L.chunk > 0 ? std::min(L.chunk, qmax) : (int)std::max<long long>(1, budget / (per_mq * mg));
     qc = std::max(1, std::min(qc, qmax));
-    int bn2 = L.bn2[planes];
+    int bn2 = Lr.bn2[planes];
     Arena::Mark mk = c.arena.mark();
     auto scratch = [&](int q) {
         Planes xt{}, zt{};
         for (int p = 0; p < planes; ++p) {
-            xt.p[p] = (__nv_bfloat16*)c.arena.alloc(mg * vp * vp * 2);
+            xt.p[p] = (__nv_bfloat16*)c.arena.alloc(mg * vp * vpl * 2);
             zt.p[p] = (__nv_bfloat16*)c.arena.alloc(mg * v * (long long)q * vp * 2);
         }
         return std::make_pair(xt, zt);
@@ -1358,7 +1372,8 @@ void ladder_tc_apply(LadderTC& L, Ctx& c, const double* X, long long nmat, doubl
     if (c.tuner && !c.timing && L.chunk <= 0) {
         // GEMM2 tile width and auxiliary chunk: measured once per problem, cached
         TuneCache* tc = (TuneCache*)c.tuner;
-        const std::string key = "ladder:sm" + std::to_string(dev_info().num_sms) + ":v" + std::to_string(v) + ":naux" +
+        const std::string key = "ladder:sm" + std::to_string(dev_info().num_sms) + ":v" + std::to_string(v) +
+                                (vr != v ? "x" + std::to_string(vr) : std::string()) + ":naux" +
                                 std::to_string(naux) + ":nmat" + std::to_string(nmat) + ":p" + std::to_string(planes) +
                                 ":e" + std::to_string(md.epoch1) + "," + std::to_string(md.epoch2);
         std::vector<int> got;
@@ -1370,15 +1385,16 @@ void ladder_tc_apply(LadderTC& L, Ctx& c, const double* X, long long nmat, doubl
             std::vector<int> qcs{qc};
             if (qc / 2 >= 1) qcs.push_back(qc / 2);
             if (2 * qc <= qmax) qcs.push_back(2 * qc);
-            double* tmp = c.arena.dalloc((size_t)nmat * v * v);  // timing runs accumulate here
-            ADC_CUDA(cudaMemsetAsync(tmp, 0, (size_t)nmat * v * v * sizeof(double), c.stream));
+            double* tmp = c.arena.dalloc((size_t)nmat * v * vr);  // timing runs accumulate here
+            ADC_CUDA(cudaMemsetAsync(tmp, 0, (size_t)nmat * v * vr * sizeof(double), c.stream));
             float best = 1e30f;
             int bb = bn2, bq = qc;
             for (int q : qcs) {
                 Arena::Mark m2 = c.arena.mark();
                 auto sc = scratch(q);
-                for (int b : bn_candidates(v, maxbn, {256, 224, 208, 192, 160, 128})) {
-                    const float ms = time_on_stream(c, [&] { run_ladder(L, c, X, nmat, tmp, md, sc.first, sc.second, mg, q, b); });
+                for (int b : bn_candidates(vr, maxbn, {256, 224, 208, 192, 160, 128})) {
+                    const float ms =
+                        time_on_stream(c, [&] { run_ladder(Ll, Lr, c, X, nmat, tmp, md, sc.first, sc.second, mg, q, b); });
                     if (ms < best) best = ms, bb = b, bq = q;
                 }
                 c.arena.release(m2);
@@ -1390,7 +1406,7 @@ void ladder_tc_apply(LadderTC& L, Ctx& c, const double* X, long long nmat, doubl
         }
     }
     auto sc = scratch(qc);
-    run_ladder(L, c, X, nmat, out, md, sc.first, sc.second, mg, qc, bn2);
+    run_ladder(Ll, Lr, c, X, nmat, out, md, sc.first, sc.second, mg, qc, bn2);
     check_err(L, c);
     c.arena.release(mk);
 }
@@ -1425,7 +1441,7 @@ bool ladder_tc_apply_scratch(LadderTC& L, Ctx& c, const double* X, long long nma
     zt.p[1] = zt.p[0] + mg * v * (long long)qc * vp;
     ADC_CUDA(cudaMemsetAsync(L.d_err, 0, sizeof(int), c.stream));  // clear a timeout of an earlier call
     ADC_CUDA(cudaMemsetAsync(out, 0, (size_t)nmat * v * v * sizeof(double), c.stream));
-    run_ladder(L, c, X, nmat, out, md, xt, zt, mg, qc, L.bn2[planes]);
+    run_ladder(L, L, c, X, nmat, out, md, xt, zt, mg, qc, L.bn2[planes]);
     check_err(L, c);
     return true;
 }

@@ -24,6 +24,10 @@ struct LadderTC;  // owns the BF16 hi/lo copies of B^Q_vv in the GEMM layouts
 LadderTC* ladder_tc_create(Ctx& c, const double* Bvv, int naux, int nvir, int aux_chunk);
 void ladder_tc_destroy(LadderTC* L);
 void ladder_tc_apply(LadderTC& L, Ctx& c, const double* X, long long nmat, double* out, const LadderMode& md);
+// out[n] += sum_Q Bl^Q X[n] Br^Q for nmat rectangular Ll.v x Lr.v matrices (the two B^Q
+// factors share naux; e.g. the alpha and beta virtual blocks of an open-shell reference)
+void ladder_tc_apply_pair(LadderTC& Ll, LadderTC& Lr, Ctx& c, const double* X, long long nmat, double* out,
+                          const LadderMode& md);
 bool ladder_tc_apply_scratch(LadderTC& L, Ctx& c, const double* X, long long nmat, double* out, const LadderMode& md,
                              void* scratch, size_t bytes);
 

@@ -116,5 +116,47 @@ def test_unrestricted_argument_errors():
     L = load_library()
     e = np.zeros(2)
     assert L.adc_davidson(g._h, 0, 1e-6, None, e.ctypes.data, None, None, None) != 0  # nroots < 1
+    with pytest.raises(ADCError):  # no beta virtual orbital: no per-spin mixed-precision ladder
+        s2 = make_open_shell_system(2, 2, 2, 4, seed=0)
+        ADCUnrestricted(s2.eps_a, s2.eps_b, s2.B_a, s2.B_b, 2, 2, order=2, kind="ip", precision="bf16x3")
     assert L.adc_mp_energy(g._h, e.ctypes.data, 2) != 0
     g.close()
+
+
+@pytest.mark.parametrize("kind", ["ea", "ip"])
+def test_unrestricted_sigma_mixed(kind):
+    """Mixed-precision UADC(3) sigma (the ladder per spin block on the tensor cores with
+    split-BF16 operands, the other large contractions on the tensor-core GEMM) against the
+    oracle: the split-BF16 bound of the closed-shell mixed tests, 3e-5 of max |sigma|."""
+    from oracle.unrestricted import UnrestrictedDFADC
+    from paper_2012_06714_gb300 import ADCUnrestricted
+
+    na, nb, nmo, naux = 5, 4, 23, 41
+    s = make_open_shell_system(na, nb, nmo, naux, seed=2)
+    ref = UnrestrictedDFADC(s, 3, kind)
+    gpu = ADCUnrestricted(s.eps_a, s.eps_b, s.B_a, s.B_b, na, nb, order=3, kind=kind, precision="bf16x3")
+    X = np.random.default_rng(6).standard_normal((3, gpu.dim))
+    Sg = gpu.sigma(X)
+    Sr = ref.sigma(X)
+    gpu.close()
+    assert np.abs(Sg - Sr).max() <= 3e-5 * np.abs(Sr).max(), np.abs(Sg - Sr).max()
+
+
+@pytest.mark.parametrize("kind", ["ea", "ip"])
+def test_unrestricted_roots_mixed_vs_fp64(kind):
+    """Mixed-precision UADC(3) roots, continued with the accurate operator (FP64 contractions,
+    promoted ladder) to residual 1e-7, against the FP64 GPU roots: 1e-6 Eh and P within 1e-6."""
+    from paper_2012_06714_gb300 import ADCUnrestricted
+
+    na, nb, nmo, naux = 4, 3, 11, 30
+    s = make_open_shell_system(na, nb, nmo, naux, seed=2)
+    g64 = ADCUnrestricted(s.eps_a, s.eps_b, s.B_a, s.B_b, na, nb, order=3, kind=kind)
+    e64, p64, _, _ = g64.davidson(3, tol=1e-10, res_tol=1e-7)
+    g64.close()
+    gmx = ADCUnrestricted(s.eps_a, s.eps_b, s.B_a, s.B_b, na, nb, order=3, kind=kind, precision="bf16x3",
+                          refine_res_tol=1e-7)
+    emx, pmx, _, st = gmx.davidson(3, tol=1e-10, res_tol=1e-5)
+    gmx.close()
+    assert st["status"] == 0
+    assert np.abs(emx - e64).max() < 1e-6, np.abs(emx - e64).max()
+    assert np.abs(pmx - p64).max() < 1e-6, np.abs(pmx - p64).max()
