@@ -121,6 +121,12 @@ typedef struct {
                              /* timed once on the device with each candidate, and the */
                              /* fastest is kept (file rewritten; read at setup; one   */
                              /* table per path, shared by the process's handles)      */
+    int cuda_graphs;         /* 1: in adc_davidson the sigma of a mixed-precision      */
+                             /* handle runs as a CUDA graph per block size (captured  */
+                             /* once on fixed buffers, replayed as one launch; for    */
+                             /* small systems, where launches dominate; needs a      */
+                             /* stream of the handle's own: adc_setup_batch, or      */
+                             /* adc_set_stream); 0 (default)                          */
 } adc_options;
 
 /* Fill *opt with the defaults listed above.  Returns ADC_OK or ADC_ERR_ARG (NULL). */
@@ -156,7 +162,7 @@ int adc_setup_batch(int nmol, const double* const* eps, const double* const* Bq,
 
 /* Replace the solver options of a handle (max_space_per_root, max_iter,
  * nguess_extra, res_tol, keep_per_root, refine, transition_order,
- * refine_res_tol); precision,
+ * refine_res_tol, cuda_graphs); precision,
  * contractions and aux_chunk stay as set up.  Errors: ADC_ERR_ARG. */
 int adc_set_options(adc_handle* h, const adc_options* opt);
 

@@ -56,6 +56,7 @@ class Options(ctypes.Structure):
         ("refine_res_tol", ctypes.c_double),
         ("m11_on_the_fly", ctypes.c_int),
         ("tune_cache", ctypes.c_char_p),
+        ("cuda_graphs", ctypes.c_int),
     ]
 
 
@@ -148,7 +149,7 @@ class ADC:
 
     def __init__(self, eps, B, nocc, order=3, kind="ea", precision="fp64", max_space_per_root=8, max_iter=100,
                  nguess_extra=2, res_tol=0.0, aux_chunk=0, keep_per_root=2, contractions=-1, refine=1,
-                 transition_order=0, refine_res_tol=0.0, m11_on_the_fly=0, tune_cache=None):
+                 transition_order=0, refine_res_tol=0.0, m11_on_the_fly=0, tune_cache=None, cuda_graphs=0):
         lib = load_library()
         self._lib = lib
         opt = Options()
@@ -166,9 +167,11 @@ class ADC:
         opt.refine_res_tol = refine_res_tol
         opt.m11_on_the_fly = m11_on_the_fly
         opt.tune_cache = None if tune_cache is None else os.fsencode(tune_cache)
+        opt.cuda_graphs = cuda_graphs
         self._solver = dict(max_space_per_root=max_space_per_root, max_iter=max_iter, nguess_extra=nguess_extra,
                             res_tol=res_tol, keep_per_root=keep_per_root, refine=refine,
-                            transition_order=transition_order, refine_res_tol=refine_res_tol)
+                            transition_order=transition_order, refine_res_tol=refine_res_tol,
+                            cuda_graphs=cuda_graphs)
         if isinstance(eps, np.ndarray):
             eps = np.ascontiguousarray(eps, dtype=np.float64)
             B = np.ascontiguousarray(B, dtype=np.float64)
@@ -233,7 +236,7 @@ class ADC:
         opt = Options()
         self._lib.adc_default_options(ctypes.byref(opt))
         for k in ("max_space_per_root", "max_iter", "nguess_extra", "res_tol", "keep_per_root", "refine",
-                  "transition_order", "refine_res_tol"):
+                  "transition_order", "refine_res_tol", "cuda_graphs"):
             setattr(opt, k, kw.pop(k, self._solver[k]))
         if kw:
             raise TypeError(f"not a solver option: {sorted(kw)}")

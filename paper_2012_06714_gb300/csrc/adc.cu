@@ -68,6 +68,14 @@ struct adc_handle {
     // 1p-1p / 1h-1h block applied on the fly (m11_on_the_fly): small intermediates of step 2
     double *otf_g = nullptr, *otf_Hq = nullptr, *otf_gz = nullptr, *otf_Zm = nullptr, *otf_U = nullptr;
     std::vector<void*> owned;
+    // sigma captured as CUDA graphs (cuda_graphs): one per block size, on fixed input / output buffers
+    struct SigmaGraph {
+        long long n = 0;
+        double *X = nullptr, *S = nullptr;
+        cudaGraphExec_t exec = nullptr;
+    };
+    std::vector<SigmaGraph> graphs;
+    bool graphs_failed = false;  // a capture failed once: sigma runs without graphs on this handle
     cudaStream_t own_stream = nullptr;  // created by adc_setup_batch, destroyed with the handle
     std::string err;
     long long npairs() const {
@@ -85,6 +93,8 @@ struct adc_handle {
     }
     ~adc_handle() {
         if (ctx.stream) cudaStreamSynchronize(ctx.stream);
+        for (auto& g : graphs)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
         ladder_tc_destroy(tc);
         ladder_tc_destroy(tc_b);
         for (void* p : owned) cudaFree(p);
@@ -1137,7 +1147,8 @@ static void sigma_ip(adc_handle* h, const double* Xin, double* Sout, long long n
 
 static void sigma_unrestricted(adc_handle* h, const double* Xin, double* Sout, long long n);
 
-static void sigma_device(adc_handle* h, const double* X, double* S, long long nvec) {
+// the launches of one sigma (no host synchronisation inside: it may run under stream capture)
+static void sigma_launch(adc_handle* h, const double* X, double* S, long long nvec) {
     Ctx& c = h->ctx;
     if (!h->refining) c.gemm_mode = h->cmode_sigma;
     // a timeout of an earlier call left the flag raised; every call starts clean
@@ -1148,12 +1159,80 @@ static void sigma_device(adc_handle* h, const double* X, double* S, long long nv
         sigma_ea(h, X, S, nvec);
     else
         sigma_ip(h, X, S, nvec);
+}
+
+static void sigma_device(adc_handle* h, const double* X, double* S, long long nvec) {
+    Ctx& c = h->ctx;
+    sigma_launch(h, X, S, nvec);
     if (c.d_err) {
         int e = 0;
         ADC_CUDA(cudaMemcpyAsync(&e, c.d_err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
         ADC_CUDA(cudaStreamSynchronize(c.stream));
         if (e) throw Error(ADC_ERR_TIMEOUT, "sigma: a bounded device wait of the tensor-core GEMM timed out");
     }
+}
+
+// sigma through a CUDA graph (cuda_graphs, mixed-precision handles): the launches of one sigma
+// of n vectors are captured once on fixed buffers (after one ordinary evaluation has made every
+// allocation, operand cache entry and tile choice they need) and replayed as one launch; the
+// inputs and outputs are copied to and from the fixed buffers, and the timeout flags of the
+// tensor-core kernels are read after the replay.  A capture that fails leaves the handle on
+// ordinary launches.
+static void sigma_run(adc_handle* h, const double* X, double* S, long long n) {
+    Ctx& c = h->ctx;
+    if (!h->opt.cuda_graphs || h->graphs_failed || h->refining || h->cmode_sigma != 2 || c.timing || !c.stream) {
+        // (the legacy default stream cannot be captured: graphs need the handle on a stream of its own)
+        sigma_device(h, X, S, n);
+        return;
+    }
+    const long long dim = h->dim();
+    adc_handle::SigmaGraph* g = nullptr;
+    for (auto& e : h->graphs)
+        if (e.n == n) g = &e;
+    if (!g) {
+        adc_handle::SigmaGraph e;
+        e.n = n;
+        e.X = h->dmalloc(n * dim);
+        e.S = h->dmalloc(n * dim);
+        ADC_CUDA(cudaMemcpyAsync(e.X, X, (size_t)n * dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+        sigma_device(h, e.X, e.S, n);  // allocations, cached operands, tiles
+        ADC_CUDA(cudaStreamSynchronize(c.stream));
+        cudaGraph_t graph = nullptr;
+        bool ok = true;
+        c.capturing = true;
+        c.arena.frozen = true;
+        ADC_CUDA(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
+        try {
+            sigma_launch(h, e.X, e.S, n);
+        } catch (const std::exception&) {
+            ok = false;
+        }
+        const cudaError_t ec = cudaStreamEndCapture(c.stream, &graph);
+        c.capturing = false;
+        c.arena.frozen = false;
+        if (ok && ec == cudaSuccess && graph && cudaGraphInstantiate(&e.exec, graph, 0) == cudaSuccess) {
+            cudaGraphDestroy(graph);
+            h->graphs.push_back(e);
+            ADC_CUDA(cudaMemcpyAsync(S, e.S, (size_t)n * dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+            return;  // the ordinary evaluation above computed this call's result
+        }
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        h->graphs_failed = true;
+        ADC_CUDA(cudaMemcpyAsync(S, e.S, (size_t)n * dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+        return;
+    }
+    ADC_CUDA(cudaMemcpyAsync(g->X, X, (size_t)n * dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    ADC_CUDA(cudaGraphLaunch(g->exec, c.stream));
+    ADC_CUDA(cudaMemcpyAsync(S, g->S, (size_t)n * dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    if (c.d_err) {
+        int e = 0;
+        ADC_CUDA(cudaMemcpyAsync(&e, c.d_err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+        ADC_CUDA(cudaStreamSynchronize(c.stream));
+        if (e) throw Error(ADC_ERR_TIMEOUT, "sigma: a bounded device wait of the tensor-core GEMM timed out");
+    }
+    if (h->tc) ladder_tc_check(*h->tc, c);
+    if (h->tc_b) ladder_tc_check(*h->tc_b, c);
 }
 
 // --------------------------------------------------------------------------
@@ -1240,7 +1319,7 @@ struct Davidson {
     }
     void sigma(int first, int count) {
         auto t0 = std::chrono::steady_clock::now();
-        sigma_device(h, V + (long long)first * dim, W + (long long)first * dim, count);
+        sigma_run(h, V + (long long)first * dim, W + (long long)first * dim, count);
         ADC_CUDA(cudaStreamSynchronize(h->ctx.stream));
         sigma_seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         nsig += count;
@@ -2568,6 +2647,7 @@ int adc_set_options(adc_handle* h, const adc_options* opt) {
     h->opt.refine = opt->refine;
     h->opt.transition_order = opt->transition_order;
     h->opt.refine_res_tol = opt->refine_res_tol;
+    h->opt.cuda_graphs = opt->cuda_graphs;
     // m11_on_the_fly is fixed at setup
     return ADC_OK;
 }
@@ -2629,6 +2709,7 @@ int adc_default_options(adc_options* opt) {
     opt->refine_res_tol = 0.0;
     opt->m11_on_the_fly = 0;
     opt->tune_cache = nullptr;
+    opt->cuda_graphs = 0;
     return ADC_OK;
 }
 

@@ -466,6 +466,8 @@ void sum_slices(Ctx& c, int S, long long n, const double* T, double* C) {
 }
 
 void ensure_side_streams(Ctx& c, int count) {
+    if (c.capturing && (!c.side_fork || (int)c.side.size() < count))
+        throw Error(-3, "side stream creation during stream capture");
     if (!c.side_fork) ADC_CUDA(cudaEventCreateWithFlags(&c.side_fork, cudaEventDisableTiming));
     while ((int)c.side.size() < count) {
         cudaStream_t s = nullptr;
@@ -580,6 +582,7 @@ static void einsum_fp32(Ctx& c, const std::string& la, const std::string& lb, co
         if (constant) {
             auto it = c.f32cache.find({src, key});
             if (it != c.f32cache.end()) return (const float*)it->second;
+            if (c.capturing) throw Error(-3, "operand cache miss during stream capture");
             dst = (float*)dev_alloc(n * sizeof(float), c.stream);
             c.f32cache[{src, key}] = dst;
         } else {
@@ -651,6 +654,7 @@ static void einsum_tc(Ctx& c, const std::string& la, const std::string& lb, cons
         if (constant) {
             auto it = c.bf16cache.find({src, key});
             if (it != c.bf16cache.end()) return it->second;
+            if (c.capturing) throw Error(-3, "operand cache miss during stream capture");
             base = dev_alloc(2 * rows * Kp * 2, c.stream);
             c.bf16cache[{src, key}] = base;
         } else {
@@ -663,6 +667,7 @@ static void einsum_tc(Ctx& c, const std::string& la, const std::string& lb, cons
     void* pa = planes_of(Ap, la, fa + con, M, constA);
     void* pb = planes_of(Bp, lb, fb + con, N, constB);
     if (!c.d_err) {
+        if (c.capturing) throw Error(-3, "error flag allocation during stream capture");
         c.d_err = (int*)dev_alloc(sizeof(int), c.stream);
         ADC_CUDA(cudaMemsetAsync(c.d_err, 0, sizeof(int), c.stream));
     }

@@ -42,6 +42,7 @@ struct Error : std::runtime_error {
 class Arena {
    public:
     cudaStream_t stream = nullptr;
+    bool frozen = false;  // set while a stream capture records: growing would allocate inside the graph
     ~Arena() { free_all(); }
     struct Mark {
         size_t block, top;
@@ -67,6 +68,7 @@ class Arena {
             } else
                 break;
         }
+        if (frozen) throw Error(-3, "arena: growth during stream capture");
         size_t cap = bytes > (size_t(256) << 20) ? bytes : (size_t(256) << 20);
         void* p = nullptr;
         ADC_CUDA(cudaMallocAsync(&p, cap, stream));
@@ -136,6 +138,9 @@ struct Ctx {
     std::map<std::pair<const void*, std::string>, void*> bf16cache;
     int* d_err = nullptr;  // device flag raised by a bounded wait that gave up (tensor-core GEMMs)
     void* tuner = nullptr;  // TuneCache of the tile autotuner (ladder_tc.cuh), or NULL: cost-model tiles
+    // a CUDA-graph capture of sigma is recording on `stream`: no host synchronisation, no
+    // allocation, no tuning; the timeout flags are read after the graph's replay instead
+    bool capturing = false;
     // side streams for concurrent K slices of a contraction, with their fork / join events
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> side_join;

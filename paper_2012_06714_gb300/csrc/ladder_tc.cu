@@ -1240,6 +1240,7 @@ void run_ladder(LadderTC& Ll, LadderTC& Lr, Ctx& c, const double* X, long long n
 }
 
 void check_err(LadderTC& L, Ctx& c) {
+    if (c.capturing) return;  // read after the graph's replay
     int err = 0;
     ADC_CUDA(cudaMemcpyAsync(&err, L.d_err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     ADC_CUDA(cudaStreamSynchronize(c.stream));
@@ -1336,6 +1337,13 @@ void ladder_tc_apply(LadderTC& L, Ctx& c, const double* X, long long nmat, doubl
     ladder_tc_apply_pair(L, L, c, X, nmat, out, md);
 }
 
+void ladder_tc_check(LadderTC& L, Ctx& c) {
+    int err = 0;
+    ADC_CUDA(cudaMemcpyAsync(&err, L.d_err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    ADC_CUDA(cudaStreamSynchronize(c.stream));
+    if (err) throw Error(-5, "ladder: a bounded device wait timed out");
+}
+
 void ladder_tc_apply_pair(LadderTC& Ll, LadderTC& Lr, Ctx& c, const double* X, long long nmat, double* out,
                           const LadderMode& md) {
     LadderTC& L = Ll;
@@ -1369,7 +1377,7 @@ void ladder_tc_apply_pair(LadderTC& Ll, LadderTC& Lr, Ctx& c, const double* X, l
         }
         return std::make_pair(xt, zt);
     };
-    if (c.tuner && !c.timing && L.chunk <= 0) {
+    if (c.tuner && !c.timing && !c.capturing && L.chunk <= 0) {
         // GEMM2 tile width and auxiliary chunk: measured once per problem, cached
         TuneCache* tc = (TuneCache*)c.tuner;
         const std::string key = "ladder:sm" + std::to_string(dev_info().num_sms) + ":v" + std::to_string(v) +
@@ -1460,7 +1468,7 @@ void tc_gemm(Ctx& c, const void* const* A, const void* const* B, long long M, lo
     if (!c.d_err) throw Error(-1, "tc_gemm: no device error flag");
     const int n = (int)std::min<long long>(N, 1 << 20);
     int BN = pick_bn(n, 256);
-    if (c.tuner && !c.timing) {
+    if (c.tuner && !c.timing && !c.capturing) {
         // tile width measured once per shape (every run overwrites C, so the runs are interchangeable)
         TuneCache* tc = (TuneCache*)c.tuner;
         const std::string key = "gemm:sm" + std::to_string(dev_info().num_sms) + ":M" + std::to_string(M) + ":N" +

@@ -23,6 +23,8 @@ struct LadderTC;  // owns the BF16 hi/lo copies of B^Q_vv in the GEMM layouts
 
 LadderTC* ladder_tc_create(Ctx& c, const double* Bvv, int naux, int nvir, int aux_chunk);
 void ladder_tc_destroy(LadderTC* L);
+// throws ADC_ERR_TIMEOUT if a bounded wait of this ladder's kernels gave up (synchronises c.stream)
+void ladder_tc_check(LadderTC& L, Ctx& c);
 void ladder_tc_apply(LadderTC& L, Ctx& c, const double* X, long long nmat, double* out, const LadderMode& md);
 // out[n] += sum_Q Bl^Q X[n] Br^Q for nmat rectangular Ll.v x Lr.v matrices (the two B^Q
 // factors share naux; e.g. the alpha and beta virtual blocks of an open-shell reference)

@@ -72,3 +72,29 @@ def test_batch_uneven_sizes_concurrent():
         assert np.abs(e[k] - e1).max() < 1e-9, k
     t_seq = time.perf_counter() - t0
     print(f"16 IP-ADC(3) systems: batched {t_batch:.2f} s, one at a time {t_seq:.2f} s")
+
+
+def test_batch_cuda_graphs_same_roots():
+    """The batched IP-ADC(3) solve with each handle's sigma captured as CUDA graphs
+    (cuda_graphs = 1: one graph per block size, replayed as one launch) gives the roots of
+    the ordinary launches (same kernels, same order: 1e-10 Eh); 8 molecules of the batched
+    size distribution, mixed precision.  Wall times of both are printed."""
+    from paper_2012_06714_gb300 import ADCBatch
+
+    mols = batched_ip_molecules(8)
+    systems = []
+    for m in mols:
+        s = make_system(m["nocc"], m["nvir"], m["naux"], seed=m["seed"])
+        systems.append((s.eps, s.B, m["nocc"]))
+    opts = dict(res_tol=1e-4, max_iter=300, max_space_per_root=24, keep_per_root=4)
+    res = {}
+    for graphs in (0, 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b = ADCBatch(systems, order=3, kind="ip", precision="bf16x3", cuda_graphs=graphs, **opts)
+        e, p, st, status = b.davidson(6, tol=1e-6)
+        b.close()
+        res[graphs] = (e, time.perf_counter() - t0)
+        assert (status == 0).all()
+    assert np.abs(res[0][0] - res[1][0]).max() < 1e-10
+    print(f"8 IP-ADC(3) systems: ordinary launches {res[0][1]:.2f} s, CUDA graphs {res[1][1]:.2f} s")
