@@ -277,6 +277,52 @@ def run_ladder_case(args):
     return 0
 
 
+def run_ladder_large(args):
+    """The DF-ladder kernel at the per-launch shapes of the largest workload, EA-ADC(3) with
+    nocc=68, nvir=960, naux=3000 (1028 MOs), 4 trial vectors: 4 x 68 = 272 ladder matrices of
+    960 x 960 per sigma step.  That workload's setup does not fit one GPU as the handle is laid
+    out (its o^2 v^2 tensors are 34 GB each), so the ladder runs in a handle with nocc=4 and
+    68 trial vectors -- the same 272 matrices and the same B^Q (960 x 960 x 3000), hence the same
+    GEMM launches and flops (4 naux nvir^3 per matrix).  Reports the ladder GEMMs' live
+    CUDA-event throughput over `--steps` sigma calls after one warm-up call."""
+    import torch
+
+    from adc_inputs import make_system
+    from paper_2012_06714_gb300 import ADC
+
+    torch.cuda.set_device(0)
+    o, v, naux, nvec = 4, 960, 3000, 68
+    s = make_system(o, v, naux, seed=0)
+    t0 = time.perf_counter()
+    g = ADC(torch.from_numpy(s.eps).cuda(), torch.from_numpy(s.B).cuda(), o, order=3, kind="ea", precision="bf16x3",
+            tune_cache=args.tune_cache)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    X = torch.randn((nvec, g.dim), device="cuda", dtype=torch.float64) / np.sqrt(g.dim)
+    S = torch.empty_like(X)
+    g.sigma(X, out=S)
+    torch.cuda.synchronize()
+    g.kernel_timing(True)
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.steps)):
+        g.sigma(X, out=S)
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) / max(1, args.steps)
+    kt = g.kernel_timing(False)
+    g.close()
+    steps = max(1, args.steps)
+    bf16_peak, bf16_burst, _, src = peaks()
+    lt = kt["ladder_algo_flops"] / (kt["ladder_ms"] / 1e3) / 1e12
+    out = {"case": "DF ladder at the 1028-MO shapes: nvir=960, naux=3000, 272 matrices per sigma "
+                   "(4 vectors x 68 occupied of EA-ADC(3) 68/960/3000), run as nocc=4 x 68 vectors",
+           "ladder_flops_per_sigma": kt["ladder_algo_flops"] / steps, "ladder_ms_per_sigma": kt["ladder_ms"] / steps,
+           "ladder_launches_per_sigma": kt["ladder_launches"] / steps, "ladder_tflops": lt,
+           "frac_of_sustained_bf16_over_3": lt / (bf16_peak / 3.0), "peak_source": src,
+           "sigma_wall_s": wall, "setup_s": setup_s}
+    print(json.dumps(out))
+    return 0
+
+
 def run_davidson_case(args):
     """Small profiling case of the Davidson subspace kernels (for ncu):
     EA-ADC(3) mixed precision with nocc=24, nvir=240, naux=500 (1.38e6-element
@@ -604,6 +650,8 @@ def main():
     ap.add_argument("--ladder-case", action="store_true", help="small ladder profiling case (for ncu)")
     ap.add_argument("--davidson-case", action="store_true", help="small Davidson profiling case (for ncu)")
     ap.add_argument("--batched", action="store_true", help="batched IP-ADC(3) workload (64 molecules)")
+    ap.add_argument("--ladder-large", action="store_true",
+                    help="ladder kernel at the per-launch shapes of the 1028-MO workload")
     ap.add_argument("--nmol", type=int, default=64)
     ap.add_argument("--tune-cache", default=None,
                     help="tile autotuner cache file (tiles measured in the first warm-up step)")
@@ -616,6 +664,8 @@ def main():
         return run_fp64_plain(args)
     if args.batched:
         return run_batched(args)
+    if args.ladder_large:
+        return run_ladder_large(args)
     if args.ladder_case:
         return run_ladder_case(args)
     if args.impl == "reference":

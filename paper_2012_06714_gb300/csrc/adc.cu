@@ -2753,6 +2753,9 @@ static int setup_one(const double* eps, const double* Bq, int nocc, int nvir, in
         }
         setup(h, eps, Bq, on_device);
         ADC_CUDA(cudaStreamSynchronize(h->ctx.stream));
+        // setup's scratch (ladder Z, o^2 v^2 temporaries) goes back to the device; sigma regrows
+        // what it needs (many handles at once would otherwise each keep their setup peak)
+        h->ctx.arena.free_all();
     } catch (const adc::Error& e) {
         msg = e.what();
         int code = e.code;
@@ -2869,6 +2872,8 @@ int adc_setup_unrestricted(const double* eps_a, const double* eps_b, const doubl
     if (opt) h->opt = *opt;
     try {
         setup_unrestricted(h, eps_so.data(), Bso.data());
+        ADC_CUDA(cudaStreamSynchronize(h->ctx.stream));
+        h->ctx.arena.free_all();
     } catch (const adc::Error& e) {
         g_setup_error = e.what();
         const int code = e.code;

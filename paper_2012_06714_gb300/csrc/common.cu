@@ -19,15 +19,19 @@ struct PermArgs {
     long long sin[kMaxDim];  // input stride for each output axis
 };
 
+// I: the index type of the coordinate arithmetic (32-bit when every offset fits: integer
+// division by a runtime divisor is several times cheaper than in 64 bits)
+template <typename I>
 __global__ void permute_kernel(const double* __restrict__ in, double* __restrict__ out, PermArgs a, long long total,
                                double alpha, double beta) {
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
-        long long r = idx, off = 0;
+        I r = (I)idx, off = 0;
         for (int j = a.nd - 1; j >= 0; --j) {
-            long long cj = r % a.dout[j];
-            r /= a.dout[j];
-            off += cj * a.sin[j];
+            const I d = (I)a.dout[j];
+            const I q = r / d;
+            off += (r - q * d) * (I)a.sin[j];
+            r = q;
         }
         double v = alpha * in[off];
         out[idx] = (beta == 0.0) ? v : v + beta * out[idx];
@@ -61,19 +65,21 @@ __global__ void fill_kernel(long long n, double v, double* __restrict__ y) {
 }
 
 // out[p][r*Kp + k] (two BF16 planes) from the permuted input, zero for k >= K
+template <typename I>
 __global__ void permute_split_kernel(const double* __restrict__ in, __nv_bfloat16* __restrict__ o0,
                                      __nv_bfloat16* __restrict__ o1, PermArgs a, long long rows, long long K, long long Kp) {
     const long long total = rows * Kp;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
-        const long long r = idx / Kp, k = idx - r * Kp;
+        const I r = (I)(idx / Kp), k = (I)(idx - (long long)r * Kp);
         double x = 0.0;
-        if (k < K) {
-            long long lin = r * K + k, off = 0;
+        if (k < (I)K) {
+            I lin = r * (I)K + k, off = 0;
             for (int j = a.nd - 1; j >= 0; --j) {
-                long long cj = lin % a.dout[j];
-                lin /= a.dout[j];
-                off += cj * a.sin[j];
+                const I d = (I)a.dout[j];
+                const I q = lin / d;
+                off += (lin - q * d) * (I)a.sin[j];
+                lin = q;
             }
             x = in[off];
         }
@@ -406,7 +412,10 @@ void permute(Ctx& c, const double* in, const Shape& s, const int* perm, double* 
         total *= a.dout[j];
     }
     if (total == 0) return;
-    permute_kernel<<<grid_for(total), 256, 0, c.stream>>>(in, out, a, total, alpha, beta);
+    if (total < (1LL << 31))
+        permute_kernel<unsigned><<<grid_for(total), 256, 0, c.stream>>>(in, out, a, total, alpha, beta);
+    else
+        permute_kernel<long long><<<grid_for(total), 256, 0, c.stream>>>(in, out, a, total, alpha, beta);
     ++c.kernels;
     ADC_CUDA(cudaGetLastError());
 }
@@ -445,8 +454,12 @@ void split_planes(Ctx& c, const double* in, const Shape& s, const int* perm, lon
     PermArgs a = perm_args(s, perm, total);
     if (total != rows * K) throw Error(-1, "split_planes: shape mismatch");
     if (rows * Kp == 0) return;
-    permute_split_kernel<<<grid_for(rows * Kp), 256, 0, c.stream>>>(in, (__nv_bfloat16*)out[0], (__nv_bfloat16*)out[1], a,
-                                                                    rows, K, Kp);
+    if (rows * Kp < (1LL << 31))
+        permute_split_kernel<unsigned><<<grid_for(rows * Kp), 256, 0, c.stream>>>(
+            in, (__nv_bfloat16*)out[0], (__nv_bfloat16*)out[1], a, rows, K, Kp);
+    else
+        permute_split_kernel<long long><<<grid_for(rows * Kp), 256, 0, c.stream>>>(
+            in, (__nv_bfloat16*)out[0], (__nv_bfloat16*)out[1], a, rows, K, Kp);
     ++c.kernels;
     ADC_CUDA(cudaGetLastError());
 }

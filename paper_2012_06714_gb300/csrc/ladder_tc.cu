@@ -1377,40 +1377,34 @@ void ladder_tc_apply_pair(LadderTC& Ll, LadderTC& Lr, Ctx& c, const double* X, l
         }
         return std::make_pair(xt, zt);
     };
-    if (c.tuner && !c.timing && !c.capturing && L.chunk <= 0) {
-        // GEMM2 tile width and auxiliary chunk: measured once per problem, cached
+    if (c.tuner && !c.timing && !c.capturing && md.epoch1 == 0) {
+        // GEMM2 tile width of the sigma ladder (single-epoch GEMM1; the promoted modes of
+        // setup and refinement are one-off and keep the cost model's width): measured once
+        // per B^Q shape, on the first call's matrices, and cached
         TuneCache* tc = (TuneCache*)c.tuner;
         const std::string key = "ladder:sm" + std::to_string(dev_info().num_sms) + ":v" + std::to_string(v) +
                                 (vr != v ? "x" + std::to_string(vr) : std::string()) + ":naux" +
-                                std::to_string(naux) + ":nmat" + std::to_string(nmat) + ":p" + std::to_string(planes) +
-                                ":e" + std::to_string(md.epoch1) + "," + std::to_string(md.epoch2);
+                                std::to_string(naux) + ":p" + std::to_string(planes) + ":e" + std::to_string(md.epoch2);
         std::vector<int> got;
-        if (tune_get(tc, key, got) && got.size() == 2) {
+        if (tune_get(tc, key, got) && got.size() == 1) {
             bn2 = got[0];
-            qc = std::max(1, std::min(got[1], qmax));
         } else {
             const int maxbn = planes == 3 ? 128 : 256;
-            std::vector<int> qcs{qc};
-            if (qc / 2 >= 1) qcs.push_back(qc / 2);
-            if (2 * qc <= qmax) qcs.push_back(2 * qc);
             double* tmp = c.arena.dalloc((size_t)nmat * v * vr);  // timing runs accumulate here
             ADC_CUDA(cudaMemsetAsync(tmp, 0, (size_t)nmat * v * vr * sizeof(double), c.stream));
             float best = 1e30f;
-            int bb = bn2, bq = qc;
-            for (int q : qcs) {
-                Arena::Mark m2 = c.arena.mark();
-                auto sc = scratch(q);
-                for (int b : bn_candidates(vr, maxbn, {256, 224, 208, 192, 160, 128})) {
-                    const float ms =
-                        time_on_stream(c, [&] { run_ladder(Ll, Lr, c, X, nmat, tmp, md, sc.first, sc.second, mg, q, b); });
-                    if (ms < best) best = ms, bb = b, bq = q;
-                }
-                c.arena.release(m2);
+            int bb = bn2;
+            Arena::Mark m2 = c.arena.mark();
+            auto sc = scratch(qc);
+            for (int b : bn_candidates(vr, maxbn, {256, 224, 192, 160})) {
+                const float ms =
+                    time_on_stream(c, [&] { run_ladder(Ll, Lr, c, X, nmat, tmp, md, sc.first, sc.second, mg, qc, b); });
+                if (ms < best) best = ms, bb = b;
             }
+            c.arena.release(m2);
             check_err(L, c);
             bn2 = bb;
-            qc = bq;
-            tune_put(tc, key, {bn2, qc});
+            tune_put(tc, key, {bn2});
         }
     }
     auto sc = scratch(qc);
@@ -1479,7 +1473,7 @@ void tc_gemm(Ctx& c, const void* const* A, const void* const* B, long long M, lo
         } else {
             float best = 1e30f;
             int bb = BN, last = BN;
-            for (int b : bn_candidates(n, 256, {256, 192, 128, 64})) {
+            for (int b : bn_candidates(n, 256, {256, 128})) {
                 const float ms = time_on_stream(c, [&] { tc_gemm_bn(c, A, B, M, N, Kp, algo_flops, C, b); });
                 last = b;
                 if (ms < best) best = ms, bb = b;
