@@ -43,6 +43,9 @@ struct adc_handle {
     double *eps = nullptr, *Boo = nullptr, *Bov = nullptr, *Bvv = nullptr;
     double *ovov = nullptr, *oovv = nullptr, *oooo = nullptr, *ooov = nullptr;
     double *t = nullptr, *tau = nullptr, *t_2 = nullptr, *t1_2 = nullptr, *M11 = nullptr, *diag = nullptr;
+    // ADC(3) 2p1h / 2h1p block: the two ring terms that share the operand Y_jcb, as one integral
+    // combination (EA [i][a][j][c] = 2 (ia|jc) - (ji|ac); IP [i][a][k][b] = (ki|ab) - 2 (ia|kb))
+    double* ring2 = nullptr;
     double* t1_3 = nullptr;  // third-order singles (ADC(3) transition moments only), made on first use
     double emp[2] = {0.0, 0.0};  // MP correlation energy E(2), E(3) (Sec. III A step 2)
     // unrestricted (open-shell) reference: o, v count spin orbitals, the 2p1h / 2h1p basis
@@ -862,6 +865,15 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
     einsum(c, "Qij,Qab->ijab", 1.0, tn(h->Boo, {Q, o, o}), tn(h->Bvv, {Q, v, v}), 0.0, h->oovv, {o, o, v, v});
     einsum(c, "Qij,Qkl->ijkl", 1.0, tn(h->Boo, {Q, o, o}), tn(h->Boo, {Q, o, o}), 0.0, h->oooo, {o, o, o, o});
     einsum(c, "Qij,Qka->ijka", 1.0, tn(h->Boo, {Q, o, o}), tn(h->Bov, {Q, o, v}), 0.0, h->ooov, {o, o, o, v});
+    if (h->order >= 3) {
+        // ring2[i][a][j][c] = 2 (ia|jc) - (ji|ac) (EA) or (ji|ac) - 2 (ia|jc) (IP)
+        h->ring2 = h->dmalloc(o * v * o * v);
+        const bool ea = h->kind == ADC_EA;
+        axpby(c, o * v * o * v, ea ? 2.0 : -2.0, h->ovov, 0.0, h->ring2);
+        Shape s4{4, {o, o, v, v}};
+        int pr[4] = {1, 2, 0, 3};  // (j, i, a, c) -> (i, a, j, c)
+        permute(c, h->oovv, s4, pr, h->ring2, ea ? -1.0 : 1.0, 1.0);
+    }
     // amplitudes (Eqs. t_singles, t_doubles)
     h->t = h->dmalloc(o * o * v * v);
     k_make_t<<<grid_for(o * o * v * v), 256, 0, c.stream>>>((int)o, (int)v, h->eps, h->ovov, h->t);
@@ -1054,9 +1066,8 @@ static void sigma_ea(adc_handle* h, const double* Xin, double* Sout, long long n
         einsum(c, "nmea,imeb->niab", -1.0, tn(q, {n, o, v, v}), tc(t, {o, o, v, v}), 1.0, S2, {n, o, v, v});
         // 2p1h block, first order: ladder sum_cd (ac|bd) Y_icd (vvvv never stored)
         ladder(h, Y2, n * o, S2, h->refining ? h->lm_refine : h->lm_sigma);
-        //  - (ac|ji) Y_jcb + 2 (ai|jc) Y_jcb - (ai|jc) Y_jbc - (bd|ji) Y_jad
-        einsum(c, "jiac,njcb->niab", -1.0, tc(h->oovv, {o, o, v, v}), tn(Y2, {n, o, v, v}), 1.0, S2, {n, o, v, v});
-        einsum(c, "iajc,njcb->niab", 2.0, tc(h->ovov, {o, v, o, v}), tn(Y2, {n, o, v, v}), 1.0, S2, {n, o, v, v});
+        //  - (ac|ji) Y_jcb + 2 (ai|jc) Y_jcb - (ai|jc) Y_jbc - (bd|ji) Y_jad  (the first two as one)
+        einsum(c, "iajc,njcb->niab", 1.0, tc(h->ring2, {o, v, o, v}), tn(Y2, {n, o, v, v}), 1.0, S2, {n, o, v, v});
         einsum(c, "iajc,njbc->niab", -1.0, tc(h->ovov, {o, v, o, v}), tn(Y2, {n, o, v, v}), 1.0, S2, {n, o, v, v});
         einsum(c, "jibd,njad->niab", -1.0, tc(h->oovv, {o, o, v, v}), tn(Y2, {n, o, v, v}), 1.0, S2, {n, o, v, v});
     }
@@ -1126,8 +1137,7 @@ static void sigma_ip(adc_handle* h, const double* Xin, double* Sout, long long n
         einsum(c, "nljc,klca->njka", 1.0, tn(m, {n, o, o, v}), tc(t, {o, o, v, v}), 1.0, S2, {n, o, o, v});
         // 2h1p block, first order: -(ki|lj) Y_kla + (ki|ab) Y_kjb - 2 (ia|kb) Y_kjb + (ia|kb) Y_jkb + (kj|ab) Y_ikb
         einsum(c, "kilj,nkla->nija", -1.0, tc(h->oooo, {o, o, o, o}), tn(Y2, {n, o, o, v}), 1.0, S2, {n, o, o, v});
-        einsum(c, "kiab,nkjb->nija", 1.0, tc(h->oovv, {o, o, v, v}), tn(Y2, {n, o, o, v}), 1.0, S2, {n, o, o, v});
-        einsum(c, "iakb,nkjb->nija", -2.0, tc(h->ovov, {o, v, o, v}), tn(Y2, {n, o, o, v}), 1.0, S2, {n, o, o, v});
+        einsum(c, "iakb,nkjb->nija", 1.0, tc(h->ring2, {o, v, o, v}), tn(Y2, {n, o, o, v}), 1.0, S2, {n, o, o, v});
         einsum(c, "iakb,njkb->nija", 1.0, tc(h->ovov, {o, v, o, v}), tn(Y2, {n, o, o, v}), 1.0, S2, {n, o, o, v});
         einsum(c, "kjab,nikb->nija", 1.0, tc(h->oovv, {o, o, v, v}), tn(Y2, {n, o, o, v}), 1.0, S2, {n, o, o, v});
     }
