@@ -249,7 +249,7 @@ def run_ladder_case(args):
     """Small profiling case of the ladder kernel (for ncu): EA-ADC(3) with
     nocc=4, nvir=400, naux=400 and 40 trial vectors, i.e. 160 ladder matrices
     per sigma call -- the same per-launch GEMM shapes as the bench workload
-    (160 matrices, 10 auxiliary functions per chunk) with a few GB on the
+    (160 matrices, 40 auxiliary functions per chunk) with a few GB on the
     device.  Runs `--steps` sigma calls after one warm-up call and prints the
     ladder launch timing of the last call."""
     import torch
@@ -259,8 +259,10 @@ def run_ladder_case(args):
 
     o, v, naux, nvec = 4, 400, 400, 40
     s = make_system(o, v, naux, seed=0)
+    # contractions=1: the non-ladder terms off the tensor-core kernel, so that every k_gemm_pair
+    # launch is a ladder GEMM (setup: 2 ladders x 2 launches; each sigma: 10 chunks x 2)
     g = ADC(torch.from_numpy(s.eps).cuda(), torch.from_numpy(s.B).cuda(), o, order=3, kind="ea",
-            precision="bf16x3")
+            precision="bf16x3", contractions=1)
     X = torch.randn(nvec, g.dim, device="cuda", dtype=torch.float64)
     S = torch.empty_like(X)
     g.sigma(X, out=S)

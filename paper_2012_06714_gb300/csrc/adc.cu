@@ -96,8 +96,11 @@ struct adc_handle {
     }
     ~adc_handle() {
         if (ctx.stream) cudaStreamSynchronize(ctx.stream);
-        for (auto& g : graphs)
+        for (auto& g : graphs) {
             if (g.exec) cudaGraphExecDestroy(g.exec);
+            cudaFree(g.X);
+            cudaFree(g.S);
+        }
         ladder_tc_destroy(tc);
         ladder_tc_destroy(tc_b);
         for (void* p : owned) cudaFree(p);
@@ -1202,8 +1205,8 @@ static void sigma_run(adc_handle* h, const double* X, double* S, long long n) {
     if (!g) {
         adc_handle::SigmaGraph e;
         e.n = n;
-        e.X = h->dmalloc(n * dim);
-        e.S = h->dmalloc(n * dim);
+        e.X = (double*)dev_alloc((size_t)n * dim * sizeof(double), c.stream);
+        e.S = (double*)dev_alloc((size_t)n * dim * sizeof(double), c.stream);
         ADC_CUDA(cudaMemcpyAsync(e.X, X, (size_t)n * dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
         sigma_device(h, e.X, e.S, n);  // allocations, cached operands, tiles
         ADC_CUDA(cudaStreamSynchronize(c.stream));
@@ -1230,6 +1233,9 @@ static void sigma_run(adc_handle* h, const double* X, double* S, long long n) {
         cudaGetLastError();
         h->graphs_failed = true;
         ADC_CUDA(cudaMemcpyAsync(S, e.S, (size_t)n * dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+        ADC_CUDA(cudaStreamSynchronize(c.stream));
+        cudaFree(e.X);
+        cudaFree(e.S);
         return;
     }
     ADC_CUDA(cudaMemcpyAsync(g->X, X, (size_t)n * dim * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
@@ -1413,9 +1419,26 @@ struct Davidson {
 
 static void specfac_unrestricted(adc_handle* h, const double* Y, int nroots, double* specfac);
 
+static void drop_graphs(adc_handle* h) {
+    if (h->graphs.empty()) return;
+    cudaStreamSynchronize(h->ctx.stream);
+    for (auto& g : h->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        cudaFree(g.X);
+        cudaFree(g.S);
+    }
+    h->graphs.clear();
+}
+
 static int davidson(adc_handle* h, int nroots, double tol, const double* guess, double* energies, double* specfac,
                     double* vectors, double* stats) {
     Ctx& c = h->ctx;
+    // A captured sigma uses the scratch addresses of this call's arena layout: its graphs
+    // live exactly as long as this call.
+    struct GraphScope {
+        adc_handle* h;
+        ~GraphScope() { drop_graphs(h); }
+    } graph_scope{h};
     auto t0 = std::chrono::steady_clock::now();
     const long long dim = h->dim();
     const int nextra = std::max(0, h->opt.nguess_extra);
@@ -2955,6 +2978,9 @@ int adc_davidson(adc_handle* h, int nroots, double tol, const double* guess, dou
     GUARD(h, {
         int st = davidson(h, nroots, tol, guess, energies, specfac, vectors, stats);
         if (st == ADC_ERR_NOT_CONVERGED) h->err = "adc_davidson: not converged within max_iter";
+        // the solver's scratch (subspace, residuals, sigma intermediates) goes back to the device:
+        // many handles solved one after another would otherwise each keep their peak
+        h->ctx.arena.free_all(true);
         return st;
     })
 }

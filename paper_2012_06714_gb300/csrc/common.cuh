@@ -79,8 +79,14 @@ class Arena {
         return p;
     }
     double* dalloc(size_t n) { return (double*)alloc(n * sizeof(double)); }
-    void free_all() {
-        for (void* p : blocks_) cudaFree(p);
+    // release every block (stream-ordered on `stream` when async, else with cudaFree)
+    void free_all(bool async = false) {
+        for (void* p : blocks_) {
+            if (async)
+                cudaFreeAsync(p, stream);
+            else
+                cudaFree(p);
+        }
         blocks_.clear();
         caps_.clear();
         tops_.clear();
