@@ -743,7 +743,11 @@ void einsum(Ctx& c, const char* specstr, double alpha, const T& A, const T& B, d
     if (c.gemm_mode == 2 && nb == 1) {
         // the mixed sigma: tensor cores for the large contractions, own kernels for the rest
         const bool big = 2.0 * M * N * K >= c.fp32_min_flops;
-        if (big && std::min(M, N) > 8 && tc_gemm_fits(M, N, K)) {
+        // few-vector shapes stay on the tensor cores when their large operand is a constant of
+        // the handle (its split planes are cached once); the own bandwidth kernels take the rest
+        const bool skinny = std::min(M, N) <= 8;
+        const bool big_const = M <= N ? B.constant : A.constant;
+        if (big && tc_gemm_fits(M, N, K) && (!skinny || big_const)) {
             einsum_tc(c, sp.a, sp.b, sp.c, dim, fa, fb, con, alpha, A.p, B.p, beta, C, A.constant, B.constant);
         } else {
             const double* Ap = to_order(c, A.p, sp.a, dim, fa + con);

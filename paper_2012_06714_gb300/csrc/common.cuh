@@ -123,11 +123,11 @@ struct Ctx {
     // 0: every contraction in FP64 (DGEMM).  1: contractions of >= fp32_min_flops
     // run as FP32-accurate GEMMs (BF16x9 emulation on the tensor cores), with
     // FP64 inputs rounded to FP32 and results accumulated into FP64.  2 (the
-    // mixed sigma): unbatched contractions of >= fp32_min_flops with both free
-    // dimensions above 8 run on the tcgen05 split-BF16 GEMM (two planes, FP32
-    // partial sums promoted every 16 K blocks, FP64 result); the others on the
-    // library's own kernels (own_gemm: FP32-accurate from fp32_min_flops, else
-    // FP64).
+    // mixed sigma): unbatched contractions of >= fp32_min_flops run on the tcgen05
+    // split-BF16 GEMM (two planes, FP32 partial sums promoted every 16 K blocks,
+    // FP64 result) unless a free dimension is <= 8 and the large operand is not a
+    // cached constant; the others on the library's own kernels (own_gemm:
+    // FP32-accurate from fp32_min_flops, else FP64).
     int gemm_mode = 0;
     double fp32_min_flops = 1e8;
     int emulation_ok = -1;  // -1 unknown, 1 BF16x9 emulation available, 0 plain FP32

@@ -42,12 +42,13 @@ def test_batch_small_vs_single_and_oracle(prec):
 
 
 def test_batch_uneven_sizes_concurrent():
-    """16 molecules of the batched IP-ADC(3) size distribution (nocc 8..30,
-    nvir 60..250, naux = 3.5 nmo), mixed precision: batched roots equal the
+    """The 64 molecules of the batched IP-ADC(3) workload (nocc 8..30, nvir
+    60..250, naux = 3.5 nmo, seeds 0..63), mixed precision, solved as one batch:
+    every system converges, and every fourth one's roots equal its
     one-at-a-time roots; the wall times are printed."""
     from paper_2012_06714_gb300 import ADC, ADCBatch
 
-    mols = batched_ip_molecules(16)
+    mols = batched_ip_molecules(64)
     systems = []
     for m in mols:
         s = make_system(m["nocc"], m["nvir"], m["naux"], seed=m["seed"])
@@ -58,20 +59,21 @@ def test_batch_uneven_sizes_concurrent():
     # of several of these systems sits at the edge of a dense band of 2h1p diagonal elements, where
     # the diagonal preconditioner is weak: a larger subspace (24 vectors per root, 4 kept per root at
     # a restart) converges them
-    opts = dict(res_tol=1e-4, max_iter=300, max_space_per_root=24, keep_per_root=4)
+    opts = dict(res_tol=1e-4, max_iter=300, max_space_per_root=24, keep_per_root=4, contractions=2)
     b = ADCBatch(systems, order=3, kind="ip", precision="bf16x3", **opts)
     e, p, st, status = b.davidson(6, tol=1e-6)
     b.close()
     t_batch = time.perf_counter() - t0
     assert (status == 0).all()
     t0 = time.perf_counter()
-    for k, (eps, B, o) in enumerate(systems):
+    for k in range(0, len(systems), 4):
+        eps, B, o = systems[k]
         g = ADC(eps, B, o, order=3, kind="ip", precision="bf16x3", **opts)
         e1, _, _, _ = g.davidson(6, tol=1e-6)
         g.close()
         assert np.abs(e[k] - e1).max() < 1e-9, k
     t_seq = time.perf_counter() - t0
-    print(f"16 IP-ADC(3) systems: batched {t_batch:.2f} s, one at a time {t_seq:.2f} s")
+    print(f"64 IP-ADC(3) systems batched {t_batch:.2f} s; 16 of them one at a time {t_seq:.2f} s")
 
 
 def test_batch_cuda_graphs_same_roots():
@@ -86,7 +88,7 @@ def test_batch_cuda_graphs_same_roots():
     for m in mols:
         s = make_system(m["nocc"], m["nvir"], m["naux"], seed=m["seed"])
         systems.append((s.eps, s.B, m["nocc"]))
-    opts = dict(res_tol=1e-4, max_iter=300, max_space_per_root=24, keep_per_root=4)
+    opts = dict(res_tol=1e-4, max_iter=300, max_space_per_root=24, keep_per_root=4, contractions=2)
     res = {}
     for graphs in (0, 1):
         torch.cuda.synchronize()
