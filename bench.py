@@ -245,6 +245,22 @@ def profiled_traffic():
     return d.get("dram_bytes_per_launch") if d.get("device_code_sha256") == kernel_source_hash() else None
 
 
+def fp64_plain_profile():
+    """The FP64-plain comparator at this workload, measured by `bench.py --fp64-plain` (its FP64 setup
+    alone takes minutes on GB300's FP64 units, so it is not rerun here) and committed under
+    profiles/; None if absent."""
+    p = os.path.join(ROOT, "profiles", "fp64_plain_ea3_o40_v400_Q1400.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    f = d.get("fp64", {})
+    return {"source": "profiles/fp64_plain_ea3_o40_v400_Q1400.json (bench.py --fp64-plain)",
+            "setup_s": f.get("setup_s"), "sigma_s_per_vector": f.get("sigma_s_per_vector"),
+            "time_to_roots_s_extrapolated": f.get("time_to_roots_s_extrapolated"),
+            "mixed_total_s_same_run": d.get("mixed", {}).get("total_s"),
+            "speedup_mixed_vs_fp64_same_run": d.get("speedup_mixed_vs_fp64")}
+
+
 def run_ladder_case(args):
     """Small profiling case of the ladder kernel (for ncu): EA-ADC(3) with
     nocc=4, nvir=400, naux=400 and 40 trial vectors, i.e. 160 ladder matrices
@@ -623,6 +639,7 @@ def run_ours(args):
                  "max_residual": st["max_residual"], "status": st["status"],
                  "refine_shift_eh": st["refine_shift"], "refine_seconds": st["refine_seconds"]}
         roots["fp64_vs_mixed"] = time_to_roots_medium(dev)
+        roots["fp64_plain_this_workload"] = fp64_plain_profile()
 
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

@@ -89,10 +89,12 @@ typedef struct {
     int contractions;        /* non-ladder contractions: -1 follow precision (default:*/
                              /* FP64 -> 0; BF16X3 -> 2 in sigma, 1 in setup and      */
                              /* refinement for EA, 0 in setup and refinement for IP), */
-                             /* 0 FP64 DGEMM, 1 FP32-accurate emulated                */
-                             /* GEMM, 2 as 1 but unbatched contractions that tile the */
-                             /* GPU run on the tensor-core split-BF16 GEMM of the     */
-                             /* ladder (setup and refinement use 1)                   */
+                             /* 0 FP64 DGEMM, 1 FP32-accurate emulated GEMM, 2 (sigma)*/
+                             /* unbatched contractions of >= 1e8 flop on the tensor-  */
+                             /* core split-BF16 GEMM of the ladder, unless a free     */
+                             /* dimension is <= 8 and the large operand is not a      */
+                             /* cached constant; the rest on the library's own FP64 / */
+                             /* FP32-accurate kernels (setup and refinement use 1)    */
     int refine;              /* BF16X3 only: converged roots are re-evaluated once    */
                              /* with the accurate ladder (FP32 partial sums promoted  */
                              /* every 64-deep K block) and Rayleigh-Ritz in their     */
@@ -116,11 +118,12 @@ typedef struct {
                              /* adc_get_tensor("M11") is unavailable.  0 (default)     */
     const char* tune_cache;  /* NULL (default): tile widths from the cost model; else a */
                              /* text file of measured tile choices: a tensor-core     */
-                             /* problem not yet in it (ladder GEMM2 tile width and    */
-                             /* auxiliary chunk, generic contraction tile width) is   */
-                             /* timed once on the device with each candidate, and the */
-                             /* fastest is kept (file rewritten; read at setup; one   */
-                             /* table per path, shared by the process's handles)      */
+                             /* problem not yet in it (the sigma ladder's GEMM2 tile  */
+                             /* width per B^Q shape, a generic contraction's tile     */
+                             /* width per shape) is timed once on the device with     */
+                             /* each candidate, and the fastest is kept (file         */
+                             /* rewritten; read at setup; one table per path, shared  */
+                             /* by the process's handles)                             */
     int cuda_graphs;         /* 1: in adc_davidson the sigma of a mixed-precision      */
                              /* handle runs as a CUDA graph per block size (captured  */
                              /* once on fixed buffers, replayed as one launch; for    */
