@@ -38,16 +38,17 @@ __global__ void permute_kernel(const double* __restrict__ in, double* __restrict
     }
 }
 
-template <typename Tin, typename Tout>
+template <typename I, typename Tin, typename Tout>
 __global__ void permute_cvt_kernel(const Tin* __restrict__ in, Tout* __restrict__ out, PermArgs a, long long total,
                                    double alpha, double beta) {
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
-        long long r = idx, off = 0;
+        I r = (I)idx, off = 0;
         for (int j = a.nd - 1; j >= 0; --j) {
-            long long cj = r % a.dout[j];
-            r /= a.dout[j];
-            off += cj * a.sin[j];
+            const I d = (I)a.dout[j];
+            const I q = r / d;
+            off += (r - q * d) * (I)a.sin[j];
+            r = q;
         }
         double v = alpha * (double)in[off];
         out[idx] = (Tout)((beta == 0.0) ? v : v + beta * (double)out[idx]);
@@ -65,8 +66,8 @@ __global__ void fill_kernel(long long n, double v, double* __restrict__ y) {
 }
 
 // out[p][r*Kp + k] (two BF16 planes) from the permuted input, zero for k >= K
-template <typename I>
-__global__ void permute_split_kernel(const double* __restrict__ in, __nv_bfloat16* __restrict__ o0,
+template <typename I, typename Tin>
+__global__ void permute_split_kernel(const Tin* __restrict__ in, __nv_bfloat16* __restrict__ o0,
                                      __nv_bfloat16* __restrict__ o1, PermArgs a, long long rows, long long K, long long Kp) {
     const long long total = rows * Kp;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -81,7 +82,7 @@ __global__ void permute_split_kernel(const double* __restrict__ in, __nv_bfloat1
                 off += (lin - q * d) * (I)a.sin[j];
                 lin = q;
             }
-            x = in[off];
+            x = (double)in[off];
         }
         const __nv_bfloat16 h = __double2bfloat16(x);
         o0[idx] = h;
@@ -412,7 +413,7 @@ void permute(Ctx& c, const double* in, const Shape& s, const int* perm, double* 
         total *= a.dout[j];
     }
     if (total == 0) return;
-    if (total < (1LL << 31))
+    if (total <= 0xffffffffLL)  // every offset is below total
         permute_kernel<unsigned><<<grid_for(total), 256, 0, c.stream>>>(in, out, a, total, alpha, beta);
     else
         permute_kernel<long long><<<grid_for(total), 256, 0, c.stream>>>(in, out, a, total, alpha, beta);
@@ -443,25 +444,50 @@ static void permute_cvt(Ctx& c, const Tin* in, const Shape& s, const int* perm, 
     long long total;
     PermArgs a = perm_args(s, perm, total);
     if (total == 0) return;
-    permute_cvt_kernel<Tin, Tout><<<grid_for(total), 256, 0, c.stream>>>(in, out, a, total, alpha, beta);
+    if (total <= 0xffffffffLL)
+        permute_cvt_kernel<unsigned, Tin, Tout><<<grid_for(total), 256, 0, c.stream>>>(in, out, a, total, alpha, beta);
+    else
+        permute_cvt_kernel<long long, Tin, Tout><<<grid_for(total), 256, 0, c.stream>>>(in, out, a, total, alpha, beta);
+    ++c.kernels;
+    ADC_CUDA(cudaGetLastError());
+}
+
+template <typename Tin>
+static void split_planes_t(Ctx& c, const Tin* in, const PermArgs& a, long long rows, long long K, long long Kp,
+                           void* const* out) {
+    // 32-bit coordinates when the output index fits (every input offset is below rows * K)
+    if (rows * Kp <= 0xffffffffLL)
+        permute_split_kernel<unsigned, Tin><<<grid_for(rows * Kp), 256, 0, c.stream>>>(
+            in, (__nv_bfloat16*)out[0], (__nv_bfloat16*)out[1], a, rows, K, Kp);
+    else
+        permute_split_kernel<long long, Tin><<<grid_for(rows * Kp), 256, 0, c.stream>>>(
+            in, (__nv_bfloat16*)out[0], (__nv_bfloat16*)out[1], a, rows, K, Kp);
     ++c.kernels;
     ADC_CUDA(cudaGetLastError());
 }
 
 void split_planes(Ctx& c, const double* in, const Shape& s, const int* perm, long long rows, long long K, long long Kp,
-                  void* const* out) {
+                  void* const* out, bool in32) {
     long long total;
     PermArgs a = perm_args(s, perm, total);
     if (total != rows * K) throw Error(-1, "split_planes: shape mismatch");
     if (rows * Kp == 0) return;
-    if (rows * Kp < (1LL << 31))
-        permute_split_kernel<unsigned><<<grid_for(rows * Kp), 256, 0, c.stream>>>(
-            in, (__nv_bfloat16*)out[0], (__nv_bfloat16*)out[1], a, rows, K, Kp);
+    if (in32)
+        split_planes_t(c, (const float*)in, a, rows, K, Kp, out);
     else
-        permute_split_kernel<long long><<<grid_for(rows * Kp), 256, 0, c.stream>>>(
-            in, (__nv_bfloat16*)out[0], (__nv_bfloat16*)out[1], a, rows, K, Kp);
-    ++c.kernels;
-    ADC_CUDA(cudaGetLastError());
+        split_planes_t(c, in, a, rows, K, Kp, out);
+}
+
+void permute_any(Ctx& c, const void* in, bool in32, const Shape& s, const int* perm, void* out, bool out32,
+                 double alpha, double beta) {
+    if (!in32 && !out32)
+        permute(c, (const double*)in, s, perm, (double*)out, alpha, beta);
+    else if (in32 && out32)
+        permute_cvt(c, (const float*)in, s, perm, (float*)out, alpha, beta);
+    else if (in32)
+        permute_cvt(c, (const float*)in, s, perm, (double*)out, alpha, beta);
+    else
+        permute_cvt(c, (const double*)in, s, perm, (float*)out, alpha, beta);
 }
 
 void axpby(Ctx& c, long long n, double alpha, const double* x, double beta, double* y) {
@@ -542,9 +568,10 @@ Spec parse(const char* spec) {
 bool has(const std::string& s, char x) { return s.find(x) != std::string::npos; }
 
 // permute src (letters ls, dims) into the letter order lt; returns pointer (src if identity)
+// (an FP32 operand is always converted into an FP64 copy)
 const double* to_order(Ctx& c, const double* src, const std::string& ls, const std::map<char, long long>& dim,
-                       const std::string& lt) {
-    if (ls == lt) return src;
+                       const std::string& lt, bool f32 = false) {
+    if (ls == lt && !f32) return src;
     Shape sh;
     sh.nd = (int)ls.size();
     long long n = 1;
@@ -555,7 +582,7 @@ const double* to_order(Ctx& c, const double* src, const std::string& ls, const s
     int perm[kMaxDim];
     for (int j = 0; j < sh.nd; ++j) perm[j] = (int)ls.find(lt[j]);
     double* dst = c.arena.dalloc(n);
-    permute(c, src, sh, perm, dst, 1.0, 0.0);
+    permute_any(c, src, f32, sh, perm, dst, false, 1.0, 0.0);
     return dst;
 }
 
@@ -566,15 +593,17 @@ const double* to_order(Ctx& c, const double* src, const std::string& ls, const s
 // permuted and accumulated into the FP64 output.
 static void einsum_fp32(Ctx& c, const std::string& la, const std::string& lb, const std::string& lc,
                         std::map<char, long long>& dim, const std::string& batch, const std::string& fa,
-                        const std::string& fb, const std::string& con, double alpha, const double* Ap, const double* Bp,
-                        double beta, double* C, bool constA, bool constB) {
+                        const std::string& fb, const std::string& con, double alpha, const T& A, const T& B,
+                        double beta, void* C, bool c32) {
     auto prod = [&](const std::string& l) {
         long long p = 1;
         for (char x : l) p *= dim[x];
         return p;
     };
     long long nb = prod(batch), M = prod(fa), N = prod(fb), K = prod(con);
-    auto conv = [&](const double* src, const std::string& ls, const std::string& lt, bool constant) {
+    auto conv = [&](const T& X, const std::string& ls, const std::string& lt) {
+        // an FP32 operand already in GEMM order is used in place
+        if (X.f32 && ls == lt) return (const float*)X.p;
         Shape sh;
         sh.nd = (int)ls.size();
         long long n = 1;
@@ -592,22 +621,25 @@ static void einsum_fp32(Ctx& c, const std::string& la, const std::string& lb, co
             key += ',';
         }
         float* dst;
-        if (constant) {
-            auto it = c.f32cache.find({src, key});
+        if (X.constant && (size_t)n * sizeof(float) <= c.cache_max_bytes) {
+            auto it = c.f32cache.find({X.p, key});
             if (it != c.f32cache.end()) return (const float*)it->second;
             if (c.capturing) throw Error(-3, "operand cache miss during stream capture");
             dst = (float*)dev_alloc(n * sizeof(float), c.stream);
-            c.f32cache[{src, key}] = dst;
+            c.f32cache[{X.p, key}] = dst;
         } else {
             dst = (float*)c.arena.alloc(n * sizeof(float));
         }
-        permute_cvt<double, float>(c, src, sh, perm, dst, 1.0, 0.0);
+        permute_any(c, X.p, X.f32, sh, perm, dst, true, 1.0, 0.0);
         return (const float*)dst;
     };
-    const float* A32 = conv(Ap, la, batch + fa + con, constA);
-    const float* B32 = conv(Bp, lb, batch + con + fb, constB);
-    float* T32 = (float*)c.arena.alloc(nb * M * N * sizeof(float));
-    const float one = 1.0f, zero = 0.0f;
+    const float* A32 = conv(A, la, batch + fa + con);
+    const float* B32 = conv(B, lb, batch + con + fb);
+    const std::string tord = batch + fa + fb;
+    // an FP32 output in the GEMM's order is written by the GEMM itself (C = alpha AB + beta C)
+    const bool direct = c32 && tord == lc;
+    float* T32 = direct ? (float*)C : (float*)c.arena.alloc(nb * M * N * sizeof(float));
+    const float one = direct ? (float)alpha : 1.0f, zero = direct ? (float)beta : 0.0f;
     // row-major T[M][N] = A[M][K] B[K][N]  <=>  column-major T^T = B^T A^T
     auto run = [&](cublasComputeType_t ct) {
         return cublasGemmStridedBatchedEx(c.blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)N, (int)M, (int)K, &one, B32, CUDA_R_32F,
@@ -627,13 +659,13 @@ static void einsum_fp32(Ctx& c, const std::string& la, const std::string& lb, co
     } else {
         ADC_BLAS(run(CUBLAS_COMPUTE_32F));
     }
-    std::string tord = batch + fa + fb;
+    if (direct) return;
     Shape sh;
     sh.nd = (int)tord.size();
     for (int j = 0; j < sh.nd; ++j) sh.d[j] = dim[tord[j]];
     int perm[kMaxDim];
     for (int j = 0; j < sh.nd; ++j) perm[j] = (int)tord.find(lc[j]);
-    permute_cvt<float, double>(c, T32, sh, perm, C, alpha, beta);
+    permute_any(c, T32, true, sh, perm, C, c32, alpha, beta);
 }
 
 // Tensor-core contraction (gemm_mode 2): operands permuted into K-major GEMM
@@ -642,14 +674,14 @@ static void einsum_fp32(Ctx& c, const std::string& la, const std::string& lb, co
 // accumulated into the output.
 static void einsum_tc(Ctx& c, const std::string& la, const std::string& lb, const std::string& lc,
                       std::map<char, long long>& dim, const std::string& fa, const std::string& fb, const std::string& con,
-                      double alpha, const double* Ap, const double* Bp, double beta, double* C, bool constA, bool constB) {
+                      double alpha, const T& A, const T& B, double beta, void* C, bool c32) {
     auto prod = [&](const std::string& l) {
         long long p = 1;
         for (char x : l) p *= dim[x];
         return p;
     };
     const long long M = prod(fa), N = prod(fb), K = prod(con), Kp = (K + 7) / 8 * 8;
-    auto planes_of = [&](const double* src, const std::string& ls, const std::string& lt, long long rows, bool constant) {
+    auto planes_of = [&](const T& X, const std::string& ls, const std::string& lt, long long rows) {
         Shape sh;
         sh.nd = (int)ls.size();
         for (int j = 0; j < sh.nd; ++j) sh.d[j] = dim.at(ls[j]);
@@ -664,21 +696,21 @@ static void einsum_tc(Ctx& c, const std::string& la, const std::string& lb, cons
         }
         key += std::to_string(K);
         void* base = nullptr;
-        if (constant) {
-            auto it = c.bf16cache.find({src, key});
+        if (X.constant && (size_t)(2 * rows * Kp * 2) <= c.cache_max_bytes) {
+            auto it = c.bf16cache.find({X.p, key});
             if (it != c.bf16cache.end()) return it->second;
             if (c.capturing) throw Error(-3, "operand cache miss during stream capture");
             base = dev_alloc(2 * rows * Kp * 2, c.stream);
-            c.bf16cache[{src, key}] = base;
+            c.bf16cache[{X.p, key}] = base;
         } else {
             base = c.arena.alloc(2 * rows * Kp * 2);
         }
         void* out[2] = {base, (char*)base + rows * Kp * 2};
-        split_planes(c, src, sh, perm, rows, K, Kp, out);
+        split_planes(c, X.p, sh, perm, rows, K, Kp, out, X.f32);
         return base;
     };
-    void* pa = planes_of(Ap, la, fa + con, M, constA);
-    void* pb = planes_of(Bp, lb, fb + con, N, constB);
+    void* pa = planes_of(A, la, fa + con, M);
+    void* pb = planes_of(B, lb, fb + con, N);
     if (!c.d_err) {
         if (c.capturing) throw Error(-3, "error flag allocation during stream capture");
         c.d_err = (int*)dev_alloc(sizeof(int), c.stream);
@@ -694,11 +726,11 @@ static void einsum_tc(Ctx& c, const std::string& la, const std::string& lb, cons
     for (int j = 0; j < sh.nd; ++j) sh.d[j] = dim[tord[j]];
     int perm[kMaxDim];
     for (int j = 0; j < sh.nd; ++j) perm[j] = (int)tord.find(lc[j]);
-    permute(c, T, sh, perm, C, alpha, beta);
+    permute_any(c, T, false, sh, perm, C, c32, alpha, beta);
 }
 
-void einsum(Ctx& c, const char* specstr, double alpha, const T& A, const T& B, double beta, double* C,
-            const std::vector<long long>& cdims) {
+static void einsum_core(Ctx& c, const char* specstr, double alpha, const T& A, const T& B, double beta, void* C, bool c32,
+                        const std::vector<long long>& cdims) {
     Spec sp = parse(specstr);
     if (sp.a.size() != A.dims.size() || sp.b.size() != B.dims.size() || sp.c.size() != cdims.size())
         throw Error(-1, std::string("einsum: rank mismatch in ") + specstr);
@@ -748,13 +780,13 @@ void einsum(Ctx& c, const char* specstr, double alpha, const T& A, const T& B, d
         const bool skinny = std::min(M, N) <= 8;
         const bool big_const = M <= N ? B.constant : A.constant;
         if (big && tc_gemm_fits(M, N, K) && (!skinny || big_const)) {
-            einsum_tc(c, sp.a, sp.b, sp.c, dim, fa, fb, con, alpha, A.p, B.p, beta, C, A.constant, B.constant);
+            einsum_tc(c, sp.a, sp.b, sp.c, dim, fa, fb, con, alpha, A, B, beta, C, c32);
         } else {
-            const double* Ap = to_order(c, A.p, sp.a, dim, fa + con);
-            const double* Bp = to_order(c, B.p, sp.b, dim, con + fb);
+            const double* Ap = to_order(c, A.p, sp.a, dim, fa + con, A.f32);
+            const double* Bp = to_order(c, B.p, sp.b, dim, con + fb, B.f32);
             const std::string tord = fa + fb;
-            if (tord == sp.c) {
-                own_gemm(c, M, N, K, alpha, Ap, K, Bp, N, beta, C, N, big);
+            if (tord == sp.c && !c32) {
+                own_gemm(c, M, N, K, alpha, Ap, K, Bp, N, beta, (double*)C, N, big);
             } else {
                 double* Tm = c.arena.dalloc((size_t)(M * N));
                 own_gemm(c, M, N, K, 1.0, Ap, K, Bp, N, 0.0, Tm, N, big);
@@ -763,22 +795,22 @@ void einsum(Ctx& c, const char* specstr, double alpha, const T& A, const T& B, d
                 for (int j = 0; j < sh.nd; ++j) sh.d[j] = dim[tord[j]];
                 int perm[kMaxDim];
                 for (int j = 0; j < sh.nd; ++j) perm[j] = (int)tord.find(sp.c[j]);
-                permute(c, Tm, sh, perm, C, alpha, beta);
+                permute_any(c, Tm, false, sh, perm, C, c32, alpha, beta);
             }
         }
         c.arena.release(mk);
         return;
     }
     if (c.gemm_mode >= 1 && 2.0 * nb * M * N * K >= c.fp32_min_flops) {
-        einsum_fp32(c, sp.a, sp.b, sp.c, dim, batch, fa, fb, con, alpha, A.p, B.p, beta, C, A.constant, B.constant);
+        einsum_fp32(c, sp.a, sp.b, sp.c, dim, batch, fa, fb, con, alpha, A, B, beta, C, c32);
         c.arena.release(mk);
         return;
     }
-    const double* Ap = to_order(c, A.p, sp.a, dim, batch + fa + con);
-    const double* Bp = to_order(c, B.p, sp.b, dim, batch + con + fb);
+    const double* Ap = to_order(c, A.p, sp.a, dim, batch + fa + con, A.f32);
+    const double* Bp = to_order(c, B.p, sp.b, dim, batch + con + fb, B.f32);
     std::string tord = batch + fa + fb;
-    if (tord == sp.c) {
-        gemm(c, false, false, M, N, K, alpha, Ap, K, M * K, Bp, N, K * N, beta, C, N, M * N, nb);
+    if (tord == sp.c && !c32) {
+        gemm(c, false, false, M, N, K, alpha, Ap, K, M * K, Bp, N, K * N, beta, (double*)C, N, M * N, nb);
     } else {
         double* Tm = c.arena.dalloc((size_t)(nb * M * N));
         gemm(c, false, false, M, N, K, 1.0, Ap, K, M * K, Bp, N, K * N, 0.0, Tm, N, M * N, nb);
@@ -787,9 +819,19 @@ void einsum(Ctx& c, const char* specstr, double alpha, const T& A, const T& B, d
         for (int j = 0; j < sh.nd; ++j) sh.d[j] = dim[tord[j]];
         int perm[kMaxDim];
         for (int j = 0; j < sh.nd; ++j) perm[j] = (int)tord.find(sp.c[j]);
-        permute(c, Tm, sh, perm, C, alpha, beta);
+        permute_any(c, Tm, false, sh, perm, C, c32, alpha, beta);
     }
     c.arena.release(mk);
+}
+
+void einsum(Ctx& c, const char* spec, double alpha, const T& A, const T& B, double beta, double* C,
+            const std::vector<long long>& cdims) {
+    einsum_core(c, spec, alpha, A, B, beta, C, false, cdims);
+}
+
+void einsum(Ctx& c, const char* spec, double alpha, const T& A, const T& B, double beta, float* C,
+            const std::vector<long long>& cdims) {
+    einsum_core(c, spec, alpha, A, B, beta, C, true, cdims);
 }
 
 }  // namespace adc

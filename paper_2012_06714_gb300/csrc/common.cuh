@@ -44,18 +44,33 @@ class Arena {
     cudaStream_t stream = nullptr;
     bool frozen = false;  // set while a stream capture records: growing would allocate inside the graph
     ~Arena() { free_all(); }
+    // requests of at least big_bytes (0: never) get a block of their own, freed (stream-
+    // ordered) by the release() of the enclosing mark: scratch of very different sizes at
+    // the same stack depth then cannot fragment the kept blocks
+    size_t big_bytes = 0;
     struct Mark {
-        size_t block, top;
+        size_t block, top, nbig;
     };
-    Mark mark() const { return {cur_, blocks_.empty() ? 0 : tops_[cur_]}; }
+    Mark mark() const { return {cur_, blocks_.empty() ? 0 : tops_[cur_], big_.size()}; }
     void release(Mark m) {
         for (size_t b = m.block + 1; b < tops_.size(); ++b) tops_[b] = 0;
         cur_ = m.block;
         if (!tops_.empty()) tops_[cur_] = m.top;
+        while (big_.size() > m.nbig) {
+            cudaFreeAsync(big_.back(), stream);
+            big_.pop_back();
+        }
     }
     void* alloc(size_t bytes) {
         bytes = (bytes + 255) & ~size_t(255);
         if (bytes == 0) bytes = 256;
+        if (big_bytes && bytes >= big_bytes) {
+            if (frozen) throw Error(-3, "arena: growth during stream capture");
+            void* p = nullptr;
+            ADC_CUDA(cudaMallocAsync(&p, bytes, stream));
+            big_.push_back(p);
+            return p;
+        }
         while (cur_ < blocks_.size()) {
             if (tops_[cur_] + bytes <= caps_[cur_]) {
                 void* p = (char*)blocks_[cur_] + tops_[cur_];
@@ -81,6 +96,8 @@ class Arena {
     double* dalloc(size_t n) { return (double*)alloc(n * sizeof(double)); }
     // release every block (stream-ordered on `stream` when async, else with cudaFree)
     void free_all(bool async = false) {
+        for (void* p : big_) blocks_.push_back(p);
+        big_.clear();
         for (void* p : blocks_) {
             if (async)
                 cudaFreeAsync(p, stream);
@@ -99,7 +116,7 @@ class Arena {
     }
 
    private:
-    std::vector<void*> blocks_;
+    std::vector<void*> blocks_, big_;
     std::vector<size_t> caps_, tops_;
     size_t cur_ = 0;
 };
@@ -142,6 +159,9 @@ struct Ctx {
     std::map<std::pair<const void*, std::string>, float*> f32cache;
     // split BF16 planes (K-major GEMM operand order) of operands marked constant
     std::map<std::pair<const void*, std::string>, void*> bf16cache;
+    // constant operands are cached in these forms only if the copy is at most this size
+    // (larger ones are converted per call into scratch)
+    size_t cache_max_bytes = ~size_t(0);
     int* d_err = nullptr;  // device flag raised by a bounded wait that gave up (tensor-core GEMMs)
     void* tuner = nullptr;  // TuneCache of the tile autotuner (ladder_tc.cuh), or NULL: cost-model tiles
     // a CUDA-graph capture of sigma is recording on `stream`: no host synchronisation, no
@@ -183,16 +203,24 @@ struct T {
     const double* p;
     std::vector<long long> dims;
     bool constant = false;  // contents never change while the handle lives (FP32 copy may be cached)
+    bool f32 = false;       // p points to FP32 values (read as such; FP64 operand paths convert)
 };
 // C[lc] = beta * C + alpha * sum A[la] B[lb] ; spec "la,lb->lc" with single-letter indices.
 void einsum(Ctx& c, const char* spec, double alpha, const T& A, const T& B, double beta, double* C,
             const std::vector<long long>& cdims);
+// the same with an FP32 output (the contraction's arithmetic is unchanged; the result and
+// beta * C are formed in FP64, or FP32 where the GEMM writes the output itself, and rounded once)
+void einsum(Ctx& c, const char* spec, double alpha, const T& A, const T& B, double beta, float* C,
+            const std::vector<long long>& cdims);
+// out = alpha * permute(in) + beta * out between FP64 / FP32 arrays (in32 / out32: FP32)
+void permute_any(Ctx& c, const void* in, bool in32, const Shape& s, const int* perm, void* out, bool out32,
+                 double alpha, double beta);
 
 // Permute `in` (shape s, output axis j = input axis perm[j]) into row-major
 // [rows][K] order and split each value x into BF16 planes x = p0 + p1 (two
 // planes), written K-major as out[p][r * Kp + k] with zeros for K <= k < Kp.
 void split_planes(Ctx& c, const double* in, const Shape& s, const int* perm, long long rows, long long K, long long Kp,
-                  void* const* out);
+                  void* const* out, bool in32 = false);
 
 // The library's own kernels for small and skinny contractions (row-major A [M][K],
 // B [K][N], C [M][N] with leading dimensions): C = alpha A B + beta C.  M <= 8 or
