@@ -341,6 +341,132 @@ def run_ladder_large(args):
     return 0
 
 
+class MemorySampler:
+    """Peak device memory in use (nvidia-smi, every 200 ms) while a phase runs."""
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.gpu = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", "--query-gpu=memory.used,memory.total",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        used, total = [], []
+        for r in self.f.read().strip().splitlines():
+            try:
+                a, b = (float(x) for x in r.split(","))
+            except ValueError:
+                continue
+            used.append(a)
+            total.append(b)
+        if not used:
+            return None
+        return {"peak_used_mib": max(used), "total_mib": max(total), "samples": len(used)}
+
+
+def run_large(args):
+    """The 1028-MO workload end to end: EA-ADC(3), nocc=68, nvir=960, naux=3000 (B^Q 25 GB in
+    FP64), mixed precision in the lean layout (the o^2 v^2 tensors are 34 GB each in FP64),
+    4 roots with a subspace of up to 16 vectors per root.  Reports setup time, the sigma step
+    of 4 trial vectors (ladder TFLOP/s timed live with CUDA events), the S-symmetry of M at
+    this size (x0^T S M x1 = x1^T S M x0, a parity property that holds at any size), the time
+    to 4 roots and the peak device memory."""
+    import torch
+
+    from adc_inputs import make_system
+    from paper_2012_06714_gb300 import ADC
+
+    torch.cuda.set_device(0)
+    o, v, naux, nvec = 68, 960, 3000, 4
+    need = 8.0 * naux * (o + v) ** 2  # the host copy of B^Q
+    try:
+        avail = float([ln.split()[1] for ln in open("/proc/meminfo") if ln.startswith("MemAvailable")][0]) * 1024
+    except (OSError, IndexError, ValueError):
+        avail = 0.0
+    if avail < 2.0 * need:
+        print(json.dumps({"case": "1028-MO workload", "unavailable": f"host memory {avail / 1e9:.0f} GB available, "
+                                                                     f"{2 * need / 1e9:.0f} GB wanted"}))
+        return 1
+    t0 = time.perf_counter()
+    s = make_system(o, v, naux, seed=0)
+    gen_s = time.perf_counter() - t0
+    mem = MemorySampler(torch.cuda.current_device())
+    mem.start()
+    t0 = time.perf_counter()
+    g = ADC(s.eps, s.B, o, order=3, kind="ea", precision="bf16x3", lean=1, res_tol=1e-4, max_space_per_root=16,
+            keep_per_root=4, nguess_extra=0, max_iter=200, tune_cache=args.tune_cache)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    del s
+    mp = g.mp_energy()
+    out = {"case": "EA-ADC(3) nocc=68 nvir=960 naux=3000 (1028 MOs), bf16x3, lean layout", "setup_s": setup_s,
+           "input_generation_s": gen_s, "dim": g.dim, "mp_energy_eh": list(mp)}
+    gen = torch.Generator(device="cuda").manual_seed(1)
+    X = torch.randn((nvec, g.dim), device="cuda", dtype=torch.float64, generator=gen) / np.sqrt(g.dim)
+    S = torch.empty_like(X)
+    g.sigma(X, out=S)
+    torch.cuda.synchronize()
+    # S-symmetry: (S x)_1p = x_1p, (S x)_2p1h = 2 Y - Y(ab swap)
+
+    def apply_S(x):
+        y2 = x[v:].view(o, v, v)
+        return torch.cat([x[:v], (2.0 * y2 - y2.transpose(1, 2)).reshape(-1)])
+
+    a = float(X[0] @ apply_S(S[1]))
+    b = float(X[1] @ apply_S(S[0]))
+    scale = float(np.sqrt(abs(float(X[0] @ apply_S(S[0]))) * abs(float(X[1] @ apply_S(S[1])))))
+    out["s_symmetry_rel"] = abs(a - b) / scale
+    out["sigma_finite"] = bool(torch.isfinite(S).all())
+    g.kernel_timing(True)
+    steps = max(1, args.steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        g.sigma(X, out=S)
+    e1.record()
+    torch.cuda.synchronize()
+    kt = g.kernel_timing(False)
+    ms = e0.elapsed_time(e1) / steps
+    bf16_peak, bf16_burst, _, src = peaks()
+    lt = kt["ladder_algo_flops"] / (kt["ladder_ms"] / 1e3) / 1e12
+    out["sigma"] = {"ms_per_step": ms, "tflops": ladder_flops(o, v, naux, nvec) / (ms / 1e3) / 1e12,
+                    "ladder_tflops": lt, "ladder_frac_of_sustained_bf16_over_3": lt / (bf16_peak / 3.0),
+                    "ladder_ms_per_step": kt["ladder_ms"] / steps, "peak_source": src,
+                    "launches_per_step": kt["kernels"] / steps}
+    del X, S
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    e, p, _, st = g.davidson(4, tol=1e-6)
+    out["time_to_roots"] = {"seconds": time.perf_counter() - t0, "setup_seconds": setup_s,
+                            "subspace": "<= 16 vectors per root, restart onto 4 per root; |dE| <= 1e-6 Eh, "
+                                        "residual 1e-4, then one accurate-operator Rayleigh-Ritz step",
+                            "energies_eh": [float(x) for x in e], "spectroscopic_factors": [float(x) for x in p],
+                            "iterations": st["iterations"], "sigma_vectors": st["sigma_vectors"],
+                            "sigma_seconds": st["sigma_seconds"], "max_residual": st["max_residual"],
+                            "status": st["status"], "refine_shift_eh": st["refine_shift"],
+                            "refine_seconds": st["refine_seconds"]}
+    out["memory"] = mem.stop()
+    g.close()
+    print(json.dumps(out))
+    return 0
+
+
 def run_davidson_case(args):
     """Small profiling case of the Davidson subspace kernels (for ncu):
     EA-ADC(3) mixed precision with nocc=24, nvir=240, naux=500 (1.38e6-element
@@ -673,6 +799,8 @@ def main():
     ap.add_argument("--batched", action="store_true", help="batched IP-ADC(3) workload (64 molecules)")
     ap.add_argument("--ladder-large", action="store_true",
                     help="ladder kernel at the per-launch shapes of the 1028-MO workload")
+    ap.add_argument("--large", action="store_true",
+                    help="the 1028-MO workload end to end (setup, sigma, time to 4 roots) in the lean layout")
     ap.add_argument("--nmol", type=int, default=64)
     ap.add_argument("--tune-cache", default=None,
                     help="tile autotuner cache file (tiles measured in the first warm-up step)")
@@ -687,6 +815,8 @@ def main():
         return run_batched(args)
     if args.ladder_large:
         return run_ladder_large(args)
+    if args.large:
+        return run_large(args)
     if args.ladder_case:
         return run_ladder_case(args)
     if args.impl == "reference":

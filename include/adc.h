@@ -130,6 +130,18 @@ typedef struct {
                              /* small systems, where launches dominate; needs a      */
                              /* stream of the handle's own: adc_setup_batch, or      */
                              /* adc_set_stream); 0 (default)                          */
+    int lean;                /* memory layout of a closed-shell EA handle in BF16X3    */
+                             /* precision: 1 lean -- the o^2 v^2 integrals and         */
+                             /* amplitudes of sigma held in FP32 (every contraction   */
+                             /* reading them is split-BF16 or FP32-accurate, so the   */
+                             /* results are those of the plain layout up to rounding),*/
+                             /* no tau / ring2 tensors (their contractions expanded),  */
+                             /* operand copies made per call rather than cached,       */
+                             /* setup's o^2 v^2 temporaries in FP32; about a third of  */
+                             /* the plain layout's memory (e.g. nocc=68, nvir=960,     */
+                             /* naux=3000 fits one GPU); needs m11_on_the_fly = 0.     */
+                             /* 0 plain; -1 (default) lean when the plain layout's     */
+                             /* setup would not fit the free device memory            */
 } adc_options;
 
 /* Fill *opt with the defaults listed above.  Returns ADC_OK or ADC_ERR_ARG (NULL). */

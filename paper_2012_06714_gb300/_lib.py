@@ -57,6 +57,7 @@ class Options(ctypes.Structure):
         ("m11_on_the_fly", ctypes.c_int),
         ("tune_cache", ctypes.c_char_p),
         ("cuda_graphs", ctypes.c_int),
+        ("lean", ctypes.c_int),
     ]
 
 
@@ -149,7 +150,7 @@ class ADC:
 
     def __init__(self, eps, B, nocc, order=3, kind="ea", precision="fp64", max_space_per_root=8, max_iter=100,
                  nguess_extra=2, res_tol=0.0, aux_chunk=0, keep_per_root=2, contractions=-1, refine=1,
-                 transition_order=0, refine_res_tol=0.0, m11_on_the_fly=0, tune_cache=None, cuda_graphs=0):
+                 transition_order=0, refine_res_tol=0.0, m11_on_the_fly=0, tune_cache=None, cuda_graphs=0, lean=-1):
         lib = load_library()
         self._lib = lib
         opt = Options()
@@ -168,6 +169,7 @@ class ADC:
         opt.m11_on_the_fly = m11_on_the_fly
         opt.tune_cache = None if tune_cache is None else os.fsencode(tune_cache)
         opt.cuda_graphs = cuda_graphs
+        opt.lean = lean
         self._solver = dict(max_space_per_root=max_space_per_root, max_iter=max_iter, nguess_extra=nguess_extra,
                             res_tol=res_tol, keep_per_root=keep_per_root, refine=refine,
                             transition_order=transition_order, refine_res_tol=refine_res_tol,

@@ -70,6 +70,18 @@ struct adc_handle {
                              // unless the 1p-1p block is applied on the fly)
     // 1p-1p / 1h-1h block applied on the fly (m11_on_the_fly): small intermediates of step 2
     double *otf_g = nullptr, *otf_Hq = nullptr, *otf_gz = nullptr, *otf_Zm = nullptr, *otf_U = nullptr;
+    // memory-lean layout (option lean; closed-shell EA, mixed precision): the o^2 v^2 constants
+    // held in FP32 (f_*; every contraction that reads them is split-BF16 or FP32-accurate, so
+    // FP32 storage loses nothing), no tau or ring2 tensor (contractions with them expanded into
+    // ones with t and the integrals), operand copies made per call instead of cached, setup's
+    // o^2 v^2 temporaries in FP32, and the root-independent parts of the transition moments
+    // made at setup
+    bool lean = false;
+    float *f_t = nullptr, *f_t2 = nullptr, *f_ovov = nullptr, *f_oovv = nullptr;
+    float* f_tau = nullptr;  // lean: tau in FP32, only while setup needs it
+    // lean: [2][max(o,v)^2] one-particle block and [2][o][v] singles of the transition
+    // moments (index: third-order terms included)
+    double *spec_Tpp = nullptr, *spec_t1 = nullptr;
     std::vector<void*> owned;
     // sigma captured as CUDA graphs (cuda_graphs): one per block size, on fixed input / output buffers
     struct SigmaGraph {
@@ -93,6 +105,19 @@ struct adc_handle {
         void* p = dev_alloc(std::max<size_t>(n, 1) * sizeof(double), ctx.stream);
         owned.push_back(p);
         return (double*)p;
+    }
+    float* fmalloc(size_t n) {
+        void* p = dev_alloc(std::max<size_t>(n, 1) * sizeof(float), ctx.stream);
+        owned.push_back(p);
+        return (float*)p;
+    }
+    // release one owned buffer before the handle ends (stream-ordered)
+    void dfree(void* p) {
+        if (!p) return;
+        auto it = std::find(owned.begin(), owned.end(), p);
+        if (it == owned.end()) return;
+        owned.erase(it);
+        cudaFreeAsync(p, ctx.stream);
     }
     ~adc_handle() {
         if (ctx.stream) cudaStreamSynchronize(ctx.stream);
@@ -287,8 +312,76 @@ T tn(const double* p, std::initializer_list<long long> d) { return T{p, std::vec
 T tn(const double* p, const std::vector<long long>& d) { return T{p, d, false}; }
 // handle-owned tensor that never changes after setup (its FP32 operand copy may be cached)
 T tc(const double* p, std::initializer_list<long long> d) { return T{p, std::vector<long long>(d), true}; }
+// handle-owned FP32 tensor (constant)
+T tf(const float* p, std::initializer_list<long long> d) { return T{(const double*)p, std::vector<long long>(d), true, true}; }
+
+// An o^2 v^2-sized scratch tensor of setup: FP32 on a lean handle, else FP64.
+struct Buf {
+    void* p = nullptr;
+    bool f32 = false;
+    T as(std::initializer_list<long long> d) const { return T{(const double*)p, std::vector<long long>(d), false, f32}; }
+};
+Buf scratch(Arena& a, long long n, bool f32) {
+    Buf b;
+    b.f32 = f32;
+    b.p = f32 ? a.alloc((size_t)n * sizeof(float)) : (void*)a.dalloc((size_t)n);
+    return b;
+}
+void ein(Ctx& c, const char* spec, double alpha, const T& A, const T& B, double beta, const Buf& C,
+         const std::vector<long long>& d) {
+    if (C.f32)
+        einsum(c, spec, alpha, A, B, beta, (float*)C.p, d);
+    else
+        einsum(c, spec, alpha, A, B, beta, (double*)C.p, d);
+}
+// C = alpha * permute(X) + beta * C (output axis j = input axis perm[j])
+void perm_into(Ctx& c, const T& X, std::initializer_list<int> perm, const Buf& C, double alpha, double beta) {
+    Shape s{(int)X.dims.size(), {}};
+    for (int j = 0; j < s.nd; ++j) s.d[j] = X.dims[j];
+    std::vector<int> p(perm);
+    permute_any(c, X.p, X.f32, s, p.data(), C.p, C.f32, alpha, beta);
+}
 
 }  // namespace
+
+// The o^2 v^2 operands: FP32 on a lean handle once converted, else FP64.  cst marks them
+// constant (sigma: operand copies may be cached); setup passes false.
+static T op_t(const adc_handle* h, bool cst) {
+    const long long o = h->o, v = h->v;
+    if (h->f_t) return tf(h->f_t, {o, o, v, v});
+    return cst ? tc(h->t, {o, o, v, v}) : tn(h->t, {o, o, v, v});
+}
+static T op_t2(const adc_handle* h, bool cst) {
+    const long long o = h->o, v = h->v;
+    if (h->f_t2) return tf(h->f_t2, {o, o, v, v});
+    return cst ? tc(h->t_2, {o, o, v, v}) : tn(h->t_2, {o, o, v, v});
+}
+static T op_tau(const adc_handle* h, bool cst) {
+    const long long o = h->o, v = h->v;
+    if (h->f_tau) return tf(h->f_tau, {o, o, v, v});
+    if (!h->tau) throw Error(ADC_ERR_ARG, "tau is not held by this handle");
+    return cst ? tc(h->tau, {o, o, v, v}) : tn(h->tau, {o, o, v, v});
+}
+static T op_ovov(const adc_handle* h, bool cst) {
+    const long long o = h->o, v = h->v;
+    if (h->f_ovov) return tf(h->f_ovov, {o, v, o, v});
+    return cst ? tc(h->ovov, {o, v, o, v}) : tn(h->ovov, {o, v, o, v});
+}
+static T op_oovv(const adc_handle* h, bool cst) {
+    const long long o = h->o, v = h->v;
+    if (h->f_oovv) return tf(h->f_oovv, {o, o, v, v});
+    return cst ? tc(h->oovv, {o, o, v, v}) : tn(h->oovv, {o, o, v, v});
+}
+// FP32 copy of an owned FP64 tensor; the FP64 one is released
+static float* to_f32(adc_handle* h, double*& src, long long n) {
+    float* dst = h->fmalloc(n);
+    Shape s{1, {n}};
+    int id[1] = {0};
+    permute_any(h->ctx, src, false, s, id, dst, true, 1.0, 0.0);
+    h->dfree(src);
+    src = nullptr;
+    return dst;
+}
 
 // --------------------------------------------------------------------------
 // DF ladder: out[n] += sum_Q B^Q_vv X_n B^Q_vv for nmat v x v matrices
@@ -335,19 +428,22 @@ static void sym_add(adc_handle* h, const double* X, double* M, int n, double alp
     permute(c, X, s, perm, M, alpha, 1.0);
 }
 
-static void setup_m11_ea(adc_handle* h) {
+// XL: the ladder term -sum t_kl^ac [L_kl^bc - 1/2 L_kl^cb] (v x v), formed by setup while the
+// ladder of t was alive; NULL: formed here from h->Lt
+static void setup_m11_ea(adc_handle* h, const double* XL) {
     Ctx& c = h->ctx;
     const long long o = h->o, v = h->v, Q = h->naux;
     Scope sc(c.arena);
     double* M = h->M11;
     double* X = c.arena.dalloc(v * v);
-    const double* t = h->t;
+    const T T4 = op_t(h, false), OVOV = op_ovov(h, false), OOVV = op_oovv(h, false);
     // second order: -sum t_kl^ac [(kb|lc) - 1/2 (kc|lb)] + (a<->b)
-    einsum(c, "klac,kblc->ab", -1.0, tn(t, {o, o, v, v}), tn(h->ovov, {o, v, o, v}), 0.0, X, {v, v});
-    einsum(c, "klac,kclb->ab", 0.5, tn(t, {o, o, v, v}), tn(h->ovov, {o, v, o, v}), 1.0, X, {v, v});
+    einsum(c, "klac,kblc->ab", -1.0, T4, OVOV, 0.0, X, {v, v});
+    einsum(c, "klac,kclb->ab", 0.5, T4, OVOV, 1.0, X, {v, v});
     sym_add(h, X, M, (int)v, 1.0);
     if (h->order < 3) return;
-    const double *t2 = h->t_2, *t1 = h->t1_2;
+    const double* t1 = h->t1_2;
+    const T T2 = op_t2(h, false);
     // t1(2): sum_kc t_k^c [2 (kc|ab) - (kb|ac)] + (a<->b)
     double* g = c.arena.dalloc(Q);
     einsum(c, "Qkc,kc->Q", 1.0, tn(h->Bov, {Q, o, v}), tn(t1, {o, v}), 0.0, g, {Q});
@@ -356,38 +452,45 @@ static void setup_m11_ea(adc_handle* h) {
     einsum(c, "kc,Qac->Qka", 1.0, tn(t1, {o, v}), tn(h->Bvv, {Q, v, v}), 0.0, Hq, {Q, o, v});
     einsum(c, "Qkb,Qka->ab", -1.0, tn(h->Bov, {Q, o, v}), tn(Hq, {Q, o, v}), 1.0, X, {v, v});
     // t2(2): same shape as second order
-    einsum(c, "klac,kblc->ab", -1.0, tn(t2, {o, o, v, v}), tn(h->ovov, {o, v, o, v}), 1.0, X, {v, v});
-    einsum(c, "klac,kclb->ab", 0.5, tn(t2, {o, o, v, v}), tn(h->ovov, {o, v, o, v}), 1.0, X, {v, v});
+    einsum(c, "klac,kblc->ab", -1.0, T2, OVOV, 1.0, X, {v, v});
+    einsum(c, "klac,kclb->ab", 0.5, T2, OVOV, 1.0, X, {v, v});
     // vvvv, one open line: -sum t_kl^ac [L_kl^bc - 1/2 L_kl^cb], L_kl = sum_cd (bc..) ladder of t
-    const double* L = h->Lt;
-    einsum(c, "klac,klbc->ab", -1.0, tn(t, {o, o, v, v}), tn(L, {o, o, v, v}), 1.0, X, {v, v});
-    einsum(c, "klac,klcb->ab", 0.5, tn(t, {o, o, v, v}), tn(L, {o, o, v, v}), 1.0, X, {v, v});
+    if (XL) {
+        axpby(c, v * v, 1.0, XL, 1.0, X);
+    } else {
+        const T L = tn(h->Lt, {o, o, v, v});
+        einsum(c, "klac,klbc->ab", -1.0, T4, L, 1.0, X, {v, v});
+        einsum(c, "klac,klcb->ab", 0.5, T4, L, 1.0, X, {v, v});
+    }
     // ring with the open lines on the amplitudes (G_A with t_km^ac, G_B with t_km^ca):
-    //   u1 = -t/2 + t^T, u2 = t - 2 t^T, u3 = t - t^T/2 (t^T swaps the virtual pair)
-    double* u = c.arena.dalloc(o * o * v * v);
-    double* G = c.arena.dalloc(o * o * v * v);
-    Shape s4{4, {o, o, v, v}};
-    int swp[4] = {0, 1, 3, 2};
-    auto make_u = [&](double a, double b) {  // u = a t + b t^T
-        axpby(c, o * o * v * v, a, t, 0.0, u);
-        permute(c, t, s4, swp, u, b, 1.0);
-    };
-    // G_A = sum_ld (kl|db) u1_lm^cd + sum_ld (kb|ld) u2_lm^cd
-    make_u(-0.5, 1.0);
-    einsum(c, "kldb,lmcd->kmcb", 1.0, tn(h->oovv, {o, o, v, v}), tn(u, {o, o, v, v}), 0.0, G, {o, o, v, v});
-    double* GB = c.arena.dalloc(o * o * v * v);
-    einsum(c, "kbld,lmcd->kmcb", 1.0, tn(h->ovov, {o, v, o, v}), tn(u, {o, o, v, v}), 0.0, GB, {o, o, v, v});  // u1 part of G_B
-    make_u(1.0, -2.0);
-    einsum(c, "kbld,lmcd->kmcb", 1.0, tn(h->ovov, {o, v, o, v}), tn(u, {o, o, v, v}), 1.0, G, {o, o, v, v});
-    make_u(1.0, -0.5);
-    einsum(c, "kldb,lmcd->kmcb", 1.0, tn(h->oovv, {o, o, v, v}), tn(u, {o, o, v, v}), 1.0, GB, {o, o, v, v});
-    einsum(c, "kmac,kmcb->ab", 1.0, tn(t, {o, o, v, v}), tn(G, {o, o, v, v}), 1.0, X, {v, v});
-    einsum(c, "kmca,kmcb->ab", 1.0, tn(t, {o, o, v, v}), tn(GB, {o, o, v, v}), 1.0, X, {v, v});
+    //   u1 = -t/2 + t^T, u2 = t - 2 t^T, u3 = t - t^T/2 (t^T swaps the virtual pair).
+    // u is held as [l][d][m][c] (the order in which it enters the GEMMs), G and GB as
+    // [k][b][m][c] (the order in which the GEMMs write them); FP32 on a lean handle.
+    {
+        Scope rs(c.arena);
+        const long long n4 = o * o * v * v;
+        Buf u = scratch(c.arena, n4, h->lean), G = scratch(c.arena, n4, h->lean), GB = scratch(c.arena, n4, h->lean);
+        auto make_u = [&](double a, double b) {  // u[l][d][m][c] = a t_lm^cd + b t_lm^dc
+            perm_into(c, T4, {0, 3, 1, 2}, u, a, 0.0);
+            perm_into(c, T4, {0, 2, 1, 3}, u, b, 1.0);
+        };
+        const T U = u.as({o, v, o, v});
+        // G_A = sum_ld (kl|db) u1_lm^cd + sum_ld (kb|ld) u2_lm^cd
+        make_u(-0.5, 1.0);
+        ein(c, "kldb,ldmc->kbmc", 1.0, OOVV, U, 0.0, G, {o, v, o, v});
+        ein(c, "kbld,ldmc->kbmc", 1.0, OVOV, U, 0.0, GB, {o, v, o, v});  // u1 part of G_B
+        make_u(1.0, -2.0);
+        ein(c, "kbld,ldmc->kbmc", 1.0, OVOV, U, 1.0, G, {o, v, o, v});
+        make_u(1.0, -0.5);
+        ein(c, "kldb,ldmc->kbmc", 1.0, OOVV, U, 1.0, GB, {o, v, o, v});
+        einsum(c, "kmac,kbmc->ab", 1.0, T4, G.as({o, v, o, v}), 1.0, X, {v, v});
+        einsum(c, "kmca,kbmc->ab", 1.0, T4, GB.as({o, v, o, v}), 1.0, X, {v, v});
+    }
     sym_add(h, X, M, (int)v, 1.0);
     // vvvv with both lines on the integral: sum_cd [2 (ab|cd) - (ad|cb)] (2X - X')_cd
     double* Z = c.arena.dalloc(v * v);
-    einsum(c, "klce,klde->cd", 2.0, tn(t, {o, o, v, v}), tn(t, {o, o, v, v}), 0.0, Z, {v, v});
-    einsum(c, "klce,kled->cd", -1.0, tn(t, {o, o, v, v}), tn(t, {o, o, v, v}), 1.0, Z, {v, v});
+    einsum(c, "klce,klde->cd", 2.0, T4, T4, 0.0, Z, {v, v});
+    einsum(c, "klce,kled->cd", -1.0, T4, T4, 1.0, Z, {v, v});
     einsum(c, "Qcd,cd->Q", 1.0, tn(h->Bvv, {Q, v, v}), tn(Z, {v, v}), 0.0, g, {Q});
     einsum(c, "Q,Qab->ab", 2.0, tn(g, {Q}), tn(h->Bvv, {Q, v, v}), 1.0, M, {v, v});
     double* H2 = c.arena.dalloc(Q * v * v);
@@ -395,10 +498,10 @@ static void setup_m11_ea(adc_handle* h) {
     einsum(c, "Qac,Qcb->ab", -1.0, tn(H2, {Q, v, v}), tn(h->Bvv, {Q, v, v}), 1.0, M, {v, v});
     // ring with both lines on the integral: -sum_kl [2 (kl|ab) - (kb|la)] (2U - U')_kl
     double* U = c.arena.dalloc(o * o);
-    einsum(c, "kmcd,lmcd->kl", 2.0, tn(t, {o, o, v, v}), tn(t, {o, o, v, v}), 0.0, U, {o, o});
-    einsum(c, "kmcd,lmdc->kl", -1.0, tn(t, {o, o, v, v}), tn(t, {o, o, v, v}), 1.0, U, {o, o});
-    einsum(c, "klab,kl->ab", -2.0, tn(h->oovv, {o, o, v, v}), tn(U, {o, o}), 1.0, M, {v, v});
-    einsum(c, "kbla,kl->ab", 1.0, tn(h->ovov, {o, v, o, v}), tn(U, {o, o}), 1.0, M, {v, v});
+    einsum(c, "kmcd,lmcd->kl", 2.0, T4, T4, 0.0, U, {o, o});
+    einsum(c, "kmcd,lmdc->kl", -1.0, T4, T4, 1.0, U, {o, o});
+    einsum(c, "klab,kl->ab", -2.0, OOVV, tn(U, {o, o}), 1.0, M, {v, v});
+    einsum(c, "kbla,kl->ab", 1.0, OVOV, tn(U, {o, o}), 1.0, M, {v, v});
 }
 
 static void setup_m11_ip(adc_handle* h) {
@@ -714,25 +817,24 @@ static void make_t1_third_order(adc_handle* h) {
     double* out = h->dmalloc(o * v);
     {
         Scope sc(c.arena);
-        const double *t = h->t, *tau = h->tau, *t1 = h->t1_2, *t2 = h->t_2;
-        const T T4 = tn(t, {o, o, v, v}), U4 = tn(tau, {o, o, v, v});
+        const double* t1 = h->t1_2;
+        const bool f32 = h->lean;  // o^2 v^2 temporaries in FP32 on a lean handle
+        const T T4 = op_t(h, false), U4 = op_tau(h, false), T2 = op_t2(h, false);
         const T Boo = tn(h->Boo, {Q, o, o}), Bvv = tn(h->Bvv, {Q, v, v});
         double* num = c.arena.dalloc(o * v);
         // A1 = sum [2 (ia|jb) - (ij|ab)] t_j^b(2)
-        einsum(c, "iajb,jb->ia", 2.0, tn(h->ovov, {o, v, o, v}), tn(t1, {o, v}), 0.0, num, {o, v});
-        einsum(c, "jiab,jb->ia", -1.0, tn(h->oovv, {o, o, v, v}), tn(t1, {o, v}), 1.0, num, {o, v});
-        Shape s4{4, {o, o, v, v}};
-        int swp[4] = {0, 1, 3, 2};
+        einsum(c, "iajb,jb->ia", 2.0, op_ovov(h, false), tn(t1, {o, v}), 0.0, num, {o, v});
+        einsum(c, "jiab,jb->ia", -1.0, op_oovv(h, false), tn(t1, {o, v}), 1.0, num, {o, v});
         {
             // A2: the t1(2) expression with tau(2) = 2 t2(2) - t2(2)(ab swap)
             Scope s2(c.arena);
-            double* tau2 = c.arena.dalloc(o2v2);
-            axpby(c, o2v2, 2.0, t2, 0.0, tau2);
-            permute(c, t2, s4, swp, tau2, -1.0, 1.0);
+            Buf tau2 = scratch(c.arena, o2v2, f32);
+            perm_into(c, T2, {0, 1, 2, 3}, tau2, 2.0, 0.0);
+            perm_into(c, T2, {0, 1, 3, 2}, tau2, -1.0, 1.0);
             double* G = c.arena.dalloc(Q * o * v);
-            einsum(c, "Qkc,ikdc->Qid", 1.0, tn(h->Bov, {Q, o, v}), tn(tau2, {o, o, v, v}), 0.0, G, {Q, o, v});
+            einsum(c, "Qkc,ikdc->Qid", 1.0, tn(h->Bov, {Q, o, v}), tau2.as({o, o, v, v}), 0.0, G, {Q, o, v});
             einsum(c, "Qid,Qad->ia", 1.0, tn(G, {Q, o, v}), Bvv, 1.0, num, {o, v});
-            einsum(c, "kilc,klac->ia", -1.0, tn(h->ooov, {o, o, o, v}), tn(tau2, {o, o, v, v}), 1.0, num, {o, v});
+            einsum(c, "kilc,klac->ia", -1.0, tn(h->ooov, {o, o, o, v}), tau2.as({o, o, v, v}), 1.0, num, {o, v});
         }
         {
             // E1/2 and -F1/2 through G_jb^Q = sum_kc (kc|Q) tau_jk^bc
@@ -748,8 +850,8 @@ static void make_t1_third_order(adc_handle* h) {
         {
             // E2/4 = -sum t_jk^ad V_jkdi, V_jkdi = sum_Q sum_b B^Q_db sum_c tau_jk^cb B^Q_ic
             Scope s2(c.arena);
-            double* tauS = c.arena.dalloc(o2v2);  // tau_jk^cb stored [j][k][b][c]
-            permute(c, tau, s4, swp, tauS, 1.0, 0.0);
+            Buf tauS = scratch(c.arena, o2v2, f32);  // tau_jk^cb stored [j][k][b][c]
+            perm_into(c, U4, {0, 1, 3, 2}, tauS, 1.0, 0.0);
             double* V = c.arena.dalloc(v * o * o * o);  // [d][j][k][i]
             // auxiliary functions per chunk: the aux_chunk option if set, else a 4 GiB slab of W
             const long long per = v * o * o * o;
@@ -758,7 +860,7 @@ static void make_t1_third_order(adc_handle* h) {
             double* W = c.arena.dalloc(qc * per);  // [Q][b][j][k][i]
             for (long long q0 = 0; q0 < Q; q0 += qc) {
                 const long long nq = std::min(qc, Q - q0);
-                einsum(c, "jkbc,Qic->Qbjki", 1.0, tn(tauS, {o, o, v, v}), tn(h->Bov + q0 * o * v, {nq, o, v}), 0.0, W,
+                einsum(c, "jkbc,Qic->Qbjki", 1.0, tauS.as({o, o, v, v}), tn(h->Bov + q0 * o * v, {nq, o, v}), 0.0, W,
                        {nq, v, o, o, o});
                 einsum(c, "Qdb,Qbjki->djki", 1.0, tn(h->Bvv + q0 * v * v, {nq, v, v}), tn(W, {nq, v, o, o, o}),
                        q0 == 0 ? 0.0 : 1.0, V, {v, o, o, o});
@@ -769,17 +871,18 @@ static void make_t1_third_order(adc_handle* h) {
             // E3 (+1) and F2 (-1) through the ring products
             //   R1_ik^dc = sum tau_ij^db tau_jk^bc,  R2_ik^cd = -sum (tau_ij^db t_jk^bc + tau_ij^bd t_jk^cb)
             Scope s2(c.arena);
-            double* R = c.arena.dalloc(o2v2);
+            Buf R = scratch(c.arena, o2v2, f32);
+            const T RT = R.as({o, o, v, v});
             double* H = c.arena.dalloc(Q * std::max(std::max(o * v, v * v), o * o));
-            einsum(c, "ijdb,jkbc->ikdc", 1.0, U4, U4, 0.0, R, {o, o, v, v});
-            einsum(c, "Qkc,ikdc->Qid", 1.0, tn(h->Bov, {Q, o, v}), tn(R, {o, o, v, v}), 0.0, H, {Q, o, v});
+            ein(c, "ijdb,jkbc->ikdc", 1.0, U4, U4, 0.0, R, {o, o, v, v});
+            einsum(c, "Qkc,ikdc->Qid", 1.0, tn(h->Bov, {Q, o, v}), RT, 0.0, H, {Q, o, v});
             einsum(c, "Qid,Qad->ia", 1.0, tn(H, {Q, o, v}), Bvv, 1.0, num, {o, v});   // E3: (ad|kc) R1
             einsum(c, "Qla,Qli->ia", -1.0, tn(H, {Q, o, v}), Boo, 1.0, num, {o, v});  // F2: (li|kc) R1
-            einsum(c, "ijdb,jkbc->ikcd", -1.0, U4, T4, 0.0, R, {o, o, v, v});
-            einsum(c, "ijbd,jkcb->ikcd", -1.0, U4, T4, 1.0, R, {o, o, v, v});
-            einsum(c, "Qcd,ikcd->Qik", 1.0, Bvv, tn(R, {o, o, v, v}), 0.0, H, {Q, o, o});
+            ein(c, "ijdb,jkbc->ikcd", -1.0, U4, T4, 0.0, R, {o, o, v, v});
+            ein(c, "ijbd,jkcb->ikcd", -1.0, U4, T4, 1.0, R, {o, o, v, v});
+            einsum(c, "Qcd,ikcd->Qik", 1.0, Bvv, RT, 0.0, H, {Q, o, o});
             einsum(c, "Qik,Qka->ia", 1.0, tn(H, {Q, o, o}), tn(h->Bov, {Q, o, v}), 1.0, num, {o, v});  // E3: (ka|cd) R2
-            einsum(c, "Qlk,lkca->Qca", 1.0, Boo, tn(R, {o, o, v, v}), 0.0, H, {Q, v, v});
+            einsum(c, "Qlk,lkca->Qca", 1.0, Boo, RT, 0.0, H, {Q, v, v});
             einsum(c, "Qca,Qic->ia", -1.0, tn(H, {Q, v, v}), tn(h->Bov, {Q, o, v}), 1.0, num, {o, v});  // F2: (lk|ic) R2
         }
         {
@@ -815,6 +918,8 @@ static void make_t1_third_order(adc_handle* h) {
     c.gemm_mode = saved;
     h->t1_3 = out;
 }
+
+static void transition_parts(adc_handle* h, bool third, double* Tpp, double* t1x);
 
 static void setup(adc_handle* h, const double* eps_in, const double* B_in, int on_device) {
     Ctx& c = h->ctx;
@@ -860,15 +965,17 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
         noalloc_prepare();  // the allocation-free ladder's scratch address on this device, resolved up front
     }
     // integrals (Eq. 19)
-    h->ovov = h->dmalloc(o * v * o * v);
-    h->oovv = h->dmalloc(o * o * v * v);
+    const long long o2v2 = o * o * v * v;
+    const bool lean = h->lean;
+    h->ovov = h->dmalloc(o2v2);
+    h->oovv = h->dmalloc(o2v2);
     h->oooo = h->dmalloc(o * o * o * o);
     h->ooov = h->dmalloc(o * o * o * v);
     einsum(c, "Qia,Qjb->iajb", 1.0, tn(h->Bov, {Q, o, v}), tn(h->Bov, {Q, o, v}), 0.0, h->ovov, {o, v, o, v});
     einsum(c, "Qij,Qab->ijab", 1.0, tn(h->Boo, {Q, o, o}), tn(h->Bvv, {Q, v, v}), 0.0, h->oovv, {o, o, v, v});
     einsum(c, "Qij,Qkl->ijkl", 1.0, tn(h->Boo, {Q, o, o}), tn(h->Boo, {Q, o, o}), 0.0, h->oooo, {o, o, o, o});
     einsum(c, "Qij,Qka->ijka", 1.0, tn(h->Boo, {Q, o, o}), tn(h->Bov, {Q, o, v}), 0.0, h->ooov, {o, o, o, v});
-    if (h->order >= 3) {
+    if (h->order >= 3 && !lean) {
         // ring2[i][a][j][c] = 2 (ia|jc) - (ji|ac) (EA) or (ji|ac) - 2 (ia|jc) (IP)
         h->ring2 = h->dmalloc(o * v * o * v);
         const bool ea = h->kind == ADC_EA;
@@ -878,86 +985,109 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
         permute(c, h->oovv, s4, pr, h->ring2, ea ? -1.0 : 1.0, 1.0);
     }
     // amplitudes (Eqs. t_singles, t_doubles)
-    h->t = h->dmalloc(o * o * v * v);
-    k_make_t<<<grid_for(o * o * v * v), 256, 0, c.stream>>>((int)o, (int)v, h->eps, h->ovov, h->t);
+    h->t = h->dmalloc(o2v2);
+    k_make_t<<<grid_for(o2v2), 256, 0, c.stream>>>((int)o, (int)v, h->eps, h->ovov, h->t);
     launch_check(c);
-    h->tau = h->dmalloc(o * o * v * v);
-    {
-        axpby(c, o * o * v * v, 2.0, h->t, 0.0, h->tau);
+    if (!lean) {
+        h->tau = h->dmalloc(o2v2);
+        axpby(c, o2v2, 2.0, h->t, 0.0, h->tau);
         Shape s4{4, {o, o, v, v}};
         int swp[4] = {0, 1, 3, 2};
         permute(c, h->t, s4, swp, h->tau, -1.0, 1.0);
     }
-    Scope setup_scope(c.arena);
-    if (h->order >= 3) {
-        const double* t = h->t;
-        // the ladder of t outlives setup when the EA 1p-1p block is applied on the fly
-        h->Lt = (h->opt.m11_on_the_fly && h->kind == ADC_EA) ? h->dmalloc(o * o * v * v) : c.arena.dalloc(o * o * v * v);
-        fill(c, o * o * v * v, 0.0, h->Lt);
-        ladder(h, t, o * o, h->Lt, h->lm_setup);  // sum_cd (ac|bd) t_ij^cd (it feeds M_11 directly)
-        if (h->opt.precision != ADC_PREC_FP64 && h->tc) {
-            // The tensor core's truncating FP32 accumulation biases each promoted partial sum toward
-            // zero, about linearly in the accumulation length.  With L(E) the ladder accumulated in
-            // epochs of E K blocks, 2 L(1) - L(2) removes the linear part of that bias (Richardson
-            // extrapolation in E): measured on t2(2), bias -1.8e-7 -> -6e-8 relative.
-            Scope rs(c.arena);
-            double* L2 = c.arena.dalloc(o * o * v * v);
-            fill(c, o * o * v * v, 0.0, L2);
-            const LadderMode twice{h->lm_setup.planes, 2 * h->lm_setup.epoch1, 2 * h->lm_setup.epoch2};
-            ladder(h, t, o * o, L2, twice);
-            axpby(c, o * o * v * v, -1.0, L2, 2.0, h->Lt);
-        }
-        Scope sc(c.arena);
-        h->t_2 = h->dmalloc(o * o * v * v);
-        double* N = h->t_2;
-        ADC_CUDA(cudaMemcpyAsync(N, h->Lt, o * o * v * v * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
-        einsum(c, "kilj,klab->ijab", 1.0, tn(h->oooo, {o, o, o, o}), tn(t, {o, o, v, v}), 1.0, N, {o, o, v, v});
-        double* W = c.arena.dalloc(o * o * v * v);
-        einsum(c, "kcjb,ikac->ijab", 2.0, tn(h->ovov, {o, v, o, v}), tn(t, {o, o, v, v}), 0.0, W, {o, o, v, v});
-        einsum(c, "kcjb,ikca->ijab", -1.0, tn(h->ovov, {o, v, o, v}), tn(t, {o, o, v, v}), 1.0, W, {o, o, v, v});
-        einsum(c, "kjbc,ikac->ijab", -1.0, tn(h->oovv, {o, o, v, v}), tn(t, {o, o, v, v}), 1.0, W, {o, o, v, v});
-        einsum(c, "kjac,ikcb->ijab", -1.0, tn(h->oovv, {o, o, v, v}), tn(t, {o, o, v, v}), 1.0, W, {o, o, v, v});
-        axpby(c, o * o * v * v, 1.0, W, 1.0, N);
-        Shape s4{4, {o, o, v, v}};
-        int tr[4] = {1, 0, 3, 2};
-        permute(c, W, s4, tr, N, 1.0, 1.0);
-        k_div_D2<<<grid_for(o * o * v * v), 256, 0, c.stream>>>((int)o, (int)v, h->eps, N);
-        launch_check(c);
-        // singles: D t_i^a = sum (kc|ad)(2 t_ik^dc - t_ik^cd) - sum (ki|lc)(2 t_kl^ac - t_kl^ca)
-        h->t1_2 = h->dmalloc(o * v);
-        double* Gq = c.arena.dalloc(Q * o * v);
-        einsum(c, "Qkc,ikdc->Qid", 1.0, tn(h->Bov, {Q, o, v}), tn(h->tau, {o, o, v, v}), 0.0, Gq, {Q, o, v});
-        einsum(c, "Qid,Qad->ia", 1.0, tn(Gq, {Q, o, v}), tn(h->Bvv, {Q, v, v}), 0.0, h->t1_2, {o, v});
-        einsum(c, "kilc,klac->ia", -1.0, tn(h->ooov, {o, o, o, v}), tn(h->tau, {o, o, v, v}), 1.0, h->t1_2, {o, v});
-        k_div_D1<<<grid_for(o * v), 256, 0, c.stream>>>((int)o, (int)v, h->eps, h->t1_2);
-        launch_check(c);
-    }
-    {
-        // MPn correlation energy: E(k+1) = sum (ia|jb) (2 t_ij^ab - t_ij^ba), t = t2(k);
-        // o^2 v^2 work, always in FP64
+    // MPn correlation energy: E(k+1) = sum (ia|jb) (2 t_ij^ab - t_ij^ba), t = t2(k); o^2 v^2
+    // work, always in FP64 (an FP32 integral operand is read into an FP64 copy)
+    auto mp_energy = [&](const T& tk) {
         Scope sc(c.arena);
         const int saved = c.gemm_mode;
         c.gemm_mode = 0;
         double* part = c.arena.dalloc(o);
+        einsum(c, "iajb,ijab->i", 2.0, op_ovov(h, false), tk, 0.0, part, {o});
+        einsum(c, "iajb,ijba->i", -1.0, op_ovov(h, false), tk, 1.0, part, {o});
         std::vector<double> hp(o);
-        for (int k = 0; k < (h->order >= 3 ? 2 : 1); ++k) {
-            const double* tk = h->tau;
-            if (k == 1) {
-                double* tau2 = c.arena.dalloc(o * o * v * v);
-                axpby(c, o * o * v * v, 2.0, h->t_2, 0.0, tau2);
-                Shape s4{4, {o, o, v, v}};
-                int swp[4] = {0, 1, 3, 2};
-                permute(c, h->t_2, s4, swp, tau2, -1.0, 1.0);
-                tk = tau2;
-            }
-            einsum(c, "iajb,ijab->i", 1.0, tn(h->ovov, {o, v, o, v}), tn(tk, {o, o, v, v}), 0.0, part, {o});
-            ADC_CUDA(cudaMemcpyAsync(hp.data(), part, o * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
-            ADC_CUDA(cudaStreamSynchronize(c.stream));
-            double e = 0.0;
-            for (double x : hp) e += x;
-            h->emp[k] = e;
-        }
+        ADC_CUDA(cudaMemcpyAsync(hp.data(), part, o * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        ADC_CUDA(cudaStreamSynchronize(c.stream));
         c.gemm_mode = saved;
+        double e = 0.0;
+        for (double x : hp) e += x;
+        return e;
+    };
+    h->emp[0] = mp_energy(tn(h->t, {o, o, v, v}));
+    if (lean) {
+        // every later use of the integrals is a split-BF16 or FP32-accurate contraction
+        h->f_oovv = to_f32(h, h->oovv, o2v2);
+        h->f_ovov = to_f32(h, h->ovov, o2v2);
+    }
+    Scope setup_scope(c.arena);
+    double* XL = nullptr;  // EA: the ladder term of the 1p-1p block, formed while the ladder of t is alive
+    if (h->order >= 3) {
+        const T T4 = op_t(h, false);
+        const bool keep_Lt = h->opt.m11_on_the_fly && h->kind == ADC_EA;  // sigma applies the block from it
+        double* Lt = h->dmalloc(o2v2);
+        fill(c, o2v2, 0.0, Lt);
+        ladder(h, h->t, o * o, Lt, h->lm_setup);  // sum_cd (ac|bd) t_ij^cd (it feeds M_11 directly)
+        if (h->opt.precision != ADC_PREC_FP64 && h->tc) {
+            // The tensor core's truncating FP32 accumulation biases each promoted partial sum toward
+            // zero, about linearly in the accumulation length.  With L(E) the ladder accumulated in
+            // epochs of E K blocks, 2 L(1) - L(2) removes the linear part of that bias (Richardson
+            // extrapolation in E): measured on t2(2), bias -1.8e-7 -> -6e-8 relative.  Formed in
+            // place: Lt <- -2 L(1), then += L(2), then negated.
+            const LadderMode twice{h->lm_setup.planes, 2 * h->lm_setup.epoch1, 2 * h->lm_setup.epoch2};
+            axpby(c, o2v2, 0.0, Lt, -2.0, Lt);
+            ladder(h, h->t, o * o, Lt, twice);
+            axpby(c, o2v2, 0.0, Lt, -1.0, Lt);
+        }
+        double* N = Lt;  // t2(2) numerator, formed in the ladder's buffer unless the ladder is kept
+        if (keep_Lt) {
+            h->Lt = Lt;
+            N = h->dmalloc(o2v2);
+            ADC_CUDA(cudaMemcpyAsync(N, Lt, o2v2 * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+        } else if (h->kind == ADC_EA) {
+            // X_ab = -sum t_kl^ac [L_kl^bc - 1/2 L_kl^cb] (one open line through the ladder)
+            XL = c.arena.dalloc(v * v);
+            einsum(c, "klac,klbc->ab", -1.0, T4, tn(Lt, {o, o, v, v}), 0.0, XL, {v, v});
+            einsum(c, "klac,klcb->ab", 0.5, T4, tn(Lt, {o, o, v, v}), 1.0, XL, {v, v});
+        }
+        h->t_2 = N;
+        {
+            Scope sc(c.arena);
+            einsum(c, "kilj,klab->ijab", 1.0, tn(h->oooo, {o, o, o, o}), T4, 1.0, N, {o, o, v, v});
+            const T OVOV = op_ovov(h, false), OOVV = op_oovv(h, false);
+            Buf W = scratch(c.arena, o2v2, lean);
+            ein(c, "kcjb,ikac->ijab", 2.0, OVOV, T4, 0.0, W, {o, o, v, v});
+            ein(c, "kcjb,ikca->ijab", -1.0, OVOV, T4, 1.0, W, {o, o, v, v});
+            ein(c, "kjbc,ikac->ijab", -1.0, OOVV, T4, 1.0, W, {o, o, v, v});
+            ein(c, "kjac,ikcb->ijab", -1.0, OOVV, T4, 1.0, W, {o, o, v, v});
+            const Buf Nb{N, false};
+            perm_into(c, W.as({o, o, v, v}), {0, 1, 2, 3}, Nb, 1.0, 1.0);
+            perm_into(c, W.as({o, o, v, v}), {1, 0, 3, 2}, Nb, 1.0, 1.0);
+        }
+        k_div_D2<<<grid_for(o2v2), 256, 0, c.stream>>>((int)o, (int)v, h->eps, N);
+        launch_check(c);
+        // singles: D t_i^a = sum (kc|ad)(2 t_ik^dc - t_ik^cd) - sum (ki|lc)(2 t_kl^ac - t_kl^ca)
+        h->t1_2 = h->dmalloc(o * v);
+        {
+            Scope sc(c.arena);
+            if (lean) {
+                h->f_tau = (float*)c.arena.alloc(o2v2 * sizeof(float));
+                const Buf tb{h->f_tau, true};
+                perm_into(c, T4, {0, 1, 2, 3}, tb, 2.0, 0.0);
+                perm_into(c, T4, {0, 1, 3, 2}, tb, -1.0, 1.0);
+            }
+            const T U4 = op_tau(h, false);
+            double* Gq = c.arena.dalloc(Q * o * v);
+            einsum(c, "Qkc,ikdc->Qid", 1.0, tn(h->Bov, {Q, o, v}), U4, 0.0, Gq, {Q, o, v});
+            einsum(c, "Qid,Qad->ia", 1.0, tn(Gq, {Q, o, v}), tn(h->Bvv, {Q, v, v}), 0.0, h->t1_2, {o, v});
+            einsum(c, "kilc,klac->ia", -1.0, tn(h->ooov, {o, o, o, v}), U4, 1.0, h->t1_2, {o, v});
+            h->f_tau = nullptr;
+        }
+        k_div_D1<<<grid_for(o * v), 256, 0, c.stream>>>((int)o, (int)v, h->eps, h->t1_2);
+        launch_check(c);
+        h->emp[1] = mp_energy(tn(h->t_2, {o, o, v, v}));
+    }
+    if (lean) {
+        h->f_t = to_f32(h, h->t, o2v2);
+        if (h->t_2) h->f_t2 = to_f32(h, h->t_2, o2v2);
     }
     const long long n1 = h->n1();
     if (h->opt.m11_on_the_fly) {
@@ -982,7 +1112,7 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
         ADC_CUDA(cudaStreamSynchronize(c.stream));
     }
     if (h->kind == ADC_EA) {
-        setup_m11_ea(h);
+        setup_m11_ea(h, XL);
     } else {
         // The 1h-1h block's contractions run in FP64 in every precision: on strongly correlated
         // inputs its third-order terms cancel to a small fraction of their parts, and FP32-accurate
@@ -992,7 +1122,20 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
         setup_m11_ip(h);
         c.gemm_mode = saved;
     }
-    h->Lt = nullptr;
+    if (lean) {
+        // what the transition moments need beyond t and t2(2), made while setup's memory is free
+        Scope sc(c.arena);
+        h->f_tau = (float*)c.arena.alloc(o2v2 * sizeof(float));
+        const Buf tb{h->f_tau, true};
+        perm_into(c, op_t(h, false), {0, 1, 2, 3}, tb, 2.0, 0.0);
+        perm_into(c, op_t(h, false), {0, 1, 3, 2}, tb, -1.0, 1.0);
+        const long long np = std::max(o, v);
+        h->spec_Tpp = h->dmalloc(2 * np * np);
+        h->spec_t1 = h->dmalloc(2 * o * v);
+        for (int third = 0; third <= (h->order >= 3 ? 1 : 0); ++third)
+            transition_parts(h, third != 0, h->spec_Tpp + third * np * np, h->spec_t1 + third * o * v);
+        h->f_tau = nullptr;
+    }
     h->diag = h->dmalloc(h->dim());
     k_diag<<<grid_for(h->dim()), 256, 0, c.stream>>>(h->kind == ADC_EA, (int)o, (int)v, h->eps, h->M11, h->diag);
     launch_check(c);
@@ -1035,21 +1178,26 @@ static void sigma_ea(adc_handle* h, const double* Xin, double* Sout, long long n
     k_diag22<<<grid_for(n * blk), 256, 0, c.stream>>>(1, (int)o, (int)v, n, h->eps, Y2, S2);
     launch_check(c);
     if (h->order >= 3) {
-        const double *t = h->t, *tau = h->tau;
+        const T T4 = op_t(h, true);
         // coupling row, second order:
         //  sum (al|jm) t_lm^dc Y~_jcd
         double* Z = c.arena.dalloc(n * o * o * o);
-        einsum(c, "lmdc,njcd->nlmj", 1.0, tc(t, {o, o, v, v}), tn(Yt, {n, o, v, v}), 0.0, Z, {n, o, o, o});
+        einsum(c, "lmdc,njcd->nlmj", 1.0, T4, tn(Yt, {n, o, v, v}), 0.0, Z, {n, o, o, o});
         // P^Q_l collects the terms of the form sum_Ql P^Q_l (Q|la) (contracted once, below)
         double* P = c.arena.dalloc(n * Q * o);
         einsum(c, "Qjm,nlmj->nQl", 1.0, tc(h->Boo, {Q, o, o}), tn(Z, {n, o, o, o}), 0.0, P, {n, Q, o});
-        //  sum (ad|em)(2 t_jm^ce - t_jm^ec) Y~_jcd
+        //  sum (ad|em)(2 t_jm^ce - t_jm^ec) Y~_jcd  (a lean handle holds no tau: two contractions with t)
         double* V = c.arena.dalloc(n * o * v * v);
-        einsum(c, "jmce,njcd->nmed", 1.0, tc(tau, {o, o, v, v}), tn(Yt, {n, o, v, v}), 0.0, V, {n, o, v, v});
+        if (h->tau) {
+            einsum(c, "jmce,njcd->nmed", 1.0, tc(h->tau, {o, o, v, v}), tn(Yt, {n, o, v, v}), 0.0, V, {n, o, v, v});
+        } else {
+            einsum(c, "jmce,njcd->nmed", 2.0, T4, tn(Yt, {n, o, v, v}), 0.0, V, {n, o, v, v});
+            einsum(c, "jmec,njcd->nmed", -1.0, T4, tn(Yt, {n, o, v, v}), 1.0, V, {n, o, v, v});
+        }
         einsum(c, "nmed,Qme->nQd", 1.0, tn(V, {n, o, v, v}), tc(h->Bov, {Q, o, v}), 1.0, Wq, {n, Q, v});
         //  - sum (am|ed) [t_jm^ce Y~_jcd + t_jm^ed Y~_jdc]   (the two exchange-type terms)
-        einsum(c, "jmce,njcd->nmed", 1.0, tc(t, {o, o, v, v}), tn(Yt, {n, o, v, v}), 0.0, V, {n, o, v, v});
-        einsum(c, "jmec,njdc->nmed", 1.0, tc(t, {o, o, v, v}), tn(Yt, {n, o, v, v}), 1.0, V, {n, o, v, v});
+        einsum(c, "jmce,njcd->nmed", 1.0, T4, tn(Yt, {n, o, v, v}), 0.0, V, {n, o, v, v});
+        einsum(c, "jmec,njdc->nmed", 1.0, T4, tn(Yt, {n, o, v, v}), 1.0, V, {n, o, v, v});
         einsum(c, "nmed,Qed->nQm", -1.0, tn(V, {n, o, v, v}), tc(h->Bvv, {Q, v, v}), 1.0, P, {n, Q, o});
         einsum(c, "nQl,Qla->na", 1.0, tn(P, {n, Q, o}), tc(h->Bov, {Q, o, v}), 1.0, s1, {n, v});
         // 2p1h column, second order:
@@ -1058,21 +1206,33 @@ static void sigma_ea(adc_handle* h, const double* Xin, double* Sout, long long n
         einsum(c, "nc,Qlc->nQl", 1.0, tn(y1, {n, v}), tc(h->Bov, {Q, o, v}), 0.0, p, {n, Q, o});
         double* Pl = c.arena.dalloc(n * o * o * o);
         einsum(c, "nQl,Qim->nlim", 1.0, tn(p, {n, Q, o}), tc(h->Boo, {Q, o, o}), 0.0, Pl, {n, o, o, o});
-        einsum(c, "nlim,lmba->niab", 1.0, tn(Pl, {n, o, o, o}), tc(t, {o, o, v, v}), 1.0, S2, {n, o, v, v});
+        einsum(c, "nlim,lmba->niab", 1.0, tn(Pl, {n, o, o, o}), T4, 1.0, S2, {n, o, v, v});
         //  sum_me (cb|em)(2 t_im^ae - t_im^ea) Y_c
         double* q = c.arena.dalloc(n * o * v * v);
         einsum(c, "nQb,Qme->nbme", 1.0, tn(hq, {n, Q, v}), tc(h->Bov, {Q, o, v}), 0.0, q, {n, v, o, v});
-        einsum(c, "nbme,imae->niab", 1.0, tn(q, {n, v, o, v}), tc(tau, {o, o, v, v}), 1.0, S2, {n, o, v, v});
+        if (h->tau) {
+            einsum(c, "nbme,imae->niab", 1.0, tn(q, {n, v, o, v}), tc(h->tau, {o, o, v, v}), 1.0, S2, {n, o, v, v});
+        } else {
+            einsum(c, "nbme,imae->niab", 2.0, tn(q, {n, v, o, v}), T4, 1.0, S2, {n, o, v, v});
+            einsum(c, "nbme,imea->niab", -1.0, tn(q, {n, v, o, v}), T4, 1.0, S2, {n, o, v, v});
+        }
         //  - sum_me (cm|eb) t_im^ae Y_c - sum_me (cm|ea) t_im^eb Y_c
         einsum(c, "nQm,Qeb->nmeb", 1.0, tn(p, {n, Q, o}), tc(h->Bvv, {Q, v, v}), 0.0, q, {n, o, v, v});
-        einsum(c, "nmeb,imae->niab", -1.0, tn(q, {n, o, v, v}), tc(t, {o, o, v, v}), 1.0, S2, {n, o, v, v});
-        einsum(c, "nmea,imeb->niab", -1.0, tn(q, {n, o, v, v}), tc(t, {o, o, v, v}), 1.0, S2, {n, o, v, v});
+        einsum(c, "nmeb,imae->niab", -1.0, tn(q, {n, o, v, v}), T4, 1.0, S2, {n, o, v, v});
+        einsum(c, "nmea,imeb->niab", -1.0, tn(q, {n, o, v, v}), T4, 1.0, S2, {n, o, v, v});
         // 2p1h block, first order: ladder sum_cd (ac|bd) Y_icd (vvvv never stored)
         ladder(h, Y2, n * o, S2, h->refining ? h->lm_refine : h->lm_sigma);
-        //  - (ac|ji) Y_jcb + 2 (ai|jc) Y_jcb - (ai|jc) Y_jbc - (bd|ji) Y_jad  (the first two as one)
-        einsum(c, "iajc,njcb->niab", 1.0, tc(h->ring2, {o, v, o, v}), tn(Y2, {n, o, v, v}), 1.0, S2, {n, o, v, v});
-        einsum(c, "iajc,njbc->niab", -1.0, tc(h->ovov, {o, v, o, v}), tn(Y2, {n, o, v, v}), 1.0, S2, {n, o, v, v});
-        einsum(c, "jibd,njad->niab", -1.0, tc(h->oovv, {o, o, v, v}), tn(Y2, {n, o, v, v}), 1.0, S2, {n, o, v, v});
+        //  - (ac|ji) Y_jcb + 2 (ai|jc) Y_jcb - (ai|jc) Y_jbc - (bd|ji) Y_jad  (the first two as one
+        //  contraction with ring2, or two on a lean handle)
+        const T OVOV = op_ovov(h, true), OOVV = op_oovv(h, true), Y2T = tn(Y2, {n, o, v, v});
+        if (h->ring2) {
+            einsum(c, "iajc,njcb->niab", 1.0, tc(h->ring2, {o, v, o, v}), Y2T, 1.0, S2, {n, o, v, v});
+        } else {
+            einsum(c, "iajc,njcb->niab", 2.0, OVOV, Y2T, 1.0, S2, {n, o, v, v});
+            einsum(c, "jiac,njcb->niab", -1.0, OOVV, Y2T, 1.0, S2, {n, o, v, v});
+        }
+        einsum(c, "iajc,njbc->niab", -1.0, OVOV, Y2T, 1.0, S2, {n, o, v, v});
+        einsum(c, "jibd,njad->niab", -1.0, OOVV, Y2T, 1.0, S2, {n, o, v, v});
     }
     // coupling row: every sum_Qd W^Q_d (Q|da) term at once
     einsum(c, "nQd,Qda->na", 1.0, tn(Wq, {n, Q, v}), tc(h->Bvv, {Q, v, v}), 1.0, s1, {n, v});
@@ -1417,6 +1577,62 @@ struct Davidson {
     }
 };
 
+// Root-independent parts of the transition moments (Eqs. T_ea, T_ip; Appendix): the
+// one-particle block of T without its unit diagonal, Tpp (EA: [v][v], T_cb - d_cb; IP: [o][o]),
+// and the singles row t1x [o][v] = t1(2) [+ t1(3) + 1/2 sum tau t1(2)] (third: T through
+// third order).  In the setup's contraction arithmetic.
+static void transition_parts(adc_handle* h, bool third, double* Tpp, double* t1x) {
+    Ctx& c = h->ctx;
+    const int saved = c.gemm_mode;
+    c.gemm_mode = h->cmode_setup;
+    const long long o = h->o, v = h->v, Q = h->naux;
+    Scope sc(c.arena);
+    const T T4 = op_t(h, false);
+    if (h->t1_2) {
+        axpby(c, o * v, 1.0, h->t1_2, 0.0, t1x);
+    } else {
+        // second-order singles are part of T(2) also for ADC(2)
+        double* Gq = c.arena.dalloc(Q * o * v);
+        einsum(c, "Qkc,ikdc->Qid", 1.0, tn(h->Bov, {Q, o, v}), op_tau(h, false), 0.0, Gq, {Q, o, v});
+        einsum(c, "Qid,Qad->ia", 1.0, tn(Gq, {Q, o, v}), tn(h->Bvv, {Q, v, v}), 0.0, t1x, {o, v});
+        einsum(c, "kilc,klac->ia", -1.0, tn(h->ooov, {o, o, o, v}), op_tau(h, false), 1.0, t1x, {o, v});
+        k_div_D1<<<grid_for(o * v), 256, 0, c.stream>>>((int)o, (int)v, h->eps, t1x);
+        launch_check(c);
+    }
+    if (third) {
+        make_t1_third_order(h);
+        axpby(c, o * v, 1.0, h->t1_3, 1.0, t1x);
+        const char* spec = h->kind == ADC_EA ? "klbc,lc->kb" : "jlcd,ld->jc";
+        einsum(c, spec, 0.5, op_tau(h, false), tn(h->t1_2, {o, v}), 1.0, t1x, {o, v});
+    }
+    if (h->kind == ADC_EA) {
+        // T_{c,b} = d_cb + B(t, t)_cb [+ B(t, t2) + B(t2, t)],
+        // B(x, y)_cb = -sum x_kl^cd y_kl^bd + 1/2 sum x_kl^cd y_kl^db
+        einsum(c, "klcd,klbd->cb", -1.0, T4, T4, 0.0, Tpp, {v, v});
+        einsum(c, "klcd,kldb->cb", 0.5, T4, T4, 1.0, Tpp, {v, v});
+        if (third) {
+            const T T2 = op_t2(h, false);
+            einsum(c, "klcd,klbd->cb", -1.0, T4, T2, 1.0, Tpp, {v, v});
+            einsum(c, "klcd,kldb->cb", 0.5, T4, T2, 1.0, Tpp, {v, v});
+            einsum(c, "klcd,klbd->cb", -1.0, T2, T4, 1.0, Tpp, {v, v});
+            einsum(c, "klcd,kldb->cb", 0.5, T2, T4, 1.0, Tpp, {v, v});
+        }
+    } else {
+        // T_{k,j} = d_kj + B'(t, t)_kj [+ B'(t, t2) + B'(t2, t)],
+        // B'(x, y)_kj = -sum x_kl^cd y_jl^cd + 1/2 sum x_kl^cd y_jl^dc
+        einsum(c, "klcd,jlcd->kj", -1.0, T4, T4, 0.0, Tpp, {o, o});
+        einsum(c, "klcd,jldc->kj", 0.5, T4, T4, 1.0, Tpp, {o, o});
+        if (third) {
+            const T T2 = op_t2(h, false);
+            einsum(c, "klcd,jlcd->kj", -1.0, T4, T2, 1.0, Tpp, {o, o});
+            einsum(c, "klcd,jldc->kj", 0.5, T4, T2, 1.0, Tpp, {o, o});
+            einsum(c, "klcd,jlcd->kj", -1.0, T2, T4, 1.0, Tpp, {o, o});
+            einsum(c, "klcd,jldc->kj", 0.5, T2, T4, 1.0, Tpp, {o, o});
+        }
+    }
+    c.gemm_mode = saved;
+}
+
 static void specfac_unrestricted(adc_handle* h, const double* Y, int nroots, double* specfac);
 
 static void drop_graphs(adc_handle* h) {
@@ -1735,7 +1951,6 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
         d.metric(X, SX, nroots, 0);
         double* Xp = c.arena.dalloc((size_t)nroots * nmo);
         fill(c, (long long)nroots * nmo, 0.0, Xp);
-        double* Tpp = c.arena.dalloc((size_t)std::max(o, v) * std::max(o, v));
         double* s1 = c.arena.dalloc((size_t)nroots * std::max(o, v));
         double* s2 = c.arena.dalloc((size_t)nroots * (h->kind == ADC_EA ? o * v * v : o * o * v));
         long long n1 = h->n1(), blk = dim - n1;
@@ -1743,47 +1958,24 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
         launch_check(c);
         k_gather<<<grid_for(nroots * blk), 256, 0, c.stream>>>(nroots, blk, SX, dim, n1, s2, blk, 0, 0.0);
         launch_check(c);
-        const double* t = h->t;
-        double* t1 = h->t1_2;
-        double* t1tmp = nullptr;
-        if (!t1) {
-            // second-order singles are part of T(2) also for ADC(2)
-            t1tmp = c.arena.dalloc(o * v);
-            double* Gq = c.arena.dalloc(h->naux * o * v);
-            einsum(c, "Qkc,ikdc->Qid", 1.0, tn(h->Bov, {h->naux, o, v}), tn(h->tau, {o, o, v, v}), 0.0, Gq, {h->naux, o, v});
-            einsum(c, "Qid,Qad->ia", 1.0, tn(Gq, {h->naux, o, v}), tn(h->Bvv, {h->naux, v, v}), 0.0, t1tmp, {o, v});
-            einsum(c, "kilc,klac->ia", -1.0, tn(h->ooov, {o, o, o, v}), tn(h->tau, {o, o, v, v}), 1.0, t1tmp, {o, v});
-            k_div_D1<<<grid_for(o * v), 256, 0, c.stream>>>((int)o, (int)v, h->eps, t1tmp);
-            launch_check(c);
-            t1 = t1tmp;
-        }
-        // X rows laid out [r][p] with p over all nmo orbitals (occupied first)
-        // ADC(3): T through third order (k + l <= 3): the density cross terms with
-        // t2(2), t1(3) + 1/2 tau t1(2) in the one-particle rows of the other space,
-        // and t2(2) beside t2(1) in the two-particle columns
+        // root-independent parts: the one-particle block T_pp' (without its unit diagonal) and
+        // the singles row t1x (precomputed by setup on a lean handle)
         const bool third = h->order >= 3 && h->opt.transition_order != 2;
-        double* t1x = nullptr;  // t1(2) [+ t1(3) + 1/2 sum tau t1(2)], [o][v]
-        if (third) {
-            make_t1_third_order(h);
-            t1x = c.arena.dalloc(o * v);
-            axpby(c, o * v, 1.0, h->t1_2, 0.0, t1x);
-            axpby(c, o * v, 1.0, h->t1_3, 1.0, t1x);
-            const char* spec = h->kind == ADC_EA ? "klbc,lc->kb" : "jlcd,ld->jc";
-            einsum(c, spec, 0.5, tn(h->tau, {o, o, v, v}), tn(h->t1_2, {o, v}), 1.0, t1x, {o, v});
-            t1 = t1x;
+        const long long np = std::max(o, v);
+        const double* Tpp;
+        const double* t1;
+        if (h->spec_Tpp) {
+            Tpp = h->spec_Tpp + (third ? np * np : 0);
+            t1 = h->spec_t1 + (third ? o * v : 0);
+        } else {
+            double* Tb = c.arena.dalloc((size_t)np * np);
+            double* tb = c.arena.dalloc((size_t)o * v);
+            transition_parts(h, third, Tb, tb);
+            Tpp = Tb;
+            t1 = tb;
         }
+        const T T4 = op_t(h, h->lean);
         if (h->kind == ADC_EA) {
-            // T_{c,b} = d_cb + B(t, t)_cb [+ B(t, t2) + B(t2, t)],
-            // B(x, y)_cb = -sum x_kl^cd y_kl^bd + 1/2 sum x_kl^cd y_kl^db
-            einsum(c, "klcd,klbd->cb", -1.0, tn(t, {o, o, v, v}), tn(t, {o, o, v, v}), 0.0, Tpp, {v, v});
-            einsum(c, "klcd,kldb->cb", 0.5, tn(t, {o, o, v, v}), tn(t, {o, o, v, v}), 1.0, Tpp, {v, v});
-            if (third) {
-                const double* t2 = h->t_2;
-                einsum(c, "klcd,klbd->cb", -1.0, tn(t, {o, o, v, v}), tn(t2, {o, o, v, v}), 1.0, Tpp, {v, v});
-                einsum(c, "klcd,kldb->cb", 0.5, tn(t, {o, o, v, v}), tn(t2, {o, o, v, v}), 1.0, Tpp, {v, v});
-                einsum(c, "klcd,klbd->cb", -1.0, tn(t2, {o, o, v, v}), tn(t, {o, o, v, v}), 1.0, Tpp, {v, v});
-                einsum(c, "klcd,kldb->cb", 0.5, tn(t2, {o, o, v, v}), tn(t, {o, o, v, v}), 1.0, Tpp, {v, v});
-            }
             double* xv = c.arena.dalloc((size_t)nroots * v);
             ADC_CUDA(cudaMemcpyAsync(xv, s1, (size_t)nroots * v * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
             einsum(c, "rb,cb->rc", 1.0, tn(s1, {nroots, v}), tn(Tpp, {v, v}), 1.0, xv, {nroots, v});
@@ -1793,23 +1985,11 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
             // T_{k,jcd} = -t_kj^dc [- t2_kj^dc]
             double* xo = c.arena.dalloc((size_t)nroots * o);
             einsum(c, "rb,kb->rk", -1.0, tn(s1, {nroots, v}), tn(t1, {o, v}), 0.0, xo, {nroots, o});
-            einsum(c, "rjcd,kjdc->rk", -1.0, tn(s2, {nroots, o, v, v}), tn(t, {o, o, v, v}), 1.0, xo, {nroots, o});
-            if (third)
-                einsum(c, "rjcd,kjdc->rk", -1.0, tn(s2, {nroots, o, v, v}), tn(h->t_2, {o, o, v, v}), 1.0, xo, {nroots, o});
+            einsum(c, "rjcd,kjdc->rk", -1.0, tn(s2, {nroots, o, v, v}), T4, 1.0, xo, {nroots, o});
+            if (third) einsum(c, "rjcd,kjdc->rk", -1.0, tn(s2, {nroots, o, v, v}), op_t2(h, h->lean), 1.0, xo, {nroots, o});
             k_gather<<<grid_for(nroots * o), 256, 0, c.stream>>>(nroots, o, xo, o, 0, Xp, nmo, 0, 0.0);
             launch_check(c);
         } else {
-            // T_{k,j} = d_kj + B'(t, t)_kj [+ B'(t, t2) + B'(t2, t)],
-            // B'(x, y)_kj = -sum x_kl^cd y_jl^cd + 1/2 sum x_kl^cd y_jl^dc
-            einsum(c, "klcd,jlcd->kj", -1.0, tn(t, {o, o, v, v}), tn(t, {o, o, v, v}), 0.0, Tpp, {o, o});
-            einsum(c, "klcd,jldc->kj", 0.5, tn(t, {o, o, v, v}), tn(t, {o, o, v, v}), 1.0, Tpp, {o, o});
-            if (third) {
-                const double* t2 = h->t_2;
-                einsum(c, "klcd,jlcd->kj", -1.0, tn(t, {o, o, v, v}), tn(t2, {o, o, v, v}), 1.0, Tpp, {o, o});
-                einsum(c, "klcd,jldc->kj", 0.5, tn(t, {o, o, v, v}), tn(t2, {o, o, v, v}), 1.0, Tpp, {o, o});
-                einsum(c, "klcd,jlcd->kj", -1.0, tn(t2, {o, o, v, v}), tn(t, {o, o, v, v}), 1.0, Tpp, {o, o});
-                einsum(c, "klcd,jldc->kj", 0.5, tn(t2, {o, o, v, v}), tn(t, {o, o, v, v}), 1.0, Tpp, {o, o});
-            }
             double* xo = c.arena.dalloc((size_t)nroots * o);
             ADC_CUDA(cudaMemcpyAsync(xo, s1, (size_t)nroots * o * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
             einsum(c, "rj,kj->rk", 1.0, tn(s1, {nroots, o}), tn(Tpp, {o, o}), 1.0, xo, {nroots, o});
@@ -1819,9 +1999,8 @@ static int davidson(adc_handle* h, int nroots, double tol, const double* guess, 
             // T_{c,ija} = -t_ij^ac [- t2_ij^ac]
             double* xv = c.arena.dalloc((size_t)nroots * v);
             einsum(c, "rj,jc->rc", 1.0, tn(s1, {nroots, o}), tn(t1, {o, v}), 0.0, xv, {nroots, v});
-            einsum(c, "rija,ijac->rc", -1.0, tn(s2, {nroots, o, o, v}), tn(t, {o, o, v, v}), 1.0, xv, {nroots, v});
-            if (third)
-                einsum(c, "rija,ijac->rc", -1.0, tn(s2, {nroots, o, o, v}), tn(h->t_2, {o, o, v, v}), 1.0, xv, {nroots, v});
+            einsum(c, "rija,ijac->rc", -1.0, tn(s2, {nroots, o, o, v}), T4, 1.0, xv, {nroots, v});
+            if (third) einsum(c, "rija,ijac->rc", -1.0, tn(s2, {nroots, o, o, v}), op_t2(h, h->lean), 1.0, xv, {nroots, v});
             k_gather<<<grid_for(nroots * v), 256, 0, c.stream>>>(nroots, v, xv, v, 0, Xp, nmo, o, 0.0);
             launch_check(c);
         }
@@ -2743,6 +2922,7 @@ int adc_default_options(adc_options* opt) {
     opt->m11_on_the_fly = 0;
     opt->tune_cache = nullptr;
     opt->cuda_graphs = 0;
+    opt->lean = -1;
     return ADC_OK;
 }
 
@@ -2779,10 +2959,32 @@ static int setup_one(const double* eps, const double* Bq, int nocc, int nvir, in
     h->kind = kind;
     adc_default_options(&h->opt);
     if (opt) h->opt = *opt;
+    const bool lean_ok = kind == ADC_EA && h->opt.precision != ADC_PREC_FP64 && !h->opt.m11_on_the_fly;
+    if (h->opt.lean > 0 && !lean_ok) {
+        msg = "adc_setup: the lean layout needs EA, BF16X3 precision and a precomputed 1p-1p block";
+        delete h;
+        return ADC_ERR_ARG;
+    }
     try {
         if (own_stream) {
             ADC_CUDA(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
             h->ctx.set_stream(h->own_stream);
+        }
+        bool lean = h->opt.lean > 0;
+        if (h->opt.lean < 0 && lean_ok) {
+            // automatic: lean when the plain layout's setup peak would not fit the free memory
+            // (B^Q blocks and input, the ladder's BF16 planes, ~9 o^2 v^2 FP64 tensors at once)
+            size_t fr = 0, tot = 0;
+            ADC_CUDA(cudaMemGetInfo(&fr, &tot));
+            const double o = nocc, v = nvir, Q = naux, nmo = o + v;
+            const double plain = 8.0 * (Q * nmo * nmo * (on_device ? 2.0 : 1.0) + 9.0 * o * o * v * v) +
+                                 8.0 * Q * v * (v + 31.0);
+            lean = plain > 0.9 * (double)fr;
+        }
+        if (lean) {
+            h->lean = true;
+            h->ctx.cache_max_bytes = 0;               // operand planes / FP32 copies made per call
+            h->ctx.arena.big_bytes = size_t(256) << 20;  // large scratch in blocks of its own
         }
         setup(h, eps, Bq, on_device);
         ADC_CUDA(cudaStreamSynchronize(h->ctx.stream));
@@ -3006,13 +3208,20 @@ int adc_get_tensor(adc_handle* h, const char* name, double* out, long long n) {
     GUARD(h, {
         const long long o = h->o, v = h->v;
         const double* src = nullptr;
+        const float* src32 = nullptr;  // a lean handle's FP32 tensor
         long long cnt = 0;
         std::string s(name);
         if (s == "M11") {
             src = h->M11;
             cnt = (long long)h->n1() * h->n1();
+        } else if (s == "t2" && h->f_t) {
+            src32 = h->f_t;
+            cnt = o * o * v * v;
         } else if (s == "t2") {
             src = h->t;
+            cnt = o * o * v * v;
+        } else if (s == "t2_2" && h->f_t2) {
+            src32 = h->f_t2;
             cnt = o * o * v * v;
         } else if (s == "t2_2") {
             src = h->t_2;
@@ -3044,13 +3253,23 @@ int adc_get_tensor(adc_handle* h, const char* name, double* out, long long n) {
             std::memcpy(out, h->X_last.data(), cnt * sizeof(double));
             return ADC_OK;
         }
-        if (!src) {
+        if (!src && !src32) {
             h->err = "adc_get_tensor: unknown or unavailable tensor " + s;
             return ADC_ERR_ARG;
         }
         if (n < cnt) {
             h->err = "adc_get_tensor: buffer too small";
             return ADC_ERR_ARG;
+        }
+        if (src32) {
+            Scope sc(h->ctx.arena);
+            double* tmp = h->ctx.arena.dalloc(cnt);
+            Shape sh{1, {cnt}};
+            int id[1] = {0};
+            permute_any(h->ctx, src32, true, sh, id, tmp, false, 1.0, 0.0);
+            ADC_CUDA(cudaMemcpyAsync(out, tmp, cnt * sizeof(double), cudaMemcpyDeviceToHost, h->ctx.stream));
+            ADC_CUDA(cudaStreamSynchronize(h->ctx.stream));
+            return ADC_OK;
         }
         ADC_CUDA(cudaMemcpyAsync(out, src, cnt * sizeof(double), cudaMemcpyDeviceToHost, h->ctx.stream));
         ADC_CUDA(cudaStreamSynchronize(h->ctx.stream));
@@ -3116,3 +3335,4 @@ void adc_destroy(adc_handle* h) {
 }
 
 }  // extern "C"
+
