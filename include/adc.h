@@ -281,7 +281,11 @@ int adc_davidson_batch(adc_handle* const* h, int nmol, int nroots, double tol, d
  * factors), "diag" [dim], or "X" [nroots][nmo]: the spectroscopic
  * amplitudes X_{p,mu} = sum_nu T_{p,nu} (S Y~)_nu of the last adc_davidson
  * that computed spectroscopic factors (Eq. spec_amp with the Appendix
- * renormalisation, P_mu = 2 sum_p X_{p,mu}^2; occupied orbitals first).
+ * renormalisation, P_mu = 2 sum_p X_{p,mu}^2; occupied orbitals first), or
+ * "setup_seconds" [8]: wall seconds of adc_setup's phases (restricted handles):
+ * inputs and the ladder's operand planes, integrals, amplitudes and E(2), the
+ * ladder of t, the rest of t2(2) with t1(2) and E(3), the one-particle block,
+ * the transition moments' parts and the diagonal, and the total.
  * n = number of doubles the buffer holds.  Errors: ADC_ERR_ARG (unknown name,
  * buffer too small, or the intermediate does not exist at this order / yet).
  */
@@ -299,6 +303,17 @@ int adc_get_tensor(adc_handle* h, const char* name, double* out, long long n);
  * Errors: ADC_ERR_ARG, ADC_ERR_CUDA.
  */
 int adc_kernel_timing(adc_handle* h, int enable, double* out);
+
+/*
+ * The launches recorded by the last adc_kernel_timing bracket, one by one (after
+ * it was stopped).  out NULL: returns the number of launches.  Else out holds at
+ * least 7 doubles per launch and receives, per launch: M, N, K (padded), tile
+ * width, algorithmic flops, milliseconds (CUDA events on the launch's stream),
+ * and 1 for the DF ladder's GEMMs, 0 for the other contractions; returns the
+ * number of launches.  Errors: ADC_ERR_ARG (NULL handle, timing still running,
+ * buffer too short), ADC_ERR_CUDA.
+ */
+long long adc_kernel_launches(adc_handle* h, double* out, long long n);
 
 /*
  * Allocation-free density-fitted ladder: out[n] = sum_Q B^Q X[n] B^Q for nmat

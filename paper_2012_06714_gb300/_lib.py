@@ -35,6 +35,7 @@ EXPORTED = [
     "adc_mp_energy",
     "adc_setup_unrestricted",
     "adc_kernel_timing",
+    "adc_kernel_launches",
     "adc_ladder_noalloc",
     "adc_last_error",
     "adc_destroy",
@@ -96,6 +97,8 @@ def load_library():
     lib.adc_mp_energy.argtypes = [P, P, ctypes.c_int]
     lib.adc_setup_unrestricted.argtypes = [P, P, P, P, I, I, I, I, I, I, ctypes.POINTER(Options), ctypes.POINTER(P)]
     lib.adc_kernel_timing.argtypes = [P, I, P]
+    lib.adc_kernel_launches.argtypes = [P, P, LL]
+    lib.adc_kernel_launches.restype = LL
     lib.adc_ladder_noalloc.argtypes = [P, P, P, LL]
     lib.adc_spectrum.argtypes = [P, P, I, D, P, I, P]
     lib.adc_mlp_nweights.argtypes = []
@@ -287,6 +290,18 @@ class ADC:
             return None
         return dict(launches=int(out[0]), ms=out[1], algo_flops=out[2], mma_flops=out[3], kernels=int(out[4]),
                     ladder_launches=int(out[5]), ladder_ms=out[6], ladder_algo_flops=out[7], ladder_mma_flops=out[8])
+
+    def kernel_launches(self):
+        """The launches of the last kernel_timing bracket: array [n, 7] of M, N, K, tile width,
+        algorithmic flops, milliseconds, ladder (1) or other contraction (0)."""
+        n = self._lib.adc_kernel_launches(self._h, None, 0)
+        if n < 0:
+            self._check(int(n))
+        out = np.zeros((max(n, 1), 7))
+        r = self._lib.adc_kernel_launches(self._h, out.ctypes.data, out.size)
+        if r < 0:
+            self._check(int(r))
+        return out[:n]
 
     def close(self):
         if getattr(self, "_h", None):

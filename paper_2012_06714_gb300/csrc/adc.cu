@@ -48,6 +48,7 @@ struct adc_handle {
     double* ring2 = nullptr;
     double* t1_3 = nullptr;  // third-order singles (ADC(3) transition moments only), made on first use
     double emp[2] = {0.0, 0.0};  // MP correlation energy E(2), E(3) (Sec. III A step 2)
+    double setup_times[8] = {};  // wall seconds of the setup phases (adc_get_tensor "setup_seconds")
     // unrestricted (open-shell) reference: o, v count spin orbitals, the 2p1h / 2h1p basis
     // holds the restricted pairs (i, a<b) / (i<j, a), and the <pq||rs> blocks are kept
     bool unrestricted = false;
@@ -923,6 +924,18 @@ static void transition_parts(adc_handle* h, bool third, double* Tpp, double* t1x
 
 static void setup(adc_handle* h, const double* eps_in, const double* B_in, int on_device) {
     Ctx& c = h->ctx;
+    // phase timer: 0 inputs and the ladder's operand planes, 1 integrals, 2 amplitudes and E(2),
+    // 3 the ladder of t, 4 the rest of t2(2), t1(2) and E(3), 5 the 1p-1p / 1h-1h block,
+    // 6 the transition moments' parts (lean) and the diagonal, 7 total
+    const auto t_start = std::chrono::steady_clock::now();
+    auto t_last = t_start;
+    auto tick = [&](int k) {
+        ADC_CUDA(cudaStreamSynchronize(c.stream));
+        const auto now = std::chrono::steady_clock::now();
+        h->setup_times[k] += std::chrono::duration<double>(now - t_last).count();
+        h->setup_times[7] = std::chrono::duration<double>(now - t_start).count();
+        t_last = now;
+    };
     ADC_BLAS(cublasCreate(&c.blas));
     ADC_BLAS(cublasSetStream(c.blas, c.stream));
     ADC_BLAS(cublasSetMathMode(c.blas, CUBLAS_DEFAULT_MATH));
@@ -964,6 +977,7 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
         h->tc = ladder_tc_create(c, h->Bvv, (int)Q, (int)v, h->opt.aux_chunk);
         noalloc_prepare();  // the allocation-free ladder's scratch address on this device, resolved up front
     }
+    tick(0);
     // integrals (Eq. 19)
     const long long o2v2 = o * o * v * v;
     const bool lean = h->lean;
@@ -984,6 +998,7 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
         int pr[4] = {1, 2, 0, 3};  // (j, i, a, c) -> (i, a, j, c)
         permute(c, h->oovv, s4, pr, h->ring2, ea ? -1.0 : 1.0, 1.0);
     }
+    tick(1);
     // amplitudes (Eqs. t_singles, t_doubles)
     h->t = h->dmalloc(o2v2);
     k_make_t<<<grid_for(o2v2), 256, 0, c.stream>>>((int)o, (int)v, h->eps, h->ovov, h->t);
@@ -1018,6 +1033,7 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
         h->f_oovv = to_f32(h, h->oovv, o2v2);
         h->f_ovov = to_f32(h, h->ovov, o2v2);
     }
+    tick(2);
     Scope setup_scope(c.arena);
     double* XL = nullptr;  // EA: the ladder term of the 1p-1p block, formed while the ladder of t is alive
     if (h->order >= 3) {
@@ -1037,6 +1053,7 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
             ladder(h, h->t, o * o, Lt, twice);
             axpby(c, o2v2, 0.0, Lt, -1.0, Lt);
         }
+        tick(3);
         double* N = Lt;  // t2(2) numerator, formed in the ladder's buffer unless the ladder is kept
         if (keep_Lt) {
             h->Lt = Lt;
@@ -1089,6 +1106,7 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
         h->f_t = to_f32(h, h->t, o2v2);
         if (h->t_2) h->f_t2 = to_f32(h, h->t_2, o2v2);
     }
+    tick(4);
     const long long n1 = h->n1();
     if (h->opt.m11_on_the_fly) {
         // step 3 skipped: sigma applies the block from intermediates (the diagonal preconditioner
@@ -1122,6 +1140,7 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
         setup_m11_ip(h);
         c.gemm_mode = saved;
     }
+    tick(5);
     if (lean) {
         // what the transition moments need beyond t and t2(2), made while setup's memory is free
         Scope sc(c.arena);
@@ -1139,7 +1158,7 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
     h->diag = h->dmalloc(h->dim());
     k_diag<<<grid_for(h->dim()), 256, 0, c.stream>>>(h->kind == ADC_EA, (int)o, (int)v, h->eps, h->M11, h->diag);
     launch_check(c);
-    ADC_CUDA(cudaStreamSynchronize(c.stream));
+    tick(6);
 }
 
 // --------------------------------------------------------------------------
@@ -3239,6 +3258,14 @@ int adc_get_tensor(adc_handle* h, const char* name, double* out, long long n) {
         } else if (s == "diag") {
             src = h->diag;
             cnt = h->dim();
+        } else if (s == "setup_seconds") {
+            cnt = 8;
+            if (n < cnt) {
+                h->err = "adc_get_tensor: buffer too small";
+                return ADC_ERR_ARG;
+            }
+            std::memcpy(out, h->setup_times, sizeof(h->setup_times));
+            return ADC_OK;
         } else if (s == "X") {
             // host copy kept by the last adc_davidson that computed spectroscopic factors
             cnt = (long long)h->X_last.size();
@@ -3289,6 +3316,7 @@ int adc_kernel_timing(adc_handle* h, int enable, double* out) {
             c.ev_ladder.clear();
             c.ev_algo.clear();
             c.ev_mma.clear();
+            c.ev_shape.clear();
             c.algo_flops = c.mma_flops = 0.0;
             c.kernels_at_start = c.kernels;
             c.timing = true;
@@ -3324,6 +3352,32 @@ int adc_kernel_timing(adc_handle* h, int enable, double* out) {
         }
         return ADC_OK;
     })
+}
+
+long long adc_kernel_launches(adc_handle* h, double* out, long long n) {
+    if (!h) return ADC_ERR_ARG;
+    Ctx& c = h->ctx;
+    const long long cnt = (long long)c.ev_start.size();
+    if (!out) return cnt;
+    if (c.timing || n < 7 * cnt) {
+        h->err = "adc_kernel_launches: timing still on, or buffer shorter than 7 doubles per launch";
+        return ADC_ERR_ARG;
+    }
+    try {
+        for (long long i = 0; i < cnt; ++i) {
+            float t = 0.f;
+            ADC_CUDA(cudaEventElapsedTime(&t, c.ev_start[i], c.ev_stop[i]));
+            double* r = out + 7 * i;
+            for (int k = 0; k < 4; ++k) r[k] = c.ev_shape[4 * i + k];
+            r[4] = c.ev_algo[i];
+            r[5] = t;
+            r[6] = c.ev_ladder[i] ? 1.0 : 0.0;
+        }
+    } catch (const adc::Error& e) {
+        h->err = e.what();
+        return e.code;
+    }
+    return cnt;
 }
 
 const char* adc_last_error(const adc_handle* h) { return h ? h->err.c_str() : g_setup_error.c_str(); }

@@ -153,6 +153,7 @@ struct Ctx {
     std::vector<cudaEvent_t> ev_start, ev_stop;
     std::vector<char> ev_ladder;          // launch is one of the DF ladder GEMMs
     std::vector<double> ev_algo, ev_mma;  // its algorithmic / issued tensor-core flops
+    std::vector<double> ev_shape;         // its M, N, K, tile width (4 per launch)
     double algo_flops = 0.0, mma_flops = 0.0;
     long long kernels_at_start = 0;
     // FP32 copies (in GEMM operand order) of operands marked constant, reused across calls

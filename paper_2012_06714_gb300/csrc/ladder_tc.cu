@@ -1109,6 +1109,7 @@ void launch_gemm(Ctx& c, const Maps& maps, int planes, int a_row0, int b_x0, int
         c.ev_ladder.push_back(ep.mode != 2);  // the DF ladder's two GEMMs (mode 2: other contractions)
         c.ev_algo.push_back(algo_flops);
         c.ev_mma.push_back(mma);
+        for (double x : {(double)M, (double)N, (double)K, (double)BN}) c.ev_shape.push_back(x);
         c.algo_flops += algo_flops;
         c.mma_flops += mma;
     }
