@@ -447,6 +447,16 @@ def run_large(args):
     torch.cuda.synchronize()
     kt = g.kernel_timing(False)
     ms = e0.elapsed_time(e1) / steps
+    # the other tensor-core contractions by shape (milliseconds summed over launches; K slices
+    # of one contraction run concurrently on side streams, so their sum exceeds their wall time)
+    shapes = {}
+    for M, N, K, BN, fl, lms, lad in g.kernel_launches():
+        if not lad:
+            a = shapes.setdefault(f"M{int(M)} N{int(N)} K{int(K)}", [0, 0.0, 0.0])
+            a[0] += 1
+            a[1] += fl / steps
+            a[2] += lms / steps
+    top = sorted(shapes.items(), key=lambda kv: -kv[1][2])[:12]
     bf16_peak, bf16_burst, _, src = peaks()
     lt = kt["ladder_algo_flops"] / (kt["ladder_ms"] / 1e3) / 1e12
     out["sigma"] = {"ms_per_step": ms, "tflops": ladder_flops(o, v, naux, nvec) / (ms / 1e3) / 1e12,
@@ -455,7 +465,9 @@ def run_large(args):
                     "other_tensor_core_ms_per_step": (kt["ms"] - kt["ladder_ms"]) / steps,
                     "other_tensor_core_tflops": (kt["algo_flops"] - kt["ladder_algo_flops"])
                     / max(kt["ms"] - kt["ladder_ms"], 1e-9) / 1e9,
-                    "launches_per_step": kt["kernels"] / steps}
+                    "launches_per_step": kt["kernels"] / steps,
+                    "other_by_shape": {k: {"launches": n // steps, "ms": t, "tflops": fl / max(t, 1e-9) / 1e9}
+                                       for k, (n, fl, t) in top}}
     del X, S
     torch.cuda.empty_cache()
     t0 = time.perf_counter()

@@ -775,11 +775,14 @@ static void einsum_core(Ctx& c, const char* specstr, double alpha, const T& A, c
     if (c.gemm_mode == 2 && nb == 1) {
         // the mixed sigma: tensor cores for the large contractions, own kernels for the rest
         const bool big = 2.0 * M * N * K >= c.fp32_min_flops;
-        // few-vector shapes stay on the tensor cores when their large operand is a constant of
-        // the handle (its split planes are cached once); the own bandwidth kernels take the rest
+        // few-vector shapes: the own bandwidth kernels read the large operand once, in place when
+        // it is an FP64 tensor already in their order ([K][N] for M <= 8, [M][K] for N <= 8);
+        // otherwise the tensor cores take them when the large operand is a constant of the
+        // handle (its split planes are cached once, the permuted FP64 copy would be made per call)
         const bool skinny = std::min(M, N) <= 8;
         const bool big_const = M <= N ? B.constant : A.constant;
-        if (big && tc_gemm_fits(M, N, K) && (!skinny || big_const)) {
+        const bool big_in_place = M <= N ? (!B.f32 && sp.b == con + fb) : (!A.f32 && sp.a == fa + con);
+        if (big && tc_gemm_fits(M, N, K) && (!skinny || (big_const && !big_in_place))) {
             einsum_tc(c, sp.a, sp.b, sp.c, dim, fa, fb, con, alpha, A, B, beta, C, c32);
         } else {
             const double* Ap = to_order(c, A.p, sp.a, dim, fa + con, A.f32);
