@@ -854,19 +854,22 @@ static void make_t1_third_order(adc_handle* h) {
         {
             // E2/4 = -sum t_jk^ad V_jkdi, V_jkdi = sum_Q sum_b B^Q_db sum_c tau_jk^cb B^Q_ic
             Scope s2(c.arena);
-            Buf tauS = scratch(c.arena, o2v2, f32);  // tau_jk^cb stored [j][k][b][c]
-            perm_into(c, U4, {0, 1, 3, 2}, tauS, 1.0, 0.0);
+            // tau_jk^cb held as [b][j][k][c], the order in which the first contraction's GEMM reads it
+            Buf tauS = scratch(c.arena, o2v2, f32);
+            perm_into(c, U4, {3, 0, 1, 2}, tauS, 1.0, 0.0);
             double* V = c.arena.dalloc(v * o * o * o);  // [d][j][k][i]
-            // auxiliary functions per chunk: the aux_chunk option if set, else a 4 GiB slab of W
+            // auxiliary functions per chunk: the aux_chunk option if set, else a slab of W of
+            // 2^29 elements (FP64) or 2^31 (FP32, lean)
             const long long per = v * o * o * o;
+            const long long slab = f32 ? (1LL << 31) : (1LL << 29);
             const long long qc = h->opt.aux_chunk > 0 ? std::min<long long>(Q, h->opt.aux_chunk)
-                                                      : std::max(1LL, std::min(Q, (1LL << 29) / std::max(per, 1LL)));
-            double* W = c.arena.dalloc(qc * per);  // [Q][b][j][k][i]
+                                                      : std::max(1LL, std::min(Q, slab / std::max(per, 1LL)));
+            Buf W = scratch(c.arena, qc * per, f32);  // [Q][b][j][k][i]
             for (long long q0 = 0; q0 < Q; q0 += qc) {
                 const long long nq = std::min(qc, Q - q0);
-                einsum(c, "jkbc,Qic->Qbjki", 1.0, tauS.as({o, o, v, v}), tn(h->Bov + q0 * o * v, {nq, o, v}), 0.0, W,
-                       {nq, v, o, o, o});
-                einsum(c, "Qdb,Qbjki->djki", 1.0, tn(h->Bvv + q0 * v * v, {nq, v, v}), tn(W, {nq, v, o, o, o}),
+                ein(c, "bjkc,Qic->Qbjki", 1.0, tauS.as({v, o, o, v}), tn(h->Bov + q0 * o * v, {nq, o, v}), 0.0, W,
+                    {nq, v, o, o, o});
+                einsum(c, "Qdb,Qbjki->djki", 1.0, tn(h->Bvv + q0 * v * v, {nq, v, v}), W.as({nq, v, o, o, o}),
                        q0 == 0 ? 0.0 : 1.0, V, {v, o, o, o});
             }
             einsum(c, "jkad,djki->ia", -1.0, T4, tn(V, {v, o, o, o}), 1.0, num, {o, v});

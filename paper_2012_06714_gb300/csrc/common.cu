@@ -90,6 +90,89 @@ __global__ void permute_split_kernel(const Tin* __restrict__ in, __nv_bfloat16* 
     }
 }
 
+// ---- transposing permutes through shared memory ----------------------------------
+// When the output's fastest axis x is strided in the input, the plain kernels above read one
+// element per memory sector.  These take a 32 x 32 tile over x and the axis y that is
+// contiguous in the input: threads read along y (coalesced), the tile is transposed in shared
+// memory, threads write along x (coalesced).  The remaining output axes index the tiles.
+struct TileArgs {
+    int nrest;
+    long long rdim[kMaxDim], rsin[kMaxDim], rsout[kMaxDim];  // other output axes: extent, input / output stride
+    long long nx, ny, sx_in, sy_out;  // x: output-innermost axis (input stride sx_in); y: input-contiguous axis
+    long long ntx, nty, nblocks;
+};
+
+// output of two split BF16 planes [rows][Kp] (the linear output index counts [rows][K])
+struct OpPlanes {
+    __nv_bfloat16 *o0, *o1;
+    long long K, Kp;
+    __device__ long long addr(long long lin) const {
+        const long long r = lin / K;
+        return r * Kp + (lin - r * K);
+    }
+    __device__ void put(long long ad, double x) const {
+        const __nv_bfloat16 h = __double2bfloat16(x);
+        o0[ad] = h;
+        o1[ad] = __double2bfloat16(x - (double)__bfloat162float(h));
+    }
+};
+// out = alpha x + beta out
+template <typename Tout>
+struct OpAxpby {
+    Tout* out;
+    double alpha, beta;
+    __device__ long long addr(long long lin) const { return lin; }
+    __device__ void put(long long ad, double x) const {
+        const double v = alpha * x;
+        out[ad] = (Tout)(beta == 0.0 ? v : v + beta * (double)out[ad]);
+    }
+};
+
+template <typename Tin, typename Op>
+__global__ void __launch_bounds__(256) k_permute_tiled(const Tin* __restrict__ in, TileArgs a, Op op) {
+    __shared__ double tile[32][33];
+    for (long long b = blockIdx.x; b < a.nblocks; b += gridDim.x) {
+        long long t = b;
+        const long long tx = t % a.ntx;
+        t /= a.ntx;
+        const long long ty = t % a.nty;
+        t /= a.nty;
+        long long in_off = 0, out_lin = 0;
+        for (int j = a.nrest - 1; j >= 0; --j) {
+            const long long cj = t % a.rdim[j];
+            t /= a.rdim[j];
+            in_off += cj * a.rsin[j];
+            out_lin += cj * a.rsout[j];
+        }
+        const long long x0 = tx * 32, y0 = ty * 32;
+        for (int i = threadIdx.y; i < 32; i += 8) {
+            const long long x = x0 + i, y = y0 + threadIdx.x;
+            if (x < a.nx && y < a.ny) tile[threadIdx.x][i] = (double)in[in_off + x * a.sx_in + y];
+        }
+        __syncthreads();
+        for (int i = threadIdx.y; i < 32; i += 8) {
+            const long long y = y0 + i, x = x0 + threadIdx.x;
+            if (y < a.ny && x < a.nx) {
+                // the row's 32 x values share one output row (x is the innermost output axis)
+                const long long ad = op.addr(out_lin + y * a.sy_out + x0);
+                op.put(ad + threadIdx.x, tile[i][threadIdx.x]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// zero the K padding columns of split planes [rows][Kp]
+__global__ void k_zero_pad(__nv_bfloat16* __restrict__ o0, __nv_bfloat16* __restrict__ o1, long long rows, long long K,
+                           long long Kp) {
+    const long long w = Kp - K, n = rows * w;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / w, k = K + (i - r * w);
+        o0[r * Kp + k] = __double2bfloat16(0.0);
+        o1[r * Kp + k] = __double2bfloat16(0.0);
+    }
+}
+
 __global__ void sum_slices_kernel(int S, long long n, const double* __restrict__ T, double* __restrict__ C) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         double a = 0.0;
@@ -398,6 +481,55 @@ void own_gemm(Ctx& c, long long M, long long N, long long K, double alpha, const
     c.arena.release(mk);
 }
 
+// The tiled form applies when, after dropping unit axes, the output's innermost axis is
+// strided in the input and both it and the input-contiguous axis are at least 8 long.
+static bool tiled_args(const PermArgs& p, TileArgs& t) {
+    long long d[kMaxDim], si[kMaxDim];
+    int nd = 0;
+    for (int j = 0; j < p.nd; ++j)
+        if (p.dout[j] > 1) {
+            d[nd] = p.dout[j];
+            si[nd] = p.sin[j];
+            ++nd;
+        }
+    if (nd < 2 || si[nd - 1] == 1) return false;
+    int jy = -1;
+    for (int j = 0; j < nd - 1; ++j)
+        if (si[j] == 1) jy = j;
+    if (jy < 0 || d[jy] < 8 || d[nd - 1] < 8) return false;
+    long long so[kMaxDim], acc = 1;
+    for (int j = nd - 1; j >= 0; --j) {
+        so[j] = acc;
+        acc *= d[j];
+    }
+    t.nrest = 0;
+    long long rest = 1;
+    for (int j = 0; j < nd - 1; ++j) {
+        if (j == jy) continue;
+        t.rdim[t.nrest] = d[j];
+        t.rsin[t.nrest] = si[j];
+        t.rsout[t.nrest] = so[j];
+        ++t.nrest;
+        rest *= d[j];
+    }
+    t.nx = d[nd - 1];
+    t.sx_in = si[nd - 1];
+    t.ny = d[jy];
+    t.sy_out = so[jy];
+    t.ntx = (t.nx + 31) / 32;
+    t.nty = (t.ny + 31) / 32;
+    t.nblocks = t.ntx * t.nty * rest;
+    return true;
+}
+
+template <typename Tin, typename Op>
+static void launch_tiled(Ctx& c, const Tin* in, const TileArgs& t, const Op& op) {
+    const long long g = std::min<long long>(t.nblocks, 152LL * 16);
+    k_permute_tiled<Tin, Op><<<(unsigned)g, dim3(32, 8), 0, c.stream>>>(in, t, op);
+    ++c.kernels;
+    ADC_CUDA(cudaGetLastError());
+}
+
 void permute(Ctx& c, const double* in, const Shape& s, const int* perm, double* out, double alpha, double beta) {
     PermArgs a;
     a.nd = s.nd;
@@ -413,6 +545,11 @@ void permute(Ctx& c, const double* in, const Shape& s, const int* perm, double* 
         total *= a.dout[j];
     }
     if (total == 0) return;
+    TileArgs t;
+    if (tiled_args(a, t)) {
+        launch_tiled(c, in, t, OpAxpby<double>{out, alpha, beta});
+        return;
+    }
     if (total <= 0xffffffffLL)  // every offset is below total
         permute_kernel<unsigned><<<grid_for(total), 256, 0, c.stream>>>(in, out, a, total, alpha, beta);
     else
@@ -444,6 +581,11 @@ static void permute_cvt(Ctx& c, const Tin* in, const Shape& s, const int* perm, 
     long long total;
     PermArgs a = perm_args(s, perm, total);
     if (total == 0) return;
+    TileArgs t;
+    if (tiled_args(a, t)) {
+        launch_tiled(c, in, t, OpAxpby<Tout>{out, alpha, beta});
+        return;
+    }
     if (total <= 0xffffffffLL)
         permute_cvt_kernel<unsigned, Tin, Tout><<<grid_for(total), 256, 0, c.stream>>>(in, out, a, total, alpha, beta);
     else
@@ -455,6 +597,17 @@ static void permute_cvt(Ctx& c, const Tin* in, const Shape& s, const int* perm, 
 template <typename Tin>
 static void split_planes_t(Ctx& c, const Tin* in, const PermArgs& a, long long rows, long long K, long long Kp,
                            void* const* out) {
+    TileArgs t;
+    if (tiled_args(a, t)) {
+        launch_tiled(c, in, t, OpPlanes{(__nv_bfloat16*)out[0], (__nv_bfloat16*)out[1], K, Kp});
+        if (Kp > K) {
+            k_zero_pad<<<grid_for(rows * (Kp - K)), 256, 0, c.stream>>>((__nv_bfloat16*)out[0], (__nv_bfloat16*)out[1],
+                                                                         rows, K, Kp);
+            ++c.kernels;
+            ADC_CUDA(cudaGetLastError());
+        }
+        return;
+    }
     // 32-bit coordinates when the output index fits (every input offset is below rows * K)
     if (rows * Kp <= 0xffffffffLL)
         permute_split_kernel<unsigned, Tin><<<grid_for(rows * Kp), 256, 0, c.stream>>>(
