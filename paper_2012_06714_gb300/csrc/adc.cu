@@ -160,6 +160,44 @@ __global__ void k_make_t(int o, int v, const double* __restrict__ eps, const dou
         t[x] = ovov[(((long long)i * v + a) * o + j) * v + b] / D;
     }
 }
+// P[p] = t[i_p][j_p] (v x v matrices) for the pairs i_p <= j_p
+__global__ void k_pairs_gather(long long np, long long vv, int o, const int* __restrict__ pi, const int* __restrict__ pj,
+                               const double* __restrict__ t, double* __restrict__ P) {
+    GRID_STRIDE(x, np * vv) {
+        const long long p = x / vv, e = x - p * vv;
+        P[x] = t[((long long)pi[p] * o + pj[p]) * vv + e];
+    }
+}
+// out[i][j] = L[p] and out[j][i] = L[p]^T for the pairs (i, j) = (i_p, j_p): 32 x 32 tiles, the
+// transposed copy through shared memory (block 32 x 8; grid over pairs x tiles)
+__global__ void k_pairs_scatter(long long np, int v, int o, const int* __restrict__ pi, const int* __restrict__ pj,
+                                const double* __restrict__ L, double* __restrict__ out) {
+    __shared__ double tile[32][33];
+    const long long nt = (v + 31) / 32, per = nt * nt, vv = (long long)v * v;
+    for (long long b = blockIdx.x; b < np * per; b += gridDim.x) {
+        const long long p = b / per, r = b - p * per;
+        const int a0 = (int)(r / nt) * 32, c0 = (int)(r % nt) * 32;
+        const int i = pi[p], j = pj[p];
+        const double* Lp = L + p * vv;
+        double* dij = out + ((long long)i * o + j) * vv;
+        double* dji = out + ((long long)j * o + i) * vv;
+        for (int y = threadIdx.y; y < 32; y += 8) {
+            const int a = a0 + y, c = c0 + threadIdx.x;
+            if (a < v && c < v) {
+                const double x = Lp[(long long)a * v + c];
+                dij[(long long)a * v + c] = x;
+                tile[y][threadIdx.x] = x;
+            }
+        }
+        __syncthreads();
+        if (i != j)
+            for (int y = threadIdx.y; y < 32; y += 8) {
+                const int c = c0 + y, a = a0 + threadIdx.x;  // out[j][i][c][a] = L[p][a][c]
+                if (a < v && c < v) dji[(long long)c * v + a] = tile[threadIdx.x][y];
+            }
+        __syncthreads();
+    }
+}
 // X[i,j,a,b] /= D_ij^ab
 __global__ void k_div_D2(int o, int v, const double* __restrict__ eps, double* __restrict__ X) {
     long long n = (long long)o * o * v * v;
@@ -1047,18 +1085,43 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
         const T T4 = op_t(h, false);
         const bool keep_Lt = h->opt.m11_on_the_fly && h->kind == ADC_EA;  // sigma applies the block from it
         double* Lt = h->dmalloc(o2v2);
-        fill(c, o2v2, 0.0, Lt);
-        ladder(h, h->t, o * o, Lt, h->lm_setup);  // sum_cd (ac|bd) t_ij^cd (it feeds M_11 directly)
-        if (h->opt.precision != ADC_PREC_FP64 && h->tc) {
-            // The tensor core's truncating FP32 accumulation biases each promoted partial sum toward
-            // zero, about linearly in the accumulation length.  With L(E) the ladder accumulated in
-            // epochs of E K blocks, 2 L(1) - L(2) removes the linear part of that bias (Richardson
-            // extrapolation in E): measured on t2(2), bias -1.8e-7 -> -6e-8 relative.  Formed in
-            // place: Lt <- -2 L(1), then += L(2), then negated.
-            const LadderMode twice{h->lm_setup.planes, 2 * h->lm_setup.epoch1, 2 * h->lm_setup.epoch2};
-            axpby(c, o2v2, 0.0, Lt, -2.0, Lt);
-            ladder(h, h->t, o * o, Lt, twice);
-            axpby(c, o2v2, 0.0, Lt, -1.0, Lt);
+        {
+            // L_ij = sum_Q B^Q t_ij B^Q, the sum_cd (ac|bd) t_ij^cd that feeds t2(2) and M_11.  With
+            // t_ji = t_ij^T and every B^Q symmetric, L_ji = L_ij^T: the ladder runs on the pairs
+            // i <= j only and the other half is their transpose.
+            Scope ps(c.arena);
+            const long long np = o * (o + 1) / 2, vv = v * v;
+            std::vector<int> hpi, hpj;
+            for (int i = 0; i < o; ++i)
+                for (int j = i; j < o; ++j) {
+                    hpi.push_back(i);
+                    hpj.push_back(j);
+                }
+            int* dpi = (int*)c.arena.alloc(2 * np * sizeof(int));
+            int* dpj = dpi + np;
+            ADC_CUDA(cudaMemcpyAsync(dpi, hpi.data(), np * sizeof(int), cudaMemcpyHostToDevice, c.stream));
+            ADC_CUDA(cudaMemcpyAsync(dpj, hpj.data(), np * sizeof(int), cudaMemcpyHostToDevice, c.stream));
+            double* P = c.arena.dalloc(np * vv);
+            double* Lp = c.arena.dalloc(np * vv);
+            k_pairs_gather<<<grid_for(np * vv), 256, 0, c.stream>>>(np, vv, (int)o, dpi, dpj, h->t, P);
+            launch_check(c);
+            fill(c, np * vv, 0.0, Lp);
+            ladder(h, P, np, Lp, h->lm_setup);
+            if (h->opt.precision != ADC_PREC_FP64 && h->tc) {
+                // The tensor core's truncating FP32 accumulation biases each promoted partial sum
+                // toward zero, about linearly in the accumulation length.  With L(E) the ladder
+                // accumulated in epochs of E K blocks, 2 L(E) - L(2E) removes the linear part of
+                // that bias (Richardson extrapolation in E): measured on t2(2), bias -1.8e-7 ->
+                // -6e-8 relative at E = 1.  Formed in place: Lp <- -2 L(E), then += L(2E), negated.
+                const LadderMode twice{h->lm_setup.planes, 2 * h->lm_setup.epoch1, 2 * h->lm_setup.epoch2};
+                axpby(c, np * vv, 0.0, Lp, -2.0, Lp);
+                ladder(h, P, np, Lp, twice);
+                axpby(c, np * vv, 0.0, Lp, -1.0, Lp);
+            }
+            const long long nt = (v + 31) / 32;
+            k_pairs_scatter<<<(unsigned)std::min<long long>(np * nt * nt, 152LL * 16), dim3(32, 8), 0, c.stream>>>(
+                np, (int)v, (int)o, dpi, dpj, Lp, Lt);
+            launch_check(c);
         }
         tick(3);
         double* N = Lt;  // t2(2) numerator, formed in the ladder's buffer unless the ladder is kept
