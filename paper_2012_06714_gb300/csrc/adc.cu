@@ -1085,10 +1085,25 @@ static void setup(adc_handle* h, const double* eps_in, const double* B_in, int o
         const T T4 = op_t(h, false);
         const bool keep_Lt = h->opt.m11_on_the_fly && h->kind == ADC_EA;  // sigma applies the block from it
         double* Lt = h->dmalloc(o2v2);
-        {
+        if (!lean) {
+            fill(c, o2v2, 0.0, Lt);
+            ladder(h, h->t, o * o, Lt, h->lm_setup);  // sum_cd (ac|bd) t_ij^cd (it feeds M_11 directly)
+            if (h->opt.precision != ADC_PREC_FP64 && h->tc) {
+                // The tensor core's truncating FP32 accumulation biases each promoted partial sum
+                // toward zero, about linearly in the accumulation length.  With L(E) the ladder
+                // accumulated in epochs of E K blocks, 2 L(E) - L(2E) removes the linear part of
+                // that bias (Richardson extrapolation in E): measured on t2(2), bias -1.8e-7 ->
+                // -6e-8 relative at E = 1.  Formed in place: Lt <- -2 L(E), then += L(2E), negated.
+                const LadderMode twice{h->lm_setup.planes, 2 * h->lm_setup.epoch1, 2 * h->lm_setup.epoch2};
+                axpby(c, o2v2, 0.0, Lt, -2.0, Lt);
+                ladder(h, h->t, o * o, Lt, twice);
+                axpby(c, o2v2, 0.0, Lt, -1.0, Lt);
+            }
+        } else {
             // L_ij = sum_Q B^Q t_ij B^Q, the sum_cd (ac|bd) t_ij^cd that feeds t2(2) and M_11.  With
-            // t_ji = t_ij^T and every B^Q symmetric, L_ji = L_ij^T: the ladder runs on the pairs
-            // i <= j only and the other half is their transpose.
+            // t_ji = t_ij^T and every B^Q symmetric, L_ji = L_ij^T: on a lean handle the ladder runs
+            // on the pairs i <= j only and the other half is their transpose (half the setup's
+            // largest cost; the plain layout evaluates every pair)
             Scope ps(c.arena);
             const long long np = o * (o + 1) / 2, vv = v * v;
             std::vector<int> hpi, hpj;
