@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <type_traits>
 
 #include <cuda_bf16.h>
 
@@ -203,7 +204,9 @@ __global__ void __launch_bounds__(SK_THREADS) k_skinny_m(int M, long long N, lon
                                                          const double* __restrict__ A, long long lda,
                                                          const double* __restrict__ B, long long ldb,
                                                          double* __restrict__ P) {
-    __shared__ double As[MM][SK_THREADS];
+    // the A chunk in shared memory, already rounded to FP32 for the FP32-product form
+    using AT = typename std::conditional<F32, float, double>::type;
+    __shared__ AT As[MM][SK_THREADS];
     const long long n = blockIdx.x * (long long)SK_THREADS + threadIdx.x;
     const long long k0 = blockIdx.y * kslice, k1 = min(K, k0 + kslice);
     double acc[MM];
@@ -214,7 +217,7 @@ __global__ void __launch_bounds__(SK_THREADS) k_skinny_m(int M, long long N, lon
         __syncthreads();
         if (threadIdx.x < kn)
 #pragma unroll
-            for (int m = 0; m < MM; ++m) As[m][threadIdx.x] = m < M ? A[m * lda + kc + threadIdx.x] : 0.0;
+            for (int m = 0; m < MM; ++m) As[m][threadIdx.x] = (AT)(m < M ? A[m * lda + kc + threadIdx.x] : 0.0);
         __syncthreads();
         if (n >= N) continue;
         const double* b = B + kc * ldb + n;
@@ -228,14 +231,13 @@ __global__ void __launch_bounds__(SK_THREADS) k_skinny_m(int M, long long N, lon
                 for (int m = 0; m < MM; ++m) part[m] = 0.f;
                 const int ke = min(kn, k2 + SK_CHUNK);
                 for (int kk = k2; kk < ke; kk += U) {
-                    double bv[U];
+                    float bv[U];
 #pragma unroll
-                    for (int u = 0; u < U; ++u) bv[u] = kk + u < ke ? b[(long long)(kk + u) * ldb] : 0.0;
+                    for (int u = 0; u < U; ++u) bv[u] = kk + u < ke ? (float)b[(long long)(kk + u) * ldb] : 0.f;
 #pragma unroll
                     for (int u = 0; u < U; ++u)
 #pragma unroll
-                        for (int m = 0; m < MM; ++m)
-                            part[m] = fmaf(kk + u < ke ? (float)As[m][kk + u] : 0.f, (float)bv[u], part[m]);
+                        for (int m = 0; m < MM; ++m) part[m] = fmaf(kk + u < ke ? (float)As[m][kk + u] : 0.f, bv[u], part[m]);
                 }
 #pragma unroll
                 for (int m = 0; m < MM; ++m) acc[m] += (double)part[m];
