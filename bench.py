@@ -261,6 +261,24 @@ def fp64_plain_profile():
             "speedup_mixed_vs_fp64_same_run": d.get("speedup_mixed_vs_fp64")}
 
 
+def large_workload_profile():
+    """The 1028-MO workload (EA-ADC(3), nocc=68, nvir=960, naux=3000), measured by `bench.py --large`
+    and committed under profiles/ (setup and solve take about eleven minutes and 254 GB, so it is
+    not rerun by the default bench); None if absent."""
+    p = os.path.join(ROOT, "profiles", "large_ea3_o68_v960_Q3000.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    sg, tr = d.get("sigma", {}), d.get("time_to_roots", {})
+    return {"source": "profiles/large_ea3_o68_v960_Q3000.json (bench.py --large)", "workload": d.get("case"),
+            "setup_s": d.get("setup_s"), "sigma_ms_per_step": sg.get("ms_per_step"), "sigma_tflops": sg.get("tflops"),
+            "ladder_tflops": sg.get("ladder_tflops"),
+            "ladder_frac_of_sustained_bf16_over_3": sg.get("ladder_frac_of_sustained_bf16_over_3"),
+            "time_to_4_roots_s": tr.get("seconds"), "sigma_vectors": tr.get("sigma_vectors"),
+            "status": tr.get("status"), "s_symmetry_rel": d.get("s_symmetry_rel"),
+            "peak_memory_mib": (d.get("memory") or {}).get("peak_used_mib")}
+
+
 def run_ladder_case(args):
     """Small profiling case of the ladder kernel (for ncu): EA-ADC(3) with
     nocc=4, nvir=400, naux=400 and 40 trial vectors, i.e. 160 ladder matrices
@@ -794,7 +812,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (B^Q > 2 GB)", "parallelism": "replicas" if world > 1 else "1 GPU",
                        "tiles": "autotuned in the first warm-up step (adc_options.tune_cache)"},
             "e2e": e2e, "roofline": roof, "gpu_launches": int(round(launches_per_step)), "clocks": clk,
-            "time_to_roots": roots}
+            "time_to_roots": roots, "large_workload": large_workload_profile()}
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
